@@ -1,0 +1,153 @@
+"""Seeded synthetic workloads (random draws and input layouts only).
+
+Layouts (the C-ABI uses the same ones):
+
+* Conventional zincblende cell = 8 sites.  Site b in 0..3 is on the first FCC sublattice
+  ("A"), b in 4..7 on the second ("B" = A site + a/4 (1,1,1)).
+* cell = (iz*ny + iy)*nx + ix;  atom = b*ncells + cell  (sublattice-major, cell-minor).
+* Bond slot of A site s (0..3) in cell c along direction k (0..3):
+  slot = (k*4 + s)*ncells + c, 16*ncells slots.  Directions in units of a/4:
+  k=0 (1,1,1), k=1 (1,-1,-1), k=2 (-1,1,-1), k=3 (-1,-1,1), from the A atom to the B atom.
+* Two-centre parameter order (14): ss_sigma, s*s*_sigma, ss*_sigma, sp_sigma, s*p_sigma,
+  sd_sigma, s*d_sigma, pp_sigma, pp_pi, pd_sigma, pd_pi, dd_sigma, dd_pi, dd_delta.
+  V[i, j, p] is the integral with the first-named orbital on an atom of species i and the
+  second on an atom of species j.
+* Onsite parameter order (4): E_s, E_p, E_d, E_s*.
+
+Random streams: a SeedSequence keyed by (seed, stream) per draw kind.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+STREAM_TB, STREAM_SPECIES, STREAM_STRAIN, STREAM_SIGMA, STREAM_DONOR, STREAM_START, STREAM_DOPING = range(7)
+
+PARAM_NAMES = ("ss_sigma", "s*s*_sigma", "ss*_sigma", "sp_sigma", "s*p_sigma", "sd_sigma",
+               "s*d_sigma", "pp_sigma", "pp_pi", "pd_sigma", "pd_pi", "dd_sigma", "dd_pi",
+               "dd_delta")
+SP3S_PARAMS = (0, 1, 2, 3, 4, 7, 8)           # the seven sp3s* two-centre integrals
+ONSITE_NAMES = ("E_s", "E_p", "E_d", "E_s*")
+
+SP3S, SP3D5S = 5, 10                          # orbitals per atom and spin
+SI_A_NM = 0.5431                              # silicon lattice constant (nm)
+
+
+def rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.SeedSequence([int(seed), int(stream)]))
+
+
+@dataclass
+class TBParams:
+    """Tight-binding parameter tables (eV) in the C-ABI layout."""
+    basis: int                                # SP3S (5) or SP3D5S (10)
+    onsite: np.ndarray                        # (nspecies, 4)
+    V: np.ndarray                             # (nspecies, nspecies, 14)
+    lambda_so: np.ndarray                     # (nspecies,)
+    eta: float = 2.0                          # Harrison exponent, V(d) = V(d0) (d0/d)^eta
+
+    @property
+    def nspecies(self) -> int:
+        return self.onsite.shape[0]
+
+
+def draw_tb_params(seed: int, basis: int, nspecies: int = 1,
+                   so_range=(0.01, 0.3)) -> TBParams:
+    """Per-species draws; pairs of unlike species take the mean of the two like-pair sets.
+
+    Ranges: E_s [-6,-3], E_p [0,3], E_d [3,6], E_s* [5,8]; every two-centre integral in
+    [-3,3]; lambda_SO in so_range.  sp3s* leaves the d entries at zero.
+    """
+    g = rng(seed, STREAM_TB)
+    onsite = np.zeros((nspecies, 4))
+    own = np.zeros((nspecies, 14))
+    lam = np.zeros(nspecies)
+    for s in range(nspecies):
+        onsite[s] = [g.uniform(-6, -3), g.uniform(0, 3), g.uniform(3, 6), g.uniform(5, 8)]
+        own[s] = g.uniform(-3, 3, size=14)
+        lam[s] = g.uniform(*so_range)
+    if basis == SP3S:
+        onsite[:, 2] = 0.0
+        mask = np.zeros(14, bool)
+        mask[list(SP3S_PARAMS)] = True
+        own[:, ~mask] = 0.0
+    V = 0.5 * (own[:, None, :] + own[None, :, :])
+    return TBParams(basis=basis, onsite=onsite, V=V, lambda_so=lam)
+
+
+@dataclass
+class LatticeSpec:
+    """A zincblende block of nx*ny*nz conventional cells with per-site species and per-bond strain.
+
+    periodic[d]: 0 hard wall (bonds leaving the block are dropped), 1 periodic, 2 periodic
+    with a Bloch phase (k given at assembly).
+    """
+    nx: int
+    ny: int
+    nz: int
+    periodic: tuple
+    species: np.ndarray                       # uint8 [8*ncells]
+    strain: np.ndarray                        # float64 [16*ncells], relative bond-length change
+    a_nm: float = SI_A_NM
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def natoms(self) -> int:
+        return 8 * self.ncells
+
+
+def lattice_spec(nx: int, ny: int, nz: int, periodic=(1, 1, 1), seed: int = 0,
+                 alloy_fraction: float = 0.0, strain_amp: float = 0.0,
+                 a_nm: float = SI_A_NM) -> LatticeSpec:
+    """Species 1 with probability alloy_fraction per site (stream 1); strain U[-amp, amp] (stream 2)."""
+    ncells = nx * ny * nz
+    if alloy_fraction > 0:
+        species = (rng(seed, STREAM_SPECIES).random(8 * ncells) < alloy_fraction).astype(np.uint8)
+    else:
+        species = np.zeros(8 * ncells, np.uint8)
+    if strain_amp > 0:
+        strain = rng(seed, STREAM_STRAIN).uniform(-strain_amp, strain_amp, size=16 * ncells)
+    else:
+        strain = np.zeros(16 * ncells)
+    return LatticeSpec(nx, ny, nz, tuple(int(p) for p in periodic), species, strain, a_nm)
+
+
+def start_block(seed: int, n: int, b: int = 1, dtype=np.float64) -> np.ndarray:
+    """Lanczos start block, uniform [-1,1] (stream 5), shape (b, n) (row = one vector)."""
+    g = rng(seed, STREAM_START)
+    x = g.uniform(-1, 1, size=(b, n))
+    if np.issubdtype(np.dtype(dtype), np.complexfloating):
+        x = x + 1j * g.uniform(-1, 1, size=(b, n))
+    return x.astype(dtype)
+
+
+def sigma_offset_fraction(seed: int) -> float:
+    """u ~ U[-0.05, 0.05] (stream 3); the shift is sigma = centre + u * width."""
+    return float(rng(seed, STREAM_SIGMA).uniform(-0.05, 0.05))
+
+
+def random_vectors(seed: int, n: int, b: int = 1, dtype=np.float64, stream: int = 99) -> np.ndarray:
+    """Generic uniform [-1,1] test vectors, shape (b, n)."""
+    g = rng(seed, stream)
+    x = g.uniform(-1, 1, size=(b, n))
+    if np.issubdtype(np.dtype(dtype), np.complexfloating):
+        x = x + 1j * g.uniform(-1, 1, size=(b, n))
+    return x.astype(dtype)
+
+
+# Named workloads -------------------------------------------------------------------------
+
+def config_si_periodic(n: int = 8, seed: int = 1):
+    """Bulk Si, n^3 cells, fully periodic, sp3s*, one species, unstrained (4,096 atoms at n=8)."""
+    return lattice_spec(n, n, n, (1, 1, 1), seed), draw_tb_params(seed, SP3S, 1)
+
+
+def config_sige_alloy(n: int = 50, seed: int = 2, spin_orbit: bool = False):
+    """Si0.7Ge0.3 random alloy, n^3 cells, hard walls, bond strain U[-2%,2%], sp3d5s*
+    (1,000,000 atoms at n=50)."""
+    lat = lattice_spec(n, n, n, (0, 0, 0), seed, alloy_fraction=0.3, strain_amp=0.02)
+    return lat, draw_tb_params(seed, SP3D5S, 2)
