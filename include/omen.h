@@ -1,0 +1,179 @@
+/*
+ * omen.h — C ABI of the GB300 tight-binding / Schrödinger–Poisson library.
+ *
+ * The calls follow the problem statement of OMEN 3-D (Lee, Ryu, Jiang, Klimeck,
+ * "Million Atom Electronic Structure and Device Calculations on Peta-Scale Computers"):
+ * an atomistic zincblende structure (Section I, Section II-A) → an empirical sp3s* /
+ * sp3d5s* tight-binding Hamiltonian with strain (Section I, abstract) → its eigenstates
+ * by an iterative (block) Lanczos solver (Section III-A item 1; benchmark unit "500 Lanczos
+ * iterations", Section II-B) → charge (Section III-A item 2) → finite-difference Poisson
+ * (Section III-A item 3) → self-consistent loop (Section III-A).
+ *
+ * Conventions (all calls):
+ *  - Every call returns an omen_status; nothing aborts or traps.  After a failure,
+ *    omen_last_error(ctx) returns a message (valid until the next call on ctx).
+ *  - Pointers named *_dev are device pointers on ctx's device; work is issued on ctx's
+ *    stream.  Pointers named *_host are host memory.  Caller owns every buffer it passes;
+ *    the library owns the opaque handles (free with the matching omen_free_*).
+ *  - One ctx per host thread.  Units: eV, nm, V, C/m^3, 1/nm.
+ *  - Structure layout: conventional cubic cells, cell = (iz*ny + iy)*nx + ix; 8 sites per
+ *    cell, site b in 0..3 on the first FCC sublattice (A) at a/4*(0,0,0),(0,2,2),(2,0,2),
+ *    (2,2,0), b in 4..7 on the second (B) at the A site + a/4*(1,1,1).
+ *    atom = b*ncells + cell.
+ *  - Bond slots: A site s of cell c along direction k (a/4 units: k=0 (1,1,1), 1 (1,-1,-1),
+ *    2 (-1,1,-1), 3 (-1,-1,1), pointing from the A atom to the B atom):
+ *    slot = (k*4 + s)*ncells + c.
+ *  - Vector layout (H rows): row = o*natoms + atom, o = spin*norb + orbital; orbitals
+ *    s, px, py, pz, [dyz, dzx, dxy, dx2-y2, d3z2-r2], s*.  A block of nvec vectors is
+ *    stored vector after vector ([nvec][nrows]).  Real Hamiltonians use double (F64) or
+ *    float (F32) elements; complex ones (spin-orbit or Bloch phase) interleave re,im.
+ */
+#ifndef OMEN_H
+#define OMEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OMEN_OK = 0,
+  OMEN_EINVAL = 1,       /* bad argument (message says which) */
+  OMEN_ENOMEM = 2,       /* device or host allocation failed */
+  OMEN_ENOCONV = 3,      /* iteration limit reached; partial results and info are filled */
+  OMEN_ENUMERIC = 4,     /* NaN/Inf or breakdown that could not be recovered */
+  OMEN_ETIMEOUT = 5,     /* a bounded device wait expired */
+  OMEN_ECUDA = 6,        /* CUDA runtime error (message has the CUDA error string) */
+  OMEN_EUNSUPPORTED = 7  /* valid request that this build does not implement */
+} omen_status;
+
+enum { OMEN_SP3S = 5, OMEN_SP3D5S = 10 };                   /* orbitals per atom and spin */
+enum { OMEN_HARD_WALL = 0, OMEN_PERIODIC = 1, OMEN_BLOCH = 2 }; /* per-direction boundary */
+enum {
+  OMEN_F64 = 0,          /* FP64 storage and arithmetic */
+  OMEN_F32 = 1,          /* FP32 bond blocks and Krylov vectors (complex64 when complex);
+                            Lanczos dots, orthogonalisation coefficients and the projected
+                            eigenproblem in FP64 */
+  OMEN_F32_REFINE64 = 2  /* OMEN_F32 solve, then an FP64 Rayleigh–Ritz refinement */
+};
+enum { OMEN_LOWEST = 0, OMEN_NEAREST = 1 };                  /* which eigenvalues */
+
+typedef struct omen_ctx omen_ctx;
+typedef struct omen_lattice omen_lattice;
+typedef struct omen_ham omen_ham;
+
+/* ---- context --------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Allocates small device work buffers. */
+omen_status omen_create(omen_ctx** out, int device, void* cuda_stream);
+void omen_destroy(omen_ctx* ctx);
+const char* omen_last_error(const omen_ctx* ctx);
+/* Set the iteration budget of bounded device waits (0 = library default).  A wait that
+ * exhausts it makes the call return OMEN_ETIMEOUT with the device still usable. */
+omen_status omen_set_wait_limit(omen_ctx* ctx, long long spins);
+
+/* ---- structure (paper Section II-A: atoms of the domain and their neighbours) ---------- */
+
+typedef struct {
+  int nx, ny, nz;            /* conventional cells along x, y, z (each >= 1) */
+  int periodic[3];           /* OMEN_HARD_WALL (bonds leaving the block are dropped),
+                                OMEN_PERIODIC, or OMEN_BLOCH (periodic with a Bloch phase) */
+  double a_nm;               /* lattice constant (nm) */
+  const uint8_t* species_host; /* [8*ncells] species index per atom (< nspecies of the
+                                  parameters used with this structure) */
+  const double* strain_host; /* [16*ncells] relative bond-length change per bond slot
+                                (d = d0 (1 + strain)), or NULL for none; slots of bonds that
+                                do not exist are ignored */
+} omen_lattice_desc;
+
+/* Copy the structure to the device.  Neighbours are implicit (computed from the cell
+ * index); no neighbour list is stored.  Errors: EINVAL (sizes), ENOMEM. */
+omen_status omen_build_lattice(omen_ctx* ctx, const omen_lattice_desc* desc, omen_lattice** out);
+void omen_free_lattice(omen_lattice* lat);
+/* Number of atoms and of existing bonds (after the hard-wall rule). */
+omen_status omen_lattice_counts(const omen_lattice* lat, long long* natoms, long long* nbonds);
+
+/* ---- Hamiltonian (paper Section I: empirical sp3s* and sp3d5s* tight binding with strain) - */
+
+typedef struct {
+  int basis;                 /* OMEN_SP3S or OMEN_SP3D5S */
+  int nspecies;              /* 1..4 */
+  double onsite[4][4];       /* [species][E_s, E_p, E_d, E_s*] (eV) */
+  double V[4][4][14];        /* [species of atom 1][species of atom 2][integral] (eV) at d0:
+                                ss_sigma, s*s*_sigma, ss*_sigma, sp_sigma, s*p_sigma, sd_sigma,
+                                s*d_sigma, pp_sigma, pp_pi, pd_sigma, pd_pi, dd_sigma, dd_pi,
+                                dd_delta; the first-named orbital sits on atom 1 */
+  double lambda_so[4];       /* spin-orbit lambda per species (eV): lambda L.sigma on p */
+  double eta;                /* Harrison exponent: integrals scale as (d0/d)^eta */
+} omen_tb_params;
+
+typedef struct {
+  int spin_orbit;            /* 0/1: double the basis and add lambda L.sigma on p */
+  int precision;             /* OMEN_F64, OMEN_F32 or OMEN_F32_REFINE64 */
+  int matrix_free;           /* 0: store every bond block; 1: regenerate blocks in H·X from
+                                species, direction and strain */
+  const double* k;           /* NULL or [3] Bloch wave vector (1/nm) for OMEN_BLOCH axes */
+  const double* U_atom_dev;  /* NULL or [natoms] onsite potential energy (eV), e.g. -phi */
+} omen_ham_opts;
+
+/* Assemble H on the device: onsite energies (+U, + spin-orbit), Slater–Koster bond blocks
+ * for the bond directions, scaled by (d0/d)^eta (Slater & Koster 1954, Table I; Harrison).
+ * The structure must outlive the Hamiltonian.  Errors: EINVAL, ENOMEM, ECUDA. */
+omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, const omen_tb_params* p,
+                            const omen_ham_opts* opts, omen_ham** out);
+void omen_free_ham(omen_ham* ham);
+/* Rows of H, whether it is complex, and the element size in bytes of its vectors. */
+omen_status omen_ham_shape(const omen_ham* ham, long long* nrows, int* is_complex, int* elem_bytes);
+/* Replace the onsite potential (eV per atom, device) without rebuilding bonds. */
+omen_status omen_ham_set_potential(omen_ctx* ctx, omen_ham* ham, const double* U_atom_dev);
+
+/* y = (H - sigma) x for nvec vectors in the Hamiltonian's vector type (device).
+ * x and y must not overlap.  This is the operation the Lanczos recurrence repeats. */
+omen_status omen_hx(omen_ctx* ctx, const omen_ham* ham, const void* x_dev, void* y_dev,
+                    int nvec, double sigma);
+/* The same product with host buffers (copies in and out on the ctx stream; synchronous). */
+omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* ham, const void* x_host, void* y_host,
+                         int nvec, double sigma);
+
+/* ---- eigenpairs (paper Section III-A item 1: (block) Lanczos) -------------------------- */
+
+typedef struct {
+  int nev;                   /* wanted eigenpairs (>= 1) */
+  int which;                 /* OMEN_LOWEST, or OMEN_NEAREST (folded spectrum: Lanczos on
+                                (H - sigma)^2, eigenvalues by Rayleigh quotients on H) */
+  double sigma;              /* shift for OMEN_NEAREST (eV) */
+  double tol;                /* target bound on each eigenvalue's error (eV), from its FP64
+                                residual r: min(r, r^2/gap) (Weyl / Kato–Temple) */
+  int max_iter;              /* maximum block steps */
+  int block;                 /* block size b (>= largest multiplicity among wanted values) */
+  int basis;                 /* maximum basis size m (a multiple of b, > nev + b) */
+  const void* v0_host;       /* [block][nrows] start block in the vector type of the
+                                Hamiltonian's precision, or NULL for a fixed default */
+} omen_eig_opts;
+
+typedef struct {
+  int iterations;            /* block steps taken */
+  long long hx_count;        /* single-vector H·X products */
+  int restarts;
+  int converged;             /* 1 if every returned pair met tol */
+  double max_residual;       /* max FP64 ||H x - lambda x|| over returned pairs (eV) */
+  double max_error_bound;    /* max FP64 min(r, r^2/gap) over returned pairs (eV) */
+  double max_residual_raw;   /* F32_REFINE64: same as max_residual before refinement */
+  double seconds;            /* wall time of the call */
+} omen_eig_info;
+
+/* nev eigenpairs of H by thick-restart block Lanczos with full (twice-applied classical
+ * Gram–Schmidt) reorthogonalisation.  evals_host[nev] ascending; evecs_dev (or NULL)
+ * receives [nev][nrows] FP64-precision vectors (double / complex128) for OMEN_F64 and
+ * OMEN_F32_REFINE64, float / complex64 for OMEN_F32.  Returns ENOCONV with the best
+ * current pairs if max_iter is reached. */
+omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_eig_opts* opts,
+                      double* evals_host, void* evecs_dev, omen_eig_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OMEN_H */

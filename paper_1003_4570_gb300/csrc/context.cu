@@ -1,0 +1,42 @@
+// Context: device, stream, last error, small work buffers.
+#include "omen_internal.h"
+
+extern "C" omen_status omen_create(omen_ctx** out, int device, void* stream) {
+  if (!out) return OMEN_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return OMEN_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return OMEN_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return OMEN_ECUDA;
+  auto* c = new omen_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->wait_limit = 0;
+  c->work_bytes = 1 << 20;
+  if (cudaMalloc(&c->d_work, c->work_bytes) != cudaSuccess || cudaMalloc(&c->d_status, 64 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    omen_destroy(c);
+    return OMEN_ENOMEM;
+  }
+  *out = c;
+  return OMEN_OK;
+}
+
+extern "C" void omen_destroy(omen_ctx* c) {
+  if (!c) return;
+  cudaFree(c->d_work);
+  cudaFree(c->d_status);
+  delete c;
+}
+
+extern "C" const char* omen_last_error(const omen_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" omen_status omen_set_wait_limit(omen_ctx* c, long long spins) {
+  if (!c || spins < 0) return set_err(c, OMEN_EINVAL, "invalid wait limit");
+  c->wait_limit = spins;
+  return OMEN_OK;
+}

@@ -1,0 +1,304 @@
+// y = (H - sigma) x: the block-sparse tight-binding product repeated by the Lanczos
+// recurrence (paper Section II-B benchmarks "500 Lanczos iterations"; Section III-A item 1).
+//
+// One thread per atom (grid.y = site b, grid.x over cells, grid.z over vectors).  Each row
+// of H has an onsite block and four bond blocks.  Bond blocks are stored once per bond
+// (A-atom slot); an A atom applies B, its B partner applies B^T, so no block is duplicated.
+// The partner's copy of the block is read within about one z-plane of cells of the first
+// read, which lies inside the L2 cache, so HBM sees each block about once.
+// Blocks are entry-major (blk[e*nslots + slot]): for a fixed entry, consecutive threads
+// (consecutive cells) read consecutive words.  Vectors are orbital-major, atom-minor, so the
+// per-orbital loads of x and stores of y are coalesced as well.
+// Bloch phase: a neighbour reached across the high (low) face of a Bloch-periodic direction d
+// is its periodic image shifted by +L_d (-L_d); its amplitude is multiplied by
+// exp(+i k_d L_d) (resp. the conjugate).
+#include "omen_internal.h"
+#include "sk_device.cuh"
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using t = double2; };
+template <> struct Cx<float> { using t = float2; };
+
+template <typename T, bool CPLX> struct VecT { using t = T; };
+template <typename T> struct VecT<T, true> { using t = typename Cx<T>::t; };
+
+template <typename T>
+struct HxArgs {
+  Geo g;
+  NeighbourTables nt;
+  const T* __restrict__ blk;          // stored blocks (entry-major), or null for matrix-free
+  const T* __restrict__ b0;           // [ns*ns*4][norb*norb] blocks at d0 (matrix-free)
+  const double* __restrict__ strain;  // [16*ncells]
+  const uint8_t* __restrict__ species;
+  const double* __restrict__ onsite;  // [ns][norb]
+  const double* __restrict__ U;       // [natoms]
+  const double* __restrict__ lambda;  // [ns]
+  const void* x;
+  void* y;
+  long long nrows;
+  double sigma;
+  double eta;
+  double2 phase[3];
+  int ns;
+};
+
+template <typename T>
+__device__ __forceinline__ typename Cx<T>::t cmul(typename Cx<T>::t a, typename Cx<T>::t b) {
+  typename Cx<T>::t r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+// Accumulator helpers: real or complex times a real block entry.
+template <typename T> __device__ __forceinline__ void fma_r(T& acc, T h, T x) { acc = fma(h, x, acc); }
+template <typename T, typename C> __device__ __forceinline__ void fma_c(C& acc, T h, C x) {
+  acc.x = fma(h, x.x, acc.x);
+  acc.y = fma(h, x.y, acc.y);
+}
+
+template <typename T, int NORB, bool CPLX, bool SO, bool MATFREE>
+__global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
+  using V = typename VecT<T, CPLX>::t;
+  constexpr int NS = SO ? 2 : 1;
+  const Geo& g = a.g;
+  const int b = blockIdx.y;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= g.ncells) return;
+  const int N = g.natoms;
+  const int atom = b * g.ncells + cell;
+  const int ix = cell % g.nx, iy = (cell / g.nx) % g.ny, iz = cell / (g.nx * g.ny);
+  const V* __restrict__ x = static_cast<const V*>(a.x) + (size_t)blockIdx.z * a.nrows;
+  V* __restrict__ y = static_cast<V*>(a.y) + (size_t)blockIdx.z * a.nrows;
+  const int sp = a.species[atom];
+  const size_t nslots = 16 * (size_t)g.ncells;
+
+  V acc[NS][NORB];
+  {
+    const T u = (T)(a.U[atom] - a.sigma);
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int o = 0; o < NORB; ++o) {
+        const T d = (T)a.onsite[sp * NORB + o] + u;
+        const V xv = x[(size_t)(s * NORB + o) * N + atom];
+        if constexpr (CPLX) {
+          acc[s][o].x = d * xv.x;
+          acc[s][o].y = d * xv.y;
+        } else {
+          acc[s][o] = d * xv;
+        }
+      }
+    if constexpr (SO) {
+      // lambda L.sigma on (px,py,pz) = orbitals 1..3, basis (spin, orbital), spin up first
+      const T lam = (T)a.lambda[sp];
+      V xu[3], xd[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        xu[i] = x[(size_t)(1 + i) * N + atom];
+        xd[i] = x[(size_t)(NORB + 1 + i) * N + atom];
+      }
+      // i*z = (-z.y, z.x)
+      // up x: -i xu_y + xd_z ; up y: i xu_x - i xd_z ; up z: i xd_y - xd_x
+      // dn x: i xd_y - xu_z ; dn y: -i xd_x - i xu_z ; dn z: i xu_y + xu_x
+      acc[0][1].x += lam * (xu[1].y + xd[2].x);
+      acc[0][1].y += lam * (-xu[1].x + xd[2].y);
+      acc[0][2].x += lam * (-xu[0].y + xd[2].y);
+      acc[0][2].y += lam * (xu[0].x - xd[2].x);
+      acc[0][3].x += lam * (-xd[1].y - xd[0].x);
+      acc[0][3].y += lam * (xd[1].x - xd[0].y);
+      acc[1][1].x += lam * (-xd[1].y - xu[2].x);
+      acc[1][1].y += lam * (xd[1].x - xu[2].y);
+      acc[1][2].x += lam * (xd[0].y + xu[2].y);
+      acc[1][2].y += lam * (-xd[0].x - xu[2].x);
+      acc[1][3].x += lam * (-xu[1].y + xu[0].x);
+      acc[1][3].y += lam * (xu[1].x + xu[0].y);
+    }
+  }
+
+  const bool is_a = b < 4;
+  const int s = is_a ? b : b - 4;
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    int ox, oy, oz, site2;
+    if (is_a) {
+      ox = a.nt.a_to_b_off[s][k][0]; oy = a.nt.a_to_b_off[s][k][1]; oz = a.nt.a_to_b_off[s][k][2];
+      site2 = a.nt.a_to_b_site[s][k];
+    } else {
+      ox = a.nt.b_to_a_off[s][k][0]; oy = a.nt.b_to_a_off[s][k][1]; oz = a.nt.b_to_a_off[s][k][2];
+      site2 = a.nt.b_to_a_site[s][k];
+    }
+    int cell2, wrap[3];
+    if (!shift_cell(g, ix, iy, iz, ox, oy, oz, cell2, wrap)) continue;
+    const int atom2 = site2 * g.ncells + cell2;
+    // bond slot belongs to the A end
+    const size_t slot = is_a ? (size_t)(k * 4 + s) * g.ncells + cell : (size_t)(k * 4 + site2) * g.ncells + cell2;
+
+    V xn[NS][NORB];
+#pragma unroll
+    for (int q = 0; q < NS; ++q)
+#pragma unroll
+      for (int o = 0; o < NORB; ++o) xn[q][o] = x[(size_t)(q * NORB + o) * N + atom2];
+    if constexpr (CPLX) {
+      if (wrap[0] | wrap[1] | wrap[2]) {
+        typename Cx<T>::t f;
+        f.x = (T)1; f.y = (T)0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (wrap[d]) {
+            typename Cx<T>::t p;
+            p.x = (T)a.phase[d].x;
+            p.y = (T)(wrap[d] > 0 ? a.phase[d].y : -a.phase[d].y);
+            f = cmul<T>(f, p);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NS; ++q)
+#pragma unroll
+          for (int o = 0; o < NORB; ++o) xn[q][o] = cmul<T>(xn[q][o], f);
+      }
+    }
+
+    const T* __restrict__ hb;
+    size_t stride;
+    T scale = (T)1;
+    if constexpr (MATFREE) {
+      const int sa = is_a ? sp : a.species[atom2];
+      const int sb = is_a ? a.species[atom2] : sp;
+      const double e1 = 1.0 + a.strain[slot];
+      scale = (T)(a.eta == 2.0 ? 1.0 / (e1 * e1) : pow(e1, -a.eta));
+      hb = a.b0 + ((size_t)(sa * a.ns + sb) * 4 + k) * (NORB * NORB);
+      stride = 1;
+    } else {
+      hb = a.blk + slot;
+      stride = nslots;
+    }
+
+    if constexpr (MATFREE) {
+      // the (d0/d)^eta factor is applied to the neighbour amplitudes once per bond
+#pragma unroll
+      for (int q = 0; q < NS; ++q)
+#pragma unroll
+        for (int o = 0; o < NORB; ++o) {
+          if constexpr (CPLX) { xn[q][o].x *= scale; xn[q][o].y *= scale; } else { xn[q][o] *= scale; }
+        }
+    }
+    if (is_a) {
+#pragma unroll
+      for (int o1 = 0; o1 < NORB; ++o1)
+#pragma unroll
+        for (int o2 = 0; o2 < NORB; ++o2) {
+          const T h = hb[(size_t)(o1 * NORB + o2) * stride];
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            if constexpr (CPLX) fma_c(acc[q][o1], h, xn[q][o2]); else fma_r(acc[q][o1], h, xn[q][o2]);
+          }
+        }
+    } else {
+#pragma unroll
+      for (int o1 = 0; o1 < NORB; ++o1)
+#pragma unroll
+        for (int o2 = 0; o2 < NORB; ++o2) {
+          const T h = hb[(size_t)(o1 * NORB + o2) * stride];
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            if constexpr (CPLX) fma_c(acc[q][o2], h, xn[q][o1]); else fma_r(acc[q][o2], h, xn[q][o1]);
+          }
+        }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NS; ++q)
+#pragma unroll
+    for (int o = 0; o < NORB; ++o) y[(size_t)(q * NORB + o) * N + atom] = acc[q][o];
+}
+
+size_t vec_elem_bytes(const omen_ham* h, int precision) {
+  const size_t r = (precision == OMEN_F64) ? 8 : 4;
+  return h->is_complex ? 2 * r : r;
+}
+
+template <typename T, int NORB, bool CPLX, bool SO, bool MF>
+static cudaError_t launch_t(const HxArgs<T>& a, int nvec, cudaStream_t st) {
+  dim3 grid((a.g.ncells + 127) / 128, 8, nvec);
+  hx_kernel<T, NORB, CPLX, SO, MF><<<grid, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int NORB>
+static cudaError_t launch_norb(const HxArgs<T>& a, const omen_ham* h, int nvec, cudaStream_t st) {
+  const bool mf = h->matrix_free;
+  if (!h->is_complex) return mf ? launch_t<T, NORB, false, false, true>(a, nvec, st) : launch_t<T, NORB, false, false, false>(a, nvec, st);
+  if (!h->spin_orbit) return mf ? launch_t<T, NORB, true, false, true>(a, nvec, st) : launch_t<T, NORB, true, false, false>(a, nvec, st);
+  return mf ? launch_t<T, NORB, true, true, true>(a, nvec, st) : launch_t<T, NORB, true, true, false>(a, nvec, st);
+}
+
+template <typename T>
+static cudaError_t launch_prec(const omen_ham* h, const T* blk, const T* b0, const void* x, void* y, int nvec,
+                               double sigma, cudaStream_t st) {
+  const omen_lattice* L = h->lat;
+  HxArgs<T> a;
+  a.g = Geo{L->nx, L->ny, L->nz, L->ncells, L->natoms, {L->periodic[0], L->periodic[1], L->periodic[2]}};
+  a.nt = host_neighbour_tables();
+  a.blk = blk;
+  a.b0 = b0;
+  a.strain = L->d_strain;
+  a.species = L->d_species;
+  a.onsite = h->d_onsite;
+  a.U = h->d_U;
+  a.lambda = h->d_lambda;
+  a.x = x;
+  a.y = y;
+  a.nrows = h->nrows;
+  a.sigma = sigma;
+  a.eta = h->eta;
+  for (int d = 0; d < 3; ++d) a.phase[d] = h->phase[d];
+  a.ns = h->nspecies;
+  return h->norb == 10 ? launch_norb<T, 10>(a, h, nvec, st) : launch_norb<T, 5>(a, h, nvec, st);
+}
+
+omen_status launch_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma, int vec_precision) {
+  if (nvec < 1 || nvec > 65535) return set_err(ctx, OMEN_EINVAL, "nvec must be 1..65535");
+  cudaError_t e;
+  if (vec_precision == OMEN_F64) {
+    if (!h->matrix_free && !h->d_blk64) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP64 blocks");
+    e = launch_prec<double>(h, h->d_blk64, h->d_b0_64, x, y, nvec, sigma, ctx->stream);
+  } else {
+    if (!h->matrix_free && !h->d_blk32) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP32 blocks");
+    e = launch_prec<float>(h, h->d_blk32, h->d_b0_32, x, y, nvec, sigma, ctx->stream);
+  }
+  if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "H·X launch failed: %s", cudaGetErrorString(e));
+  return OMEN_OK;
+}
+
+static int native_precision(const omen_ham* h) { return h->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64; }
+
+extern "C" omen_status omen_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma) {
+  if (!ctx || !h || !x || !y) return set_err(ctx, OMEN_EINVAL, "null argument");
+  return launch_hx(ctx, h, x, y, nvec, sigma, native_precision(h));
+}
+
+extern "C" omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* h, const void* xh, void* yh, int nvec, double sigma) {
+  if (!ctx || !h || !xh || !yh) return set_err(ctx, OMEN_EINVAL, "null argument");
+  if (nvec < 1) return set_err(ctx, OMEN_EINVAL, "nvec must be >= 1");
+  const size_t bytes = vec_elem_bytes(h, native_precision(h)) * (size_t)h->nrows * nvec;
+  void *dx = nullptr, *dy = nullptr;
+  if (cudaMallocAsync(&dx, bytes, ctx->stream) != cudaSuccess || cudaMallocAsync(&dy, bytes, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    if (dx) cudaFreeAsync(dx, ctx->stream);
+    return set_err(ctx, OMEN_ENOMEM, "device allocation of %zu bytes failed", bytes);
+  }
+  omen_status st = OMEN_OK;
+  cudaError_t e = cudaMemcpyAsync(dx, xh, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) {
+    st = launch_hx(ctx, h, dx, dy, nvec, sigma, native_precision(h));
+    if (st == OMEN_OK) e = cudaMemcpyAsync(yh, dy, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+  }
+  cudaFreeAsync(dx, ctx->stream);
+  cudaFreeAsync(dy, ctx->stream);
+  cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+  if (st != OMEN_OK) return st;
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return set_err(ctx, OMEN_ECUDA, "host H·X failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  return OMEN_OK;
+}

@@ -1,0 +1,869 @@
+// Thick-restart block Lanczos with full reorthogonalisation, plain and folded spectrum
+// (paper Section III-A item 1: "(block) Lanczos"; Section II-B: the Lanczos iteration is the
+// benchmarked unit).
+//
+// Operator A = H (lowest eigenvalues) or A = (H - sigma)^2 (folded spectrum: eigenvalues of H
+// nearest sigma, taken as Rayleigh quotients <x, H x>).  Each block step:
+//   W = A V_j;  twice: h = V^H W, W -= V h (classical Gram–Schmidt, applied twice);
+//   W = V_{j+1} R by Cholesky QR (twice);  T[:, j] = sum of h, T[j+1, j] = R.
+// When the basis is full, the Rayleigh–Ritz pairs of T are computed on the host in FP64;
+// the wanted Ritz vectors and the residual block are kept (Wu & Simon's thick restart, in
+// block form) and the recurrence continues from them.
+// Krylov vectors are FP64 or FP32 (complex when H is); all coefficients (h, R, T, Ritz
+// values) are accumulated and kept in FP64.  OMEN_F32_REFINE64 finishes with FP64
+// Rayleigh–Ritz steps on span{X, H X - X Lambda}.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "dense_eig.h"
+#include "omen_internal.h"
+#include "vec.cuh"
+
+using cd = std::complex<double>;
+
+static constexpr int kMaxBlockCols = 16;   // columns handled per pass by the small kernels
+static constexpr int kDotThreads = 256;
+
+// ---------------------------------------------------------------------------------------
+// P[chunk][i][j] = sum over rows of the chunk of conj(A_i[r]) * B_j[r]   (FP64 accumulators)
+template <typename T, bool C>
+__global__ void __launch_bounds__(kDotThreads) dots_partial_kernel(const void* Av, long long lda, int na,
+                                                                   const void* Bv, long long ldb, int nb,
+                                                                   long long n, int CH, double2* __restrict__ P) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* Bs = reinterpret_cast<V*>(smem_raw);
+  const V* A = static_cast<const V*>(Av);
+  const V* B = static_cast<const V*>(Bv);
+  const long long r0 = (long long)blockIdx.x * CH;
+  const int len = (int)min((long long)CH, n - r0);
+  for (int j = 0; j < nb; ++j)
+    for (int t = threadIdx.x; t < len; t += blockDim.x) Bs[j * CH + t] = B[j * ldb + r0 + t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < na; i += nw) {
+    double ar[kMaxBlockCols], ai[kMaxBlockCols];
+#pragma unroll
+    for (int j = 0; j < kMaxBlockCols; ++j) { ar[j] = 0.0; ai[j] = 0.0; }
+    const V* Ai = A + i * lda + r0;
+    for (int t = lane; t < len; t += 32) {
+      const V a = Ai[t];
+      const double xr = E::re(a), xi = E::im(a);
+#pragma unroll
+      for (int j = 0; j < kMaxBlockCols; ++j) {
+        if (j < nb) {
+          const V bv = Bs[j * CH + t];
+          const double yr = E::re(bv);
+          ar[j] = fma(xr, yr, ar[j]);
+          if constexpr (C) {
+            const double yi = E::im(bv);
+            ar[j] = fma(xi, yi, ar[j]);
+            ai[j] = fma(xr, yi, ai[j]);
+            ai[j] = fma(-xi, yr, ai[j]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxBlockCols; ++j) {
+      if (j < nb) {
+        double sr = ar[j], si = ai[j];
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) P[((size_t)blockIdx.x * na + i) * nb + j] = make_double2(sr, si);
+      }
+    }
+  }
+}
+
+__global__ void reduce_partial_kernel(const double2* __restrict__ P, int nchunks, int count, double2* __restrict__ out) {
+  const int e = blockIdx.x;
+  double sr = 0.0, si = 0.0;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    const double2 v = P[(size_t)c * count + e];
+    sr += v.x;
+    si += v.y;
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    sr = lane < nw ? red[0][lane] : 0.0;
+    si = lane < nw ? red[1][lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) out[e] = make_double2(sr, si);
+  }
+}
+
+// Y_j[r] = beta * Y_j[r] + alpha * sum_i A_i[r] M[i + j*na]   (M complex FP64, column-major)
+template <typename T, bool C>
+__global__ void combine_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M, int nb,
+                               void* Yv, long long ldy, long long n, double alpha, double beta) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Ms = reinterpret_cast<double2*>(smem_raw);
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Ms[t] = M[t];
+  __syncthreads();
+  const V* A = static_cast<const V*>(Av);
+  V* Y = static_cast<V*>(Yv);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double yr[kMaxBlockCols], yi[kMaxBlockCols];
+#pragma unroll
+    for (int j = 0; j < kMaxBlockCols; ++j) { yr[j] = 0.0; yi[j] = 0.0; }
+    for (int i = 0; i < na; ++i) {
+      const V a = A[i * lda + r];
+      const double xr = E::re(a), xi = E::im(a);
+#pragma unroll
+      for (int j = 0; j < kMaxBlockCols; ++j) {
+        if (j < nb) {
+          const double2 m = Ms[i + j * na];
+          yr[j] = fma(xr, m.x, yr[j]);
+          if constexpr (C) {
+            yr[j] = fma(-xi, m.y, yr[j]);
+            yi[j] = fma(xr, m.y, yi[j]);
+            yi[j] = fma(xi, m.x, yi[j]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxBlockCols; ++j) {
+      if (j < nb) {
+        V& out = Y[j * ldy + r];
+        double orr = alpha * yr[j], oi = alpha * yi[j];
+        if (beta != 0.0) {
+          orr += beta * E::re(out);
+          oi += beta * E::im(out);
+        }
+        out = E::make(orr, oi);
+      }
+    }
+  }
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) keyed by (seed, index): uniform [-1, 1).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+template <typename T, bool C>
+__global__ void random_fill_kernel(void* Xv, long long n, unsigned long long seed) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  V* X = static_cast<V*>(Xv);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long h1 = splitmix64(seed * 0x100000001B3ull + 2 * (unsigned long long)r);
+    const unsigned long long h2 = splitmix64(seed * 0x100000001B3ull + 2 * (unsigned long long)r + 1);
+    const double u1 = (double)(h1 >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    const double u2 = (double)(h2 >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    X[r] = E::make(u1, u2);
+  }
+}
+
+template <typename Tin, typename Tout, bool C>
+__global__ void convert_kernel(const void* Xv, void* Yv, long long n) {
+  using Ei = Elem<Tin, C>;
+  using Eo = Elem<Tout, C>;
+  const typename Ei::V* X = static_cast<const typename Ei::V*>(Xv);
+  typename Eo::V* Y = static_cast<typename Eo::V*>(Yv);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+    Y[r] = Eo::make(Ei::re(X[r]), Ei::im(X[r]));
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side helpers bound to one vector type.
+struct KrylovOps {
+  omen_ctx* ctx;
+  const omen_ham* ham;
+  int prec;            // OMEN_F64 or OMEN_F32 (element precision of these vectors)
+  bool cplx;
+  long long n;         // rows
+  size_t el;           // bytes per element
+  double2* d_partial = nullptr;
+  size_t partial_cap = 0;  // in double2
+  double2* d_small = nullptr;  // reduced results / small matrices
+  size_t small_cap = 0;
+  int sm_count = 148;
+
+  omen_status init() {
+    el = vec_elem_bytes(ham, prec);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+    small_cap = 1 << 18;
+    if (cudaMalloc(&d_small, small_cap * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, OMEN_ENOMEM, "small work buffer");
+    }
+    return OMEN_OK;
+  }
+  void release() {
+    cudaFree(d_partial);
+    cudaFree(d_small);
+  }
+  char* col(void* base, long long j) const { return static_cast<char*>(base) + (size_t)j * n * el; }
+
+  int chunk_rows(int nb) const {
+    // rows per CTA so that nb columns of B fit in ~96 KB of shared memory
+    long long ch = (96 * 1024) / ((long long)nb * el);
+    ch = std::min<long long>(ch, 8192);
+    ch = std::max<long long>(ch, 64);
+    return (int)(ch / 32 * 32);
+  }
+
+  // out (host, na x nb column-major complex) = A^H B   (A: na columns, B: nb columns)
+  omen_status dots(const void* A, int na, const void* B, int nb, std::vector<cd>& out) {
+    out.assign((size_t)na * nb, cd(0));
+    for (int j0 = 0; j0 < nb; j0 += kMaxBlockCols) {
+      const int nbj = std::min(kMaxBlockCols, nb - j0);
+      const int CH = chunk_rows(nbj);
+      const long long nchunks = (n + CH - 1) / CH;
+      const size_t need = (size_t)nchunks * na * nbj;
+      if (need > partial_cap) {
+        cudaFree(d_partial);
+        d_partial = nullptr;
+        partial_cap = 0;
+        if (cudaMalloc(&d_partial, need * sizeof(double2)) != cudaSuccess) {
+          cudaGetLastError();
+          return set_err(ctx, OMEN_ENOMEM, "partial-sum buffer");
+        }
+        partial_cap = need;
+      }
+      if ((size_t)na * nbj > small_cap) return set_err(ctx, OMEN_EINVAL, "projection too large");
+      const size_t shm = (size_t)nbj * CH * el;
+      const void* Bj = col(const_cast<void*>(B), j0);
+#define DOTS_LAUNCH(T, Cc)                                                                          \
+  do {                                                                                              \
+    cudaFuncSetAttribute(dots_partial_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+    dots_partial_kernel<T, Cc><<<(unsigned)nchunks, kDotThreads, shm, ctx->stream>>>(A, n, na, Bj, n, nbj, n, CH, d_partial); \
+  } while (0)
+      if (prec == OMEN_F64) { if (cplx) DOTS_LAUNCH(double, true); else DOTS_LAUNCH(double, false); }
+      else { if (cplx) DOTS_LAUNCH(float, true); else DOTS_LAUNCH(float, false); }
+#undef DOTS_LAUNCH
+      OMEN_CHECK_LAUNCH(ctx);
+      const int count = na * nbj;
+      reduce_partial_kernel<<<count, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, count, d_small);
+      OMEN_CHECK_LAUNCH(ctx);
+      std::vector<cd> tmp(count);
+      OMEN_CUDA(ctx, cudaMemcpyAsync(tmp.data(), d_small, count * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      // partial layout [i][j]
+      for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nbj; ++j) out[i + (size_t)(j0 + j) * na] = tmp[(size_t)i * nbj + j];
+    }
+    for (const cd& v : out)
+      if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+        return set_err(ctx, OMEN_ENUMERIC, "non-finite value in a Krylov inner product");
+    return OMEN_OK;
+  }
+
+  // Y = beta*Y + alpha * A M   (M host na x nb column-major)
+  omen_status combine(const void* A, int na, const std::vector<cd>& M, int nb, void* Y, double alpha, double beta) {
+    if ((size_t)na * kMaxBlockCols > small_cap) return set_err(ctx, OMEN_EINVAL, "combination too large");
+    for (int j0 = 0; j0 < nb; j0 += kMaxBlockCols) {
+      const int nbj = std::min(kMaxBlockCols, nb - j0);
+      std::vector<cd> Mj((size_t)na * nbj);
+      for (int j = 0; j < nbj; ++j)
+        for (int i = 0; i < na; ++i) Mj[i + (size_t)j * na] = M[i + (size_t)(j0 + j) * na];
+      OMEN_CUDA(ctx, cudaMemcpyAsync(d_small, Mj.data(), Mj.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+      const size_t shm = Mj.size() * sizeof(double2);
+      const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+      void* Yj = col(Y, j0);
+#define COMB_LAUNCH(T, Cc)                                                                           \
+  do {                                                                                               \
+    cudaFuncSetAttribute(combine_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+    combine_kernel<T, Cc><<<grid, 256, shm, ctx->stream>>>(A, n, na, d_small, nbj, Yj, n, n, alpha, beta); \
+  } while (0)
+      if (prec == OMEN_F64) { if (cplx) COMB_LAUNCH(double, true); else COMB_LAUNCH(double, false); }
+      else { if (cplx) COMB_LAUNCH(float, true); else COMB_LAUNCH(float, false); }
+#undef COMB_LAUNCH
+      OMEN_CHECK_LAUNCH(ctx);
+      // the small buffer is reused by the next chunk: wait for this kernel to read it
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    return OMEN_OK;
+  }
+
+  omen_status random_fill(void* X, int ncols, unsigned long long seed) {
+    const long long total = n * ncols;
+    const unsigned grid = (unsigned)std::min<long long>((total + 255) / 256, (long long)sm_count * 8);
+    if (prec == OMEN_F64) {
+      if (cplx) random_fill_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(X, total, seed);
+      else random_fill_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(X, total, seed);
+    } else {
+      if (cplx) random_fill_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(X, total, seed);
+      else random_fill_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(X, total, seed);
+    }
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+
+  // operator: W = A X, A = H (folded = false) or (H - sigma)^2
+  omen_status apply(const void* X, void* W, void* tmp, int nb, bool folded, double sigma, long long& count) {
+    if (!folded) {
+      count += nb;
+      return launch_hx(ctx, ham, X, W, nb, 0.0, prec);
+    }
+    omen_status s = launch_hx(ctx, ham, X, tmp, nb, sigma, prec);
+    if (s != OMEN_OK) return s;
+    count += 2 * nb;
+    return launch_hx(ctx, ham, tmp, W, nb, sigma, prec);
+  }
+
+  // Orthonormalise the nb columns of W in place (Cholesky QR, twice): W_in = W_out R.
+  // Returns 1 in `deficient` if the block is numerically rank deficient.
+  omen_status cholqr(void* W, int nb, std::vector<cd>& R, int& deficient) {
+    R.assign((size_t)nb * nb, cd(0));
+    for (int i = 0; i < nb; ++i) R[i + (size_t)i * nb] = 1.0;
+    deficient = 0;
+    std::vector<cd> G, Rk((size_t)nb * nb), Ri((size_t)nb * nb);
+    for (int pass = 0; pass < 2; ++pass) {
+      omen_status s = dots(W, nb, W, nb, G);
+      if (s != OMEN_OK) return s;
+      // Hermitian part
+      for (int j = 0; j < nb; ++j)
+        for (int i = 0; i < nb; ++i)
+          if (i > j) {
+            cd a = 0.5 * (G[i + (size_t)j * nb] + std::conj(G[j + (size_t)i * nb]));
+            G[i + (size_t)j * nb] = a;
+            G[j + (size_t)i * nb] = std::conj(a);
+          }
+      double gmax = 0;
+      for (int i = 0; i < nb; ++i) gmax = std::max(gmax, std::real(G[i + (size_t)i * nb]));
+      for (int i = 0; i < nb; ++i)
+        if (std::real(G[i + (size_t)i * nb]) <= 1e-28 * std::max(gmax, 1e-300) || gmax == 0.0) { deficient = 1; return OMEN_OK; }
+      if (cholesky_upper(nb, G.data(), Rk.data())) { deficient = 1; return OMEN_OK; }
+      // ill-conditioned after the first pass means the block lost rank
+      if (pass == 1) {
+        double dmin = 1e300, dmax = 0;
+        for (int i = 0; i < nb; ++i) {
+          dmin = std::min(dmin, std::abs(Rk[i + (size_t)i * nb]));
+          dmax = std::max(dmax, std::abs(Rk[i + (size_t)i * nb]));
+        }
+        if (dmin < 1e-6 * dmax) { deficient = 1; return OMEN_OK; }
+      }
+      upper_inverse(nb, Rk.data(), Ri.data());
+      // W <- W Ri : combine into W itself is not allowed (aliasing) -> use R^-1 on a copy
+      void* tmpW = nullptr;
+      if (cudaMallocAsync(&tmpW, (size_t)nb * n * el, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, OMEN_ENOMEM, "QR work vectors");
+      }
+      OMEN_CUDA(ctx, cudaMemcpyAsync(tmpW, W, (size_t)nb * n * el, cudaMemcpyDeviceToDevice, ctx->stream));
+      omen_status s2 = combine(tmpW, nb, Ri, nb, W, 1.0, 0.0);
+      cudaFreeAsync(tmpW, ctx->stream);
+      if (s2 != OMEN_OK) return s2;
+      // R <- Rk R
+      std::vector<cd> Rn((size_t)nb * nb, cd(0));
+      for (int j = 0; j < nb; ++j)
+        for (int i = 0; i < nb; ++i) {
+          cd s3 = 0;
+          for (int k = 0; k < nb; ++k) s3 += Rk[i + (size_t)k * nb] * R[k + (size_t)j * nb];
+          Rn[i + (size_t)j * nb] = s3;
+        }
+      R = Rn;
+    }
+    return OMEN_OK;
+  }
+
+  // Orthogonalise W (nb cols) against the first nv columns of V (twice); adds the
+  // coefficients into hsum (nv x nb).
+  omen_status orthogonalise(const void* V, int nv, void* W, int nb, std::vector<cd>* hsum) {
+    if (hsum) hsum->assign((size_t)nv * nb, cd(0));
+    if (nv == 0) return OMEN_OK;
+    std::vector<cd> h;
+    for (int pass = 0; pass < 2; ++pass) {
+      omen_status s = dots(V, nv, W, nb, h);
+      if (s != OMEN_OK) return s;
+      s = combine(V, nv, h, nb, W, -1.0, 1.0);
+      if (s != OMEN_OK) return s;
+      if (hsum)
+        for (size_t t = 0; t < h.size(); ++t) (*hsum)[t] += h[t];
+    }
+    return OMEN_OK;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+struct RitzResult {
+  std::vector<double> lam;   // eigenvalues of H (ascending)
+  std::vector<double> res;   // FP64 ||H x - lam x||
+  std::vector<double> bound; // min(res, res^2/gap)
+};
+
+// Error bound per pair from residuals and the spread of the computed values: Weyl (r) or
+// Kato–Temple (r^2 / gap) with the gap to the nearest value outside the pair's cluster.
+static void error_bounds(const std::vector<double>& lam_all, const std::vector<double>& lam,
+                         const std::vector<double>& res, std::vector<double>& bound) {
+  bound.resize(lam.size());
+  for (size_t i = 0; i < lam.size(); ++i) {
+    const double clus = 1e-7 * std::max(1.0, std::fabs(lam[i]));
+    double gap = 1e300;
+    for (double v : lam_all) {
+      const double d = std::fabs(v - lam[i]);
+      if (d > clus) gap = std::min(gap, d);
+    }
+    const double r = res[i];
+    bound[i] = (gap < 1e299) ? std::min(r, r * r / gap) : r;
+  }
+}
+
+// Rayleigh quotients and FP64-accumulated residual norms of the k columns of X (H X in HX).
+static omen_status rayleigh_residuals(KrylovOps& op, void* X, void* HX, void* R, int k, std::vector<double>& lam,
+                                      std::vector<double>& res) {
+  lam.assign(k, 0.0);
+  res.assign(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    std::vector<cd> xx, xhx;
+    omen_status s = op.dots(op.col(X, j), 1, op.col(X, j), 1, xx);
+    if (s != OMEN_OK) return s;
+    s = op.dots(op.col(X, j), 1, op.col(HX, j), 1, xhx);
+    if (s != OMEN_OK) return s;
+    lam[j] = std::real(xhx[0]) / std::real(xx[0]);
+    OMEN_CUDA(op.ctx, cudaMemcpyAsync(op.col(R, j), op.col(HX, j), op.n * op.el, cudaMemcpyDeviceToDevice, op.ctx->stream));
+    std::vector<cd> m(1, cd(lam[j]));
+    s = op.combine(op.col(X, j), 1, m, 1, op.col(R, j), -1.0, 1.0);
+    if (s != OMEN_OK) return s;
+    std::vector<cd> rr;
+    s = op.dots(op.col(R, j), 1, op.col(R, j), 1, rr);
+    if (s != OMEN_OK) return s;
+    res[j] = std::sqrt(std::max(0.0, std::real(rr[0])) / std::real(xx[0]));
+  }
+  return OMEN_OK;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+// Solve in the vector precision of `op`; on return X holds k Ritz vectors (columns) with
+// their eigenvalues in rr.lam, sorted ascending.
+static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X, int k_out, RitzResult& rr,
+                                 omen_eig_info* info, const void* v0_host, bool& converged) {
+  omen_ctx* ctx = op.ctx;
+  const int b = o->block;
+  const int m = o->basis;
+  const bool folded = (o->which == OMEN_NEAREST);
+  const long long n = op.n;
+  DevBuf Vb, Wb, Tb, Xb;
+  const size_t vbytes = (size_t)n * op.el;
+  if (cudaMalloc(&Vb.p, (size_t)(m + b) * vbytes) != cudaSuccess || cudaMalloc(&Wb.p, (size_t)b * vbytes) != cudaSuccess ||
+      cudaMalloc(&Tb.p, (size_t)std::max(b, k_out) * vbytes) != cudaSuccess ||
+      cudaMalloc(&Xb.p, (size_t)m * vbytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, OMEN_ENOMEM, "Lanczos basis (%d vectors of %lld rows)", m + b, n);
+  }
+  void* V = Vb.p;
+  void* W = Wb.p;
+  void* tmp = Tb.p;
+  // start block
+  if (v0_host) {
+    OMEN_CUDA(ctx, cudaMemcpyAsync(V, v0_host, (size_t)b * vbytes, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    omen_status s = op.random_fill(V, b, 0x5EEDull);
+    if (s != OMEN_OK) return s;
+  }
+  std::vector<cd> R;
+  int deficient = 0;
+  omen_status s = op.cholqr(V, b, R, deficient);
+  if (s != OMEN_OK) return s;
+  if (deficient) return set_err(ctx, OMEN_EINVAL, "start block is rank deficient");
+
+  const int ldT = m + b;
+  std::vector<cd> T((size_t)ldT * ldT, cd(0));
+  auto Tat = [&](int i, int j) -> cd& { return T[i + (size_t)j * ldT]; };
+  int jstart = 0, nbas = b;   // current block = V[jstart, jstart+b), basis = V[0, nbas)
+  long long hx = 0;
+  int iter = 0, restarts = 0;
+  const int max_iter = o->max_iter;
+  double gateA = -1.0;
+  converged = false;
+  std::vector<double> theta;
+  std::vector<cd> Y;
+  std::vector<cd> Rlast;
+  unsigned long long reseed = 1;
+  auto t_start = std::chrono::steady_clock::now();
+
+  while (true) {
+    // expand
+    s = op.apply(op.col(V, jstart), W, tmp, b, folded, o->sigma, hx);
+    if (s != OMEN_OK) return s;
+    std::vector<cd> hsum;
+    s = op.orthogonalise(V, nbas, W, b, &hsum);
+    if (s != OMEN_OK) return s;
+    for (int j = 0; j < b; ++j)
+      for (int i = 0; i < nbas; ++i) {
+        const cd v = hsum[i + (size_t)j * nbas];
+        Tat(i, jstart + j) = v;
+        Tat(jstart + j, i) = std::conj(v);
+      }
+    for (int j = 0; j < b; ++j)
+      for (int i = 0; i < b; ++i) {  // Hermitian average of the diagonal block
+        const cd a = 0.5 * (Tat(jstart + i, jstart + j) + std::conj(Tat(jstart + j, jstart + i)));
+        Tat(jstart + i, jstart + j) = a;
+        Tat(jstart + j, jstart + i) = std::conj(a);
+      }
+    s = op.cholqr(W, b, R, deficient);
+    if (s != OMEN_OK) return s;
+    if (deficient) {
+      // invariant subspace found: continue with fresh directions, no coupling
+      s = op.random_fill(W, b, 0xABCD0000ull + reseed++);
+      if (s != OMEN_OK) return s;
+      s = op.orthogonalise(V, nbas, W, b, nullptr);
+      if (s != OMEN_OK) return s;
+      s = op.orthogonalise(V, nbas, W, b, nullptr);
+      if (s != OMEN_OK) return s;
+      std::vector<cd> Rd;
+      s = op.cholqr(W, b, Rd, deficient);
+      if (s != OMEN_OK) return s;
+      if (deficient) return set_err(ctx, OMEN_ENUMERIC, "could not extend the Krylov basis");
+      R.assign((size_t)b * b, cd(0));
+    }
+    OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(V, nbas), W, (size_t)b * vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int j = 0; j < b; ++j)
+      for (int i = 0; i < b; ++i) {
+        Tat(nbas + i, jstart + j) = R[i + (size_t)j * b];
+        Tat(jstart + j, nbas + i) = std::conj(R[i + (size_t)j * b]);
+      }
+    Rlast = R;
+    ++iter;
+    const bool full = nbas + b > m;
+    const bool check = full || iter >= max_iter || (iter % std::max(1, 8 / b) == 0 && nbas >= o->nev + b);
+    if (check && nbas >= o->nev) {
+      // Rayleigh–Ritz on T[0:nbas, 0:nbas]
+      std::vector<cd> Tn((size_t)nbas * nbas);
+      for (int j = 0; j < nbas; ++j)
+        for (int i = 0; i < nbas; ++i) Tn[i + (size_t)j * nbas] = Tat(i, j);
+      theta.assign(nbas, 0.0);
+      Y.assign((size_t)nbas * nbas, cd(0));
+      if (hermitian_eig(nbas, Tn.data(), theta.data(), Y.data()))
+        return set_err(ctx, OMEN_ENUMERIC, "projected eigenproblem did not converge");
+      std::vector<double> resA(nbas);
+      for (int i = 0; i < nbas; ++i) {
+        double acc = 0;
+        for (int r = 0; r < b; ++r) {
+          cd v = 0;
+          for (int c = 0; c < b; ++c) v += Rlast[r + (size_t)c * b] * Y[(jstart + c) + (size_t)i * nbas];
+          acc += std::norm(v);
+        }
+        resA[i] = std::sqrt(acc);
+      }
+      const int nev = o->nev;
+      bool done = false;
+      if (!folded) {
+        std::vector<double> lam(theta.begin(), theta.begin() + nev), res(resA.begin(), resA.begin() + nev), bd;
+        error_bounds(theta, lam, res, bd);
+        done = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+      } else {
+        double rmax = *std::max_element(resA.begin(), resA.begin() + nev);
+        if (gateA < 0) gateA = std::max(o->tol, 1e-12) * 1e3;
+        if (rmax <= gateA || iter >= max_iter) {
+          // explicit check on H for the nev (+ b) Ritz vectors of smallest theta
+          const int kc = std::min(nbas, nev + b);
+          std::vector<cd> Yk((size_t)nbas * kc);
+          for (int j = 0; j < kc; ++j)
+            for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
+          s = op.combine(V, nbas, Yk, kc, Xb.p, 1.0, 0.0);
+          if (s != OMEN_OK) return s;
+          DevBuf HXb, Rb;
+          if (cudaMalloc(&HXb.p, (size_t)kc * vbytes) != cudaSuccess || cudaMalloc(&Rb.p, (size_t)kc * vbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, OMEN_ENOMEM, "Ritz check vectors");
+          }
+          s = launch_hx(ctx, op.ham, Xb.p, HXb.p, kc, 0.0, op.prec);
+          if (s != OMEN_OK) return s;
+          hx += kc;
+          std::vector<double> lamk, resk, bd;
+          s = rayleigh_residuals(op, Xb.p, HXb.p, Rb.p, kc, lamk, resk);
+          if (s != OMEN_OK) return s;
+          std::vector<double> lam(lamk.begin(), lamk.begin() + nev), res(resk.begin(), resk.begin() + nev);
+          error_bounds(lamk, lam, res, bd);
+          done = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+          if (!done) gateA = std::min(gateA, rmax) * 0.01;
+        }
+      }
+      if (done || iter >= max_iter) {
+        converged = done;
+        break;
+      }
+      if (full) {
+        // thick restart: keep kk Ritz vectors of smallest theta and the residual block
+        const int kk = std::min(m - b, std::max(o->nev + b, (nbas / 2 / b) * b));
+        std::vector<cd> Yk((size_t)nbas * kk);
+        for (int j = 0; j < kk; ++j)
+          for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
+        s = op.combine(V, nbas, Yk, kk, Xb.p, 1.0, 0.0);
+        if (s != OMEN_OK) return s;
+        OMEN_CUDA(ctx, cudaMemcpyAsync(V, Xb.p, (size_t)kk * vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(V, kk), op.col(V, nbas), (size_t)b * vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        std::fill(T.begin(), T.end(), cd(0));
+        for (int i = 0; i < kk; ++i) Tat(i, i) = theta[i];
+        for (int i = 0; i < kk; ++i)
+          for (int r = 0; r < b; ++r) {
+            cd v = 0;
+            for (int c = 0; c < b; ++c) v += Rlast[r + (size_t)c * b] * Y[(jstart + c) + (size_t)i * nbas];
+            Tat(kk + r, i) = v;
+            Tat(i, kk + r) = std::conj(v);
+          }
+        jstart = kk;
+        nbas = kk + b;
+        ++restarts;
+        continue;
+      }
+    }
+    jstart = nbas;
+    nbas += b;
+  }
+
+  // outputs: k_out Ritz vectors of smallest theta, eigenvalues of H from Rayleigh quotients
+  const int kc = std::min(nbas, k_out);
+  std::vector<cd> Yk((size_t)nbas * kc);
+  for (int j = 0; j < kc; ++j)
+    for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
+  s = op.combine(V, nbas, Yk, kc, X, 1.0, 0.0);
+  if (s != OMEN_OK) return s;
+  if (info) {
+    info->iterations = iter;
+    info->hx_count = hx;
+    info->restarts = restarts;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  (void)rr;
+  return OMEN_OK;
+}
+
+// Sort the k columns of X (and HX) by the key and permute lam/res accordingly.
+static omen_status sort_columns(KrylovOps& op, void* X, int k, std::vector<double>& key, std::vector<double>* a1,
+                                std::vector<double>* a2) {
+  std::vector<int> ord(k);
+  for (int i = 0; i < k; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return key[x] < key[y]; });
+  bool ident = true;
+  for (int i = 0; i < k; ++i) ident &= ord[i] == i;
+  if (ident) return OMEN_OK;
+  DevBuf tb;
+  if (cudaMalloc(&tb.p, (size_t)k * op.n * op.el) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(op.ctx, OMEN_ENOMEM, "sort buffer");
+  }
+  for (int i = 0; i < k; ++i)
+    OMEN_CUDA(op.ctx, cudaMemcpyAsync(op.col(tb.p, i), op.col(X, ord[i]), op.n * op.el, cudaMemcpyDeviceToDevice, op.ctx->stream));
+  OMEN_CUDA(op.ctx, cudaMemcpyAsync(X, tb.p, (size_t)k * op.n * op.el, cudaMemcpyDeviceToDevice, op.ctx->stream));
+  OMEN_CUDA(op.ctx, cudaStreamSynchronize(op.ctx->stream));
+  auto perm = [&](std::vector<double>& v) {
+    std::vector<double> t(k);
+    for (int i = 0; i < k; ++i) t[i] = v[ord[i]];
+    v = t;
+  };
+  perm(key);
+  if (a1) perm(*a1);
+  if (a2) perm(*a2);
+  return OMEN_OK;
+}
+
+// FP64 Rayleigh–Ritz refinement on span{X, H X - X Lambda}: X (k columns, FP64) in/out.
+static omen_status refine64(KrylovOps& op, void* X, int k, const omen_eig_opts* o, std::vector<double>& lam,
+                            std::vector<double>& res, std::vector<double>& bound, long long& hx) {
+  omen_ctx* ctx = op.ctx;
+  const size_t vb = (size_t)op.n * op.el;
+  DevBuf Sb, HSb, Rb;
+  if (cudaMalloc(&Sb.p, 2 * k * vb) != cudaSuccess || cudaMalloc(&HSb.p, 2 * k * vb) != cudaSuccess ||
+      cudaMalloc(&Rb.p, (size_t)k * vb) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, OMEN_ENOMEM, "refinement vectors");
+  }
+  const bool nearest = o->which == OMEN_NEAREST;
+  omen_status s;
+  for (int it = 0; it < 6; ++it) {
+    // S = [X, R], R = H X - X Lambda
+    OMEN_CUDA(ctx, cudaMemcpyAsync(Sb.p, X, k * vb, cudaMemcpyDeviceToDevice, ctx->stream));
+    std::vector<cd> Rq;
+    int def = 0;
+    s = op.cholqr(Sb.p, k, Rq, def);
+    if (s != OMEN_OK) return s;
+    if (def) return set_err(ctx, OMEN_ENUMERIC, "refinement basis lost rank");
+    s = launch_hx(ctx, op.ham, Sb.p, HSb.p, k, 0.0, OMEN_F64);
+    if (s != OMEN_OK) return s;
+    hx += k;
+    s = rayleigh_residuals(op, Sb.p, HSb.p, Rb.p, k, lam, res);
+    if (s != OMEN_OK) return s;
+    error_bounds(lam, lam, res, bound);
+    const double bmax = *std::max_element(bound.begin(), bound.end());
+    if (it > 0 && bmax <= o->tol) {
+      OMEN_CUDA(ctx, cudaMemcpyAsync(X, Sb.p, k * vb, cudaMemcpyDeviceToDevice, ctx->stream));
+      return OMEN_OK;
+    }
+    // append the residuals, orthogonalise them against X and each other
+    OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(Sb.p, k), Rb.p, k * vb, cudaMemcpyDeviceToDevice, ctx->stream));
+    s = op.orthogonalise(Sb.p, k, op.col(Sb.p, k), k, nullptr);
+    if (s != OMEN_OK) return s;
+    std::vector<cd> R2;
+    s = op.cholqr(op.col(Sb.p, k), k, R2, def);
+    if (s != OMEN_OK) return s;
+    const int ns = def ? k : 2 * k;
+    s = launch_hx(ctx, op.ham, Sb.p, HSb.p, ns, 0.0, OMEN_F64);
+    if (s != OMEN_OK) return s;
+    hx += ns;
+    std::vector<cd> G;
+    s = op.dots(Sb.p, ns, HSb.p, ns, G);
+    if (s != OMEN_OK) return s;
+    for (int j = 0; j < ns; ++j)
+      for (int i = 0; i < j; ++i) {
+        cd a = 0.5 * (G[i + (size_t)j * ns] + std::conj(G[j + (size_t)i * ns]));
+        G[i + (size_t)j * ns] = a;
+        G[j + (size_t)i * ns] = std::conj(a);
+      }
+    for (int i = 0; i < ns; ++i) G[i + (size_t)i * ns] = std::real(G[i + (size_t)i * ns]);
+    std::vector<double> w(ns);
+    std::vector<cd> Z((size_t)ns * ns);
+    if (hermitian_eig(ns, G.data(), w.data(), Z.data())) return set_err(ctx, OMEN_ENUMERIC, "refinement eigenproblem");
+    // choose k Ritz values: lowest, or nearest sigma
+    std::vector<int> ord(ns);
+    for (int i = 0; i < ns; ++i) ord[i] = i;
+    if (nearest)
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b2) { return std::fabs(w[a] - o->sigma) < std::fabs(w[b2] - o->sigma); });
+    std::vector<cd> Zk((size_t)ns * k);
+    std::vector<int> pick(ord.begin(), ord.begin() + k);
+    std::sort(pick.begin(), pick.end(), [&](int a, int b2) { return w[a] < w[b2]; });
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < ns; ++i) Zk[i + (size_t)j * ns] = Z[i + (size_t)pick[j] * ns];
+    s = op.combine(Sb.p, ns, Zk, k, X, 1.0, 0.0);
+    if (s != OMEN_OK) return s;
+  }
+  // final evaluation
+  s = launch_hx(ctx, op.ham, X, HSb.p, k, 0.0, OMEN_F64);
+  if (s != OMEN_OK) return s;
+  hx += k;
+  s = rayleigh_residuals(op, X, HSb.p, Rb.p, k, lam, res);
+  if (s != OMEN_OK) return s;
+  error_bounds(lam, lam, res, bound);
+  return OMEN_OK;
+}
+
+extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_eig_opts* o, double* evals_host,
+                                 void* evecs_dev, omen_eig_info* info) {
+  if (!ctx || !ham || !o || !evals_host) return set_err(ctx, OMEN_EINVAL, "null argument");
+  const int b = o->block;
+  if (o->nev < 1) return set_err(ctx, OMEN_EINVAL, "nev must be >= 1");
+  if (b < 1 || b > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "block must be 1..%d", kMaxBlockCols);
+  if (o->basis % b != 0 || o->basis < o->nev + 2 * b) return set_err(ctx, OMEN_EINVAL, "basis must be a multiple of block and >= nev + 2*block");
+  if (o->basis > 2048) return set_err(ctx, OMEN_EINVAL, "basis must be <= 2048");
+  if (o->which != OMEN_LOWEST && o->which != OMEN_NEAREST) return set_err(ctx, OMEN_EINVAL, "which must be LOWEST or NEAREST");
+  if (!(o->tol > 0)) return set_err(ctx, OMEN_EINVAL, "tol must be > 0");
+  if (o->max_iter < 1 || (long long)o->max_iter * b < o->nev)
+    return set_err(ctx, OMEN_EINVAL, "max_iter * block must be >= nev");
+  if ((long long)o->basis + b > ham->nrows) return set_err(ctx, OMEN_EINVAL, "basis larger than the problem");
+  OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
+  auto t0 = std::chrono::steady_clock::now();
+  omen_eig_info local{};
+  omen_eig_info* inf = info ? info : &local;
+  std::memset(inf, 0, sizeof(*inf));
+
+  const int solve_prec = (ham->precision == OMEN_F64) ? OMEN_F64 : OMEN_F32;
+  KrylovOps op{ctx, ham, solve_prec, (bool)ham->is_complex, ham->nrows};
+  omen_status s = op.init();
+  if (s != OMEN_OK) return s;
+  const int kout = std::min<long long>(o->nev + b, o->basis);
+  DevBuf Xb;
+  if (cudaMalloc(&Xb.p, (size_t)kout * ham->nrows * op.el) != cudaSuccess) {
+    cudaGetLastError();
+    op.release();
+    return set_err(ctx, OMEN_ENOMEM, "Ritz vectors");
+  }
+  RitzResult rr;
+  bool conv = false;
+  s = lanczos_solve(op, o, Xb.p, kout, rr, inf, o->v0_host, conv);
+  if (s != OMEN_OK) { op.release(); return s; }
+  // evaluate the kout Ritz vectors in the solve precision
+  DevBuf HXb, Rb;
+  if (cudaMalloc(&HXb.p, (size_t)kout * ham->nrows * op.el) != cudaSuccess ||
+      cudaMalloc(&Rb.p, (size_t)kout * ham->nrows * op.el) != cudaSuccess) {
+    cudaGetLastError();
+    op.release();
+    return set_err(ctx, OMEN_ENOMEM, "Ritz evaluation");
+  }
+  s = launch_hx(ctx, ham, Xb.p, HXb.p, kout, 0.0, solve_prec);
+  if (s == OMEN_OK) s = rayleigh_residuals(op, Xb.p, HXb.p, Rb.p, kout, rr.lam, rr.res);
+  if (s != OMEN_OK) { op.release(); return s; }
+  inf->hx_count += kout;
+  // the nev wanted among the kout: lowest, or nearest sigma (Ritz vectors are ordered by
+  // theta of A, which for the folded operator is (lambda - sigma)^2)
+  std::vector<double> key(kout);
+  for (int i = 0; i < kout; ++i) key[i] = (o->which == OMEN_NEAREST) ? std::fabs(rr.lam[i] - o->sigma) : rr.lam[i];
+  s = sort_columns(op, Xb.p, kout, key, &rr.lam, &rr.res);
+  if (s != OMEN_OK) { op.release(); return s; }
+  error_bounds(rr.lam, rr.lam, rr.res, rr.bound);
+  const int nev = o->nev;
+  std::vector<double> lam(rr.lam.begin(), rr.lam.begin() + nev), res(rr.res.begin(), rr.res.begin() + nev);
+  std::vector<double> bound(rr.bound.begin(), rr.bound.begin() + nev);
+  inf->max_residual_raw = *std::max_element(res.begin(), res.end());
+  void* Xfinal = Xb.p;
+  DevBuf X64;
+  if (ham->precision == OMEN_F32_REFINE64) {
+    KrylovOps op64{ctx, ham, OMEN_F64, (bool)ham->is_complex, ham->nrows};
+    s = op64.init();
+    if (s != OMEN_OK) { op.release(); return s; }
+    if (cudaMalloc(&X64.p, (size_t)nev * ham->nrows * op64.el) != cudaSuccess) {
+      cudaGetLastError();
+      op.release();
+      op64.release();
+      return set_err(ctx, OMEN_ENOMEM, "refinement vectors");
+    }
+    const long long tot = (long long)nev * ham->nrows;
+    const unsigned grid = (unsigned)std::min<long long>((tot + 255) / 256, 152 * 8);
+    if (ham->is_complex) convert_kernel<float, double, true><<<grid, 256, 0, ctx->stream>>>(Xb.p, X64.p, tot);
+    else convert_kernel<float, double, false><<<grid, 256, 0, ctx->stream>>>(Xb.p, X64.p, tot);
+    long long hx = 0;
+    s = refine64(op64, X64.p, nev, o, lam, res, bound, hx);
+    inf->hx_count += hx;
+    if (s == OMEN_OK) {
+      std::vector<double> key2 = lam;
+      s = sort_columns(op64, X64.p, nev, key2, &res, &bound);
+      lam = key2;
+    }
+    op64.release();
+    if (s != OMEN_OK) { op.release(); return s; }
+    Xfinal = X64.p;
+  } else {
+    std::vector<double> key2 = lam;
+    s = sort_columns(op, Xb.p, nev, key2, &res, &bound);
+    lam = key2;
+    if (s != OMEN_OK) { op.release(); return s; }
+  }
+  for (int i = 0; i < nev; ++i) evals_host[i] = lam[i];
+  inf->max_residual = *std::max_element(res.begin(), res.end());
+  inf->max_error_bound = *std::max_element(bound.begin(), bound.end());
+  inf->converged = conv && inf->max_error_bound <= o->tol;
+  if (evecs_dev) {
+    const size_t eb = (ham->precision == OMEN_F32_REFINE64) ? vec_elem_bytes(ham, OMEN_F64) : op.el;
+    s = OMEN_OK;
+    cudaError_t e = cudaMemcpyAsync(evecs_dev, Xfinal, (size_t)nev * ham->nrows * eb, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) s = set_err(ctx, OMEN_ECUDA, "copy of eigenvectors: %s", cudaGetErrorString(e));
+  }
+  cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+  op.release();
+  if (s != OMEN_OK) return s;
+  if (e2 != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "eigensolve: %s", cudaGetErrorString(e2));
+  inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (!inf->converged) return set_err(ctx, OMEN_ENOCONV, "not converged: error bound %.3e > tol %.3e after %d block steps",
+                                      inf->max_error_bound, o->tol, inf->iterations);
+  return OMEN_OK;
+}

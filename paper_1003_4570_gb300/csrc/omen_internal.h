@@ -1,0 +1,83 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/omen.h"
+
+struct omen_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  long long wait_limit = 0;
+  // small device work area: reduction partials and a status word
+  double* d_work = nullptr;
+  size_t work_bytes = 0;
+  int* d_status = nullptr;
+};
+
+struct omen_lattice {
+  int nx, ny, nz, ncells, natoms;
+  int periodic[3];
+  double a_nm;
+  uint8_t* d_species = nullptr;  // [natoms]
+  double* d_strain = nullptr;    // [16*ncells]
+  long long nbonds = 0;
+};
+
+// Per-species-pair bond blocks for the four ideal directions, at d0 (device, row-major).
+struct omen_ham {
+  const omen_lattice* lat = nullptr;
+  int norb = 0, nspin = 1, nb = 0;        // nb = norb * nspin
+  int spin_orbit = 0, precision = OMEN_F64, matrix_free = 0, bloch = 0, is_complex = 0;
+  int nspecies = 1;
+  long long nrows = 0;
+  double eta = 2.0;
+  double kvec[3] = {0, 0, 0};
+  double2 phase[3];                       // exp(i k.L_d e_d) for a +1 supercell wrap along d
+  // stored bond blocks, entry-major: blk[e * nslots + slot], e = o1*norb + o2 (A rows, B cols)
+  double* d_blk64 = nullptr;
+  float* d_blk32 = nullptr;
+  // matrix-free table: B0[((sa*ns + sb)*4 + k)*norb*norb + e]
+  double* d_b0_64 = nullptr;
+  float* d_b0_32 = nullptr;
+  // onsite energies per species and orbital [ns][norb], potential per atom
+  double* d_onsite = nullptr;
+  double* d_U = nullptr;                  // [natoms]
+  double lambda_so[4] = {0, 0, 0, 0};
+  double* d_lambda = nullptr;             // [ns]
+};
+
+// status / error helpers ---------------------------------------------------------------------
+omen_status set_err(omen_ctx* ctx, omen_status s, const char* fmt, ...);
+#define OMEN_CUDA(ctx, call)                                                            \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return set_err(ctx, OMEN_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+  } while (0)
+#define OMEN_CHECK_LAUNCH(ctx) OMEN_CUDA(ctx, cudaGetLastError())
+
+// geometry tables (constant memory), defined in lattice.cu --------------------------------
+// For A site s and direction k: the B site (4..7) of the neighbour and its cell offset.
+// For B site s (0..3 = b-4) and direction k: the A site of the neighbour and its cell offset.
+struct NeighbourTables {
+  int a_to_b_site[4][4];
+  int a_to_b_off[4][4][3];   // each component in {-1, 0}
+  int b_to_a_site[4][4];
+  int b_to_a_off[4][4][3];   // each component in {0, +1}
+};
+const NeighbourTables& host_neighbour_tables();
+omen_status upload_neighbour_tables(omen_ctx* ctx);
+
+// kernels launched from the C-ABI layer ------------------------------------------------------
+omen_status launch_assemble(omen_ctx* ctx, omen_ham* ham, const omen_tb_params* p);
+omen_status launch_hx(omen_ctx* ctx, const omen_ham* ham, const void* x, void* y, int nvec,
+                      double sigma, int vec_precision);
+
+// Krylov helper kernels (lanczos.cu)
+size_t vec_elem_bytes(const omen_ham* ham, int precision);

@@ -1,0 +1,247 @@
+"""ctypes binding of libomen.so (argument marshalling only; every step runs in the library).
+
+The functions carry the C names (omen_create, omen_build_lattice, omen_assemble_H, omen_hx,
+omen_eigs, ...).  Device buffers are passed as integers (device pointers) or as objects with
+a ``data_ptr()`` method (e.g. torch tensors); host buffers as numpy arrays.  A missing or
+unloadable library raises immediately: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libomen.so")
+
+OMEN_OK, OMEN_EINVAL, OMEN_ENOMEM, OMEN_ENOCONV, OMEN_ENUMERIC, OMEN_ETIMEOUT, OMEN_ECUDA, OMEN_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOCONV", "ENUMERIC", "ETIMEOUT", "ECUDA", "EUNSUPPORTED"]
+OMEN_SP3S, OMEN_SP3D5S = 5, 10
+OMEN_HARD_WALL, OMEN_PERIODIC, OMEN_BLOCH = 0, 1, 2
+OMEN_F64, OMEN_F32, OMEN_F32_REFINE64 = 0, 1, 2
+OMEN_LOWEST, OMEN_NEAREST = 0, 1
+
+
+class OmenError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class LatticeDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("periodic", C.c_int * 3),
+                ("a_nm", C.c_double), ("species_host", C.c_void_p), ("strain_host", C.c_void_p)]
+
+
+class TBParams(C.Structure):
+    _fields_ = [("basis", C.c_int), ("nspecies", C.c_int), ("onsite", (C.c_double * 4) * 4),
+                ("V", ((C.c_double * 14) * 4) * 4), ("lambda_so", C.c_double * 4), ("eta", C.c_double)]
+
+
+class HamOpts(C.Structure):
+    _fields_ = [("spin_orbit", C.c_int), ("precision", C.c_int), ("matrix_free", C.c_int),
+                ("k", C.c_void_p), ("U_atom_dev", C.c_void_p)]
+
+
+class EigOpts(C.Structure):
+    _fields_ = [("nev", C.c_int), ("which", C.c_int), ("sigma", C.c_double), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("block", C.c_int), ("basis", C.c_int), ("v0_host", C.c_void_p)]
+
+
+class EigInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("hx_count", C.c_longlong), ("restarts", C.c_int),
+                ("converged", C.c_int), ("max_residual", C.c_double), ("max_error_bound", C.c_double),
+                ("max_residual_raw", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libomen.so (built in-tree by paper_1003_4570_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+        sig = {
+            "omen_create": (i, [C.POINTER(vp), i, vp]),
+            "omen_destroy": (None, [vp]),
+            "omen_last_error": (C.c_char_p, [vp]),
+            "omen_set_wait_limit": (i, [vp, ll]),
+            "omen_build_lattice": (i, [vp, C.POINTER(LatticeDesc), C.POINTER(vp)]),
+            "omen_free_lattice": (None, [vp]),
+            "omen_lattice_counts": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
+            "omen_assemble_H": (i, [vp, vp, C.POINTER(TBParams), C.POINTER(HamOpts), C.POINTER(vp)]),
+            "omen_free_ham": (None, [vp]),
+            "omen_ham_shape": (i, [vp, C.POINTER(ll), C.POINTER(i), C.POINTER(i)]),
+            "omen_ham_set_potential": (i, [vp, vp, vp]),
+            "omen_hx": (i, [vp, vp, vp, vp, i, d]),
+            "omen_hx_host": (i, [vp, vp, vp, vp, i, d]),
+            "omen_eigs": (i, [vp, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    lib()
+    return [n for n in dir(_lib) if n.startswith("omen_")]
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+class Context:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def check(self, status):
+        if status != OMEN_OK:
+            raise OmenError(status, lib().omen_last_error(self.handle).decode())
+        return status
+
+    def close(self):
+        if self.handle:
+            lib().omen_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def omen_create(device=0, stream=None) -> Context:
+    h = C.c_void_p()
+    s = lib().omen_create(C.byref(h), int(device), _ptr(stream) if stream is not None else None)
+    if s != OMEN_OK:
+        raise OmenError(s, "omen_create failed (no CUDA device?)")
+    return Context(h)
+
+
+class Lattice:
+    def __init__(self, ctx, handle, keep):
+        self.ctx, self.handle, self._keep = ctx, handle, keep
+
+    def counts(self):
+        n, b = C.c_longlong(), C.c_longlong()
+        lib().omen_lattice_counts(self.handle, C.byref(n), C.byref(b))
+        return n.value, b.value
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().omen_free_lattice(self.handle)
+            self.handle = None
+
+
+def omen_build_lattice(ctx: Context, spec) -> Lattice:
+    """spec: nx, ny, nz, periodic (3), a_nm, species (uint8[8*ncells]), strain (float64[16*ncells])."""
+    species = np.ascontiguousarray(spec.species, dtype=np.uint8)
+    strain = None if spec.strain is None else np.ascontiguousarray(spec.strain, dtype=np.float64)
+    d = LatticeDesc(spec.nx, spec.ny, spec.nz, (C.c_int * 3)(*spec.periodic), float(spec.a_nm),
+                    species.ctypes.data, None if strain is None else strain.ctypes.data)
+    h = C.c_void_p()
+    ctx.check(lib().omen_build_lattice(ctx.handle, C.byref(d), C.byref(h)))
+    return Lattice(ctx, h, (species, strain))
+
+
+def tb_params_struct(p) -> TBParams:
+    """p: basis, onsite (ns,4), V (ns,ns,14), lambda_so (ns,), eta."""
+    t = TBParams()
+    ns = p.onsite.shape[0]
+    t.basis, t.nspecies, t.eta = int(p.basis), ns, float(p.eta)
+    for a in range(ns):
+        for q in range(4):
+            t.onsite[a][q] = float(p.onsite[a, q])
+        t.lambda_so[a] = float(p.lambda_so[a])
+        for b in range(ns):
+            for q in range(14):
+                t.V[a][b][q] = float(p.V[a, b, q])
+    return t
+
+
+class Hamiltonian:
+    def __init__(self, ctx, handle, lat):
+        self.ctx, self.handle, self.lattice = ctx, handle, lat
+        n, c, e = C.c_longlong(), C.c_int(), C.c_int()
+        lib().omen_ham_shape(handle, C.byref(n), C.byref(c), C.byref(e))
+        self.nrows, self.is_complex, self.elem_bytes = n.value, bool(c.value), e.value
+
+    @property
+    def numpy_dtype(self):
+        if self.is_complex:
+            return np.complex128 if self.elem_bytes == 16 else np.complex64
+        return np.float64 if self.elem_bytes == 8 else np.float32
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().omen_free_ham(self.handle)
+            self.handle = None
+
+
+def omen_assemble_H(ctx: Context, lat: Lattice, params, spin_orbit=False, precision=OMEN_F64,
+                    matrix_free=False, k=None, U_atom_dev=None) -> Hamiltonian:
+    tp = tb_params_struct(params)
+    karr = None if k is None else np.ascontiguousarray(k, dtype=np.float64)
+    o = HamOpts(int(bool(spin_orbit)), int(precision), int(bool(matrix_free)),
+                None if karr is None else karr.ctypes.data, _ptr(U_atom_dev))
+    h = C.c_void_p()
+    ctx.check(lib().omen_assemble_H(ctx.handle, lat.handle, C.byref(tp), C.byref(o), C.byref(h)))
+    return Hamiltonian(ctx, h, lat)
+
+
+def omen_ham_set_potential(ctx: Context, ham: Hamiltonian, U_atom_dev):
+    ctx.check(lib().omen_ham_set_potential(ctx.handle, ham.handle, _ptr(U_atom_dev)))
+
+
+def omen_hx(ctx: Context, ham: Hamiltonian, x_dev, y_dev, nvec=1, sigma=0.0):
+    """y = (H - sigma) x on device buffers (asynchronous on the context's stream)."""
+    ctx.check(lib().omen_hx(ctx.handle, ham.handle, _ptr(x_dev), _ptr(y_dev), int(nvec), float(sigma)))
+
+
+def omen_hx_host(ctx: Context, ham: Hamiltonian, x: np.ndarray, sigma=0.0) -> np.ndarray:
+    """The same product on host arrays of shape (nvec, nrows) or (nrows,)."""
+    x = np.ascontiguousarray(x, dtype=ham.numpy_dtype)
+    nvec = 1 if x.ndim == 1 else x.shape[0]
+    y = np.empty_like(x)
+    ctx.check(lib().omen_hx_host(ctx.handle, ham.handle, x.ctypes.data, y.ctypes.data, nvec, float(sigma)))
+    return y
+
+
+def omen_eigs(ctx: Context, ham: Hamiltonian, nev, which=OMEN_LOWEST, sigma=0.0, tol=1e-9, max_iter=1000,
+              block=1, basis=None, v0=None, evecs_dev=None, raise_on_noconv=True):
+    """Eigenpairs by thick-restart block Lanczos.  Returns (evals ndarray, info dict, status)."""
+    if basis is None:
+        basis = max(4 * block, ((2 * nev + 2 * block + block - 1) // block) * block, 32 // block * block)
+    v0a = None
+    if v0 is not None:
+        v0a = np.ascontiguousarray(v0, dtype=ham.numpy_dtype)
+    o = EigOpts(int(nev), int(which), float(sigma), float(tol), int(max_iter), int(block), int(basis),
+                None if v0a is None else v0a.ctypes.data)
+    ev = np.zeros(nev)
+    info = EigInfo()
+    s = lib().omen_eigs(ctx.handle, ham.handle, C.byref(o), ev.ctypes.data, _ptr(evecs_dev), C.byref(info))
+    if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
+        ctx.check(s)
+    return ev, info.as_dict(), s
