@@ -1,0 +1,284 @@
+"""Benchmark: H·X throughput of the tight-binding Hamiltonian on the 1M-atom SiGe alloy.
+
+Workload: Si0.7Ge0.3 random alloy of 50^3 conventional cells (1,000,000 atoms), hard walls,
+bond lengths strained by U[-2%, 2%] with Harrison d^-2 scaling, sp3d5s* (10 orbitals, 10M
+rows), seeded synthetic parameters.  One step = one application of the folded-spectrum
+operator (H - sigma)^2 to a vector, i.e. two H·X products — the unit the folded-spectrum
+Lanczos recurrence repeats (the paper times "500 Lanczos iterations").
+
+value = algorithmic bytes of the H·X products of all ranks / max-over-ranks time (GB/s).
+Algorithmic bytes per H·X: every stored bond block once (100 entries per bond), x and y once,
+one species byte and one potential word per atom.
+
+--impl reference: the CPU oracle (scipy CSR product from oracle/) on a bounded sample of the
+same workload, on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "H·X GB/s vs HBM peak; s to 16 eigenpairs at 1M atoms; SCF time vs plain"
+UNIT = "GB/s"
+N_CELLS = 50
+SAMPLE_NZ = 4          # CPU sample: 50 x 50 x 4 cells of the same recipe
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure is in the measured-peaks file)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def alg_bytes_per_hx(nbonds, natoms, nrows, elem, vec_elem, matrix_free):
+    h = 0 if matrix_free else nbonds * 100 * elem
+    extra = natoms * (1 + 8) + (nbonds * 8 if matrix_free else 0)
+    return h + 2 * nrows * vec_elem + extra
+
+
+def flops_per_hx(nbonds, natoms, norb=10):
+    return 2.0 * (2 * norb * norb * nbonds + norb * natoms)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, max, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_sample(seed=2):
+    """Bounded CPU sample of the same recipe: 50 x 50 x SAMPLE_NZ cells, oracle CSR."""
+    from oracle import hamiltonian
+    spec = synth.lattice_spec(N_CELLS, N_CELLS, SAMPLE_NZ, (0, 0, 0), seed=seed, alloy_fraction=0.3, strain_amp=0.02)
+    p = synth.draw_tb_params(seed, synth.SP3D5S, 2)
+    H = hamiltonian.assemble(spec, p)
+    from oracle import lattice
+    nb = len(lattice.find_bonds(spec.nx, spec.ny, spec.nz, spec.periodic).a)
+    return spec, H, nb
+
+
+def time_cpu_oracle(H, nbonds, natoms, steps, sigma=0.3):
+    x = synth.random_vectors(1, H.shape[0])[0]
+    y = H @ x
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        t = H @ x - sigma * x
+        y = H @ t - sigma * t
+    dt = time.perf_counter() - t0
+    alg = 2 * alg_bytes_per_hx(nbonds, natoms, H.shape[0], 8, 8, False) * steps
+    return alg / dt / 1e9, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    spec, H, nb = cpu_sample()
+    build_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        time_cpu_oracle(H, nb, spec.natoms, 1)
+    v, dt = time_cpu_oracle(H, nb, spec.natoms, args.steps)
+    sample = (f"oracle scipy CSR (H-sigma)^2 x on a 50x50x{SAMPLE_NZ}-cell slab of the same alloy recipe "
+              f"({spec.natoms} atoms, {H.shape[0]} rows, {H.nnz} nnz), {args.steps} steps in {dt:.2f} s; "
+              f"CSR assembly {build_s:.1f} s not timed")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "Si0.7Ge0.3 alloy, 2% bond strain, sp3d5s*, folded operator (H-sigma)^2 x",
+                       "atoms": spec.natoms, "rows": int(H.shape[0])},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_1003_4570_gb300 import omen
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    ctx = omen.omen_create(local_rank, stream.cuda_stream)
+    prec = {"f64": omen.OMEN_F64, "f32": omen.OMEN_F32}[args.precision]
+    spec, p = synth.config_sige_alloy(args.cells, seed=2)
+    lat = omen.omen_build_lattice(ctx, spec)
+    natoms, nbonds = lat.counts()
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, matrix_free=args.matrix_free)
+    dt = torch.float64 if prec == omen.OMEN_F64 else torch.float32
+    el = 8 if prec == omen.OMEN_F64 else 4
+    x = (torch.rand(ham.nrows, dtype=torch.float64, device="cuda") * 2 - 1).to(dt)
+    t = torch.empty_like(x)
+    y = torch.empty_like(x)
+    sigma = 0.3
+
+    def step():
+        omen.omen_hx(ctx, ham, x, t, 1, sigma)
+        omen.omen_hx(ctx, ham, t, y, 1, sigma)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    alg = alg_bytes_per_hx(nbonds, natoms, ham.nrows, el, el, args.matrix_free)
+    value = world * 2 * alg * args.steps / (ms / 1e3) / 1e9
+    launch_ms = ms / (2 * args.steps)
+
+    # end to end through the host-buffer entry point (pinned host x, y; copies timed)
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    import ctypes
+    L = omen.lib()
+    for _ in range(2):
+        ctx.check(L.omen_hx_host(ctx.handle, ham.handle, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(yh.data_ptr()), 1, sigma))
+    e2e_steps = max(5, min(50, args.steps // 10))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.check(L.omen_hx_host(ctx.handle, ham.handle, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(yh.data_ptr()), 1, sigma))
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_val = world * alg * e2e_steps / e2e_s / 1e9
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    achieved_gbs = alg / (launch_ms / 1e3) / 1e9
+    if prec == omen.OMEN_F64:
+        fl = flops_per_hx(nbonds, natoms)
+        achieved_tf = fl / (launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "hx_kernel<double,10,real,stored>", "hbm_achieved_gbs": achieved_gbs,
+                "hbm_frac_of_measured": achieved_gbs / hbm, "peak_source": "recipe nominal FP64"}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": achieved_gbs / hbm, "traffic": None,
+                "kernel": "hx_kernel<float,10,real,stored>", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+              "config": {"workload": f"Si0.7Ge0.3 alloy {args.cells}^3 cells ({natoms:,} atoms), hard wall, 2% bond "
+                                     "strain, sp3d5s*; step = folded operator (H-sigma)^2 x (two H·X)",
+                         "atoms": natoms, "bonds": nbonds, "rows": ham.nrows,
+                         "storage": "matrix-free" if args.matrix_free else "stored bond blocks",
+                         "l2": "no flush: H blocks exceed L2", "parallelism": f"replicas x{world}"},
+              "roofline": roof, "gpu_launches": 2 * args.steps,
+              "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": ham.nrows * el,
+                      "d2h_bytes_per_step": ham.nrows * el},
+              "clocks": clk.summary()}
+    if rank == 0 and not args.no_cpu:
+        t0 = time.perf_counter()
+        cspec, H, cnb = cpu_sample()
+        v, dtc = time_cpu_oracle(H, cnb, cspec.natoms, 10)
+        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"scipy CSR (H-sigma)^2 x, 10 steps on a 50x50x{SAMPLE_NZ}-cell slab "
+                                            f"({cspec.natoms} atoms) of the same recipe, {dtc:.1f} s"}
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--matrix-free", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cells", type=int, default=N_CELLS, help="cells per edge (50 = the 1M-atom workload; "
+                    "smaller only for profiling captures)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

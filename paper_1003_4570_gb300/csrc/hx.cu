@@ -1,7 +1,7 @@
 // y = (H - sigma) x: the block-sparse tight-binding product repeated by the Lanczos
 // recurrence (paper Section II-B benchmarks "500 Lanczos iterations"; Section III-A item 1).
 //
-// One thread per atom (grid.y = site b, grid.x over cells, grid.z over vectors).  Each row
+// One thread per atom (grid.x over (cell tile, site b) with b fastest, grid.z over vectors).  Each row
 // of H has an onsite block and four bond blocks.  Bond blocks are stored once per bond
 // (A-atom slot); an A atom applies B, its B partner applies B^T, so no block is duplicated.
 // The partner's copy of the block is read within about one z-plane of cells of the first
@@ -62,8 +62,10 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
   using V = typename VecT<T, CPLX>::t;
   constexpr int NS = SO ? 2 : 1;
   const Geo& g = a.g;
-  const int b = blockIdx.y;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  // site fastest in the block order: CTAs in flight cover all 8 sites of a window of cells,
+  // so the transposed (B-end) read of a bond block follows its A-end read within L2 reach
+  const int b = blockIdx.x & 7;
+  const int cell = (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
   if (cell >= g.ncells) return;
   const int N = g.natoms;
   const int atom = b * g.ncells + cell;
@@ -220,7 +222,7 @@ size_t vec_elem_bytes(const omen_ham* h, int precision) {
 
 template <typename T, int NORB, bool CPLX, bool SO, bool MF>
 static cudaError_t launch_t(const HxArgs<T>& a, int nvec, cudaStream_t st) {
-  dim3 grid((a.g.ncells + 127) / 128, 8, nvec);
+  dim3 grid(((a.g.ncells + 127) / 128) * 8, 1, nvec);
   hx_kernel<T, NORB, CPLX, SO, MF><<<grid, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
