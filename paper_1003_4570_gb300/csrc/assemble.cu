@@ -3,8 +3,9 @@
 // 1. b0 table: the Slater–Koster block of every (species pair, bond direction) at d0,
 //    from the Table I integrals (sk_device.cuh).
 // 2. bond blocks: each existing bond slot gets (d0/d)^eta * b0[pair][dir], d = d0 (1 + strain),
-//    stored entry-major (blk[e * nslots + slot]) so a warp reads 32 consecutive slots of one
-//    entry with one coalesced load.  Matrix-free Hamiltonians skip this step and H·X
+//    stored in tiles of 32 consecutive slots with the entries of a tile contiguous
+//    (blk[(tile*ne + e)*32 + lane]): a warp reads 32 slots of one entry with one coalesced
+//    128-byte load, and one bond block of a warp is a single contiguous run.  Matrix-free Hamiltonians skip this step and H·X
 //    regenerates the block from the b0 table, the two species and the strain.
 #include <cmath>
 #include <cstring>
@@ -33,23 +34,32 @@ __global__ void b0_table_kernel(const double* __restrict__ V, int ns, int norb, 
 
 __global__ void assemble_bonds_kernel(Geo g, NeighbourTables nt, const uint8_t* __restrict__ species,
                                       const double* __restrict__ strain, const double* __restrict__ b0,
-                                      int ns, int norb, double eta, double* __restrict__ blk64,
+                                      int ns, int norb, double eta, int slot_stride, double* __restrict__ blk64,
                                       float* __restrict__ blk32) {
-  const int nslots = 16 * g.ncells;
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= nslots) return;
-  const int cell = slot % g.ncells;
-  const int ks = slot / g.ncells;  // k*4 + s
+  const int npad = 16 * slot_stride;
+  const int pidx = blockIdx.x * blockDim.x + threadIdx.x;   // padded slot index
+  if (pidx >= npad) return;
+  const int cell = pidx % slot_stride;
+  const int ks = pidx / slot_stride;  // k*4 + s
+  const int ne = norb * norb;
+  const size_t base = ((size_t)(pidx >> 5) * ne) * 32 + (pidx & 31);
+  if (cell >= g.ncells) {  // padding
+    for (int e = 0; e < ne; ++e) {
+      if (blk64) blk64[base + (size_t)e * 32] = 0.0;
+      if (blk32) blk32[base + (size_t)e * 32] = 0.0f;
+    }
+    return;
+  }
+  const int slot = ks * g.ncells + cell;  // strain input layout
   const int k = ks >> 2, s = ks & 3;
   const int ix = cell % g.nx, iy = (cell / g.nx) % g.ny, iz = cell / (g.nx * g.ny);
   int cell2, wrap[3];
   const bool ok = shift_cell(g, ix, iy, iz, nt.a_to_b_off[s][k][0], nt.a_to_b_off[s][k][1], nt.a_to_b_off[s][k][2],
                              cell2, wrap);
-  const int ne = norb * norb;
   if (!ok) {
     for (int e = 0; e < ne; ++e) {
-      if (blk64) blk64[(size_t)e * nslots + slot] = 0.0;
-      if (blk32) blk32[(size_t)e * nslots + slot] = 0.0f;
+      if (blk64) blk64[base + (size_t)e * 32] = 0.0;
+      if (blk32) blk32[base + (size_t)e * 32] = 0.0f;
     }
     return;
   }
@@ -59,8 +69,8 @@ __global__ void assemble_bonds_kernel(Geo g, NeighbourTables nt, const uint8_t* 
   const double* tb = b0 + ((size_t)(sa * ns + sb) * 4 + k) * ne;
   for (int e = 0; e < ne; ++e) {
     const double v = f * tb[e];
-    if (blk64) blk64[(size_t)e * nslots + slot] = v;
-    if (blk32) blk32[(size_t)e * nslots + slot] = (float)v;
+    if (blk64) blk64[base + (size_t)e * 32] = v;
+    if (blk32) blk32[base + (size_t)e * 32] = (float)v;
   }
 }
 
@@ -142,7 +152,8 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
   for (int s = 0; s < 4; ++s) h->lambda_so[s] = p->lambda_so[s];
 
   const int ns = p->nspecies, norb = p->basis, ne = norb * norb;
-  const size_t nslots = 16 * (size_t)lat->ncells;
+  h->slot_stride = (lat->ncells + 31) / 32 * 32;
+  const size_t nslots = 16 * (size_t)h->slot_stride;
   const size_t ntab = (size_t)ns * ns * 4 * ne;
   ALLOC_OR_FAIL(h->d_b0_64, ntab * sizeof(double));
   ALLOC_OR_FAIL(h->d_b0_32, ntab * sizeof(float));
@@ -191,7 +202,7 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
     Geo g{lat->nx, lat->ny, lat->nz, lat->ncells, lat->natoms, {lat->periodic[0], lat->periodic[1], lat->periodic[2]}};
     assemble_bonds_kernel<<<(unsigned)((nslots + 255) / 256), 256, 0, ctx->stream>>>(
         g, host_neighbour_tables(), lat->d_species, lat->d_strain, h->d_b0_64, ns, norb, p->eta,
-        h->d_blk64, h->d_blk32);
+        h->slot_stride, h->d_blk64, h->d_blk32);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

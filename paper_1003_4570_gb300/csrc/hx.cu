@@ -6,12 +6,15 @@
 // (A-atom slot); an A atom applies B, its B partner applies B^T, so no block is duplicated.
 // The partner's copy of the block is read within about one z-plane of cells of the first
 // read, which lies inside the L2 cache, so HBM sees each block about once.
-// Blocks are entry-major (blk[e*nslots + slot]): for a fixed entry, consecutive threads
-// (consecutive cells) read consecutive words.  Vectors are orbital-major, atom-minor, so the
+// Blocks are stored in 32-slot tiles (entries of a tile contiguous): for a fixed entry,
+// consecutive threads (consecutive cells) read consecutive words, and a warp's whole block
+// is one contiguous run of memory.  Vectors are orbital-major, atom-minor, so the
 // per-orbital loads of x and stores of y are coalesced as well.
 // Bloch phase: a neighbour reached across the high (low) face of a Bloch-periodic direction d
 // is its periodic image shifted by +L_d (-L_d); its amplitude is multiplied by
 // exp(+i k_d L_d) (resp. the conjugate).
+#include <type_traits>
+
 #include "omen_internal.h"
 #include "sk_device.cuh"
 
@@ -40,6 +43,7 @@ struct HxArgs {
   double eta;
   double2 phase[3];
   int ns;
+  int slot_stride;
 };
 
 template <typename T>
@@ -73,7 +77,6 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
   const V* __restrict__ x = static_cast<const V*>(a.x) + (size_t)blockIdx.z * a.nrows;
   V* __restrict__ y = static_cast<V*>(a.y) + (size_t)blockIdx.z * a.nrows;
   const int sp = a.species[atom];
-  const size_t nslots = 16 * (size_t)g.ncells;
 
   V acc[NS][NORB];
   {
@@ -172,8 +175,10 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
       hb = a.b0 + ((size_t)(sa * a.ns + sb) * 4 + k) * (NORB * NORB);
       stride = 1;
     } else {
-      hb = a.blk + slot;
-      stride = nslots;
+      const size_t ks = is_a ? (size_t)(k * 4 + s) : (size_t)(k * 4 + site2);
+      const size_t pidx = ks * a.slot_stride + (is_a ? cell : cell2);
+      hb = a.blk + ((pidx >> 5) * (NORB * NORB)) * 32 + (pidx & 31);
+      stride = 32;
     }
 
     if constexpr (MATFREE) {
@@ -185,28 +190,37 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
           if constexpr (CPLX) { xn[q][o].x *= scale; xn[q][o].y *= scale; } else { xn[q][o] *= scale; }
         }
     }
-    if (is_a) {
+    // Rows of the block are loaded RB at a time into registers before their FMAs, so each
+    // thread keeps RB*NORB independent loads in flight (memory-level parallelism).
+    constexpr int RB = (sizeof(T) == 8 || MATFREE) ? 1 : (NS == 1 ? NORB : (NORB == 10 ? 5 : NORB));
 #pragma unroll
-      for (int o1 = 0; o1 < NORB; ++o1)
+    for (int r0 = 0; r0 < NORB; r0 += RB) {
+      T hr[RB * NORB];
 #pragma unroll
-        for (int o2 = 0; o2 < NORB; ++o2) {
-          const T h = hb[(size_t)(o1 * NORB + o2) * stride];
+      for (int e = 0; e < RB * NORB; ++e) hr[e] = __ldg(hb + (size_t)(r0 * NORB + e) * stride);
+      if (is_a) {
 #pragma unroll
-          for (int q = 0; q < NS; ++q) {
-            if constexpr (CPLX) fma_c(acc[q][o1], h, xn[q][o2]); else fma_r(acc[q][o1], h, xn[q][o2]);
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+          for (int o2 = 0; o2 < NORB; ++o2) {
+            const T h = hr[i * NORB + o2];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+              if constexpr (CPLX) fma_c(acc[q][r0 + i], h, xn[q][o2]); else fma_r(acc[q][r0 + i], h, xn[q][o2]);
+            }
           }
-        }
-    } else {
+      } else {
 #pragma unroll
-      for (int o1 = 0; o1 < NORB; ++o1)
+        for (int i = 0; i < RB; ++i)
 #pragma unroll
-        for (int o2 = 0; o2 < NORB; ++o2) {
-          const T h = hb[(size_t)(o1 * NORB + o2) * stride];
+          for (int o2 = 0; o2 < NORB; ++o2) {
+            const T h = hr[i * NORB + o2];
 #pragma unroll
-          for (int q = 0; q < NS; ++q) {
-            if constexpr (CPLX) fma_c(acc[q][o2], h, xn[q][o1]); else fma_r(acc[q][o2], h, xn[q][o1]);
+            for (int q = 0; q < NS; ++q) {
+              if constexpr (CPLX) fma_c(acc[q][o2], h, xn[q][r0 + i]); else fma_r(acc[q][o2], h, xn[q][r0 + i]);
+            }
           }
-        }
+      }
     }
   }
 #pragma unroll
@@ -256,6 +270,7 @@ static cudaError_t launch_prec(const omen_ham* h, const T* blk, const T* b0, con
   a.eta = h->eta;
   for (int d = 0; d < 3; ++d) a.phase[d] = h->phase[d];
   a.ns = h->nspecies;
+  a.slot_stride = h->slot_stride;
   return h->norb == 10 ? launch_norb<T, 10>(a, h, nvec, st) : launch_norb<T, 5>(a, h, nvec, st);
 }
 

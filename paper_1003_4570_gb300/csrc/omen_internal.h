@@ -39,7 +39,9 @@ struct omen_ham {
   double eta = 2.0;
   double kvec[3] = {0, 0, 0};
   double2 phase[3];                       // exp(i k.L_d e_d) for a +1 supercell wrap along d
-  // stored bond blocks, entry-major: blk[e * nslots + slot], e = o1*norb + o2 (A rows, B cols)
+  // stored bond blocks in 32-slot tiles: slot (k*4+s, cell) -> p = (k*4+s)*slot_stride + cell,
+  // entry e = o1*norb + o2 (A rows, B cols) at blk[((p >> 5) * norb*norb + e) * 32 + (p & 31)]
+  int slot_stride = 0;                    // ncells rounded up to a multiple of 32
   double* d_blk64 = nullptr;
   float* d_blk32 = nullptr;
   // matrix-free table: B0[((sa*ns + sb)*4 + k)*norb*norb + e]
