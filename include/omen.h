@@ -173,6 +173,96 @@ typedef struct {
 omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_eig_opts* opts,
                       double* evals_host, void* evecs_dev, omen_eig_info* info);
 
+/* ---- charge, Poisson, self-consistency (paper Section III-A items 2-3) ------------------- */
+
+typedef struct {
+  int nx, ny;                /* grid points along the periodic x and y directions */
+  int nz;                    /* intervals along z; unknowns at z_k = k*Lz/nz, k = 1..nz-1 */
+  double Lx_nm, Ly_nm, Lz_nm;
+  double eps_r;              /* relative permittivity (Si: 11.7) */
+} omen_grid;
+/* Grid arrays (rho, phi) hold the interior unknowns, index ((k-1)*ny + j)*nx + i.
+ * phi = 0 V on the planes z = 0 and z = Lz. */
+
+typedef struct {
+  double rtol;               /* stop when ||r|| <= rtol ||b|| */
+  int max_iter;
+} omen_cg_opts;
+
+typedef struct {
+  int iterations;
+  int converged;
+  double rel_residual;       /* ||r|| / ||b|| at exit */
+  double seconds;
+} omen_solve_info;
+
+/* Solve -div(eps0 eps_r grad phi) = rho (7-point finite differences, periodic x and y,
+ * phi = 0 at both z ends) by conjugate gradients in FP64, all iterations in one cooperative
+ * launch (paper: finite-difference Poisson solver, Section III-A item 3).
+ * rho_dev: C/m^3; phi_dev: V, initial guess in, solution out.  ENOCONV at max_iter. */
+omen_status omen_poisson(omen_ctx* ctx, const omen_grid* grid, const double* rho_dev, double* phi_dev,
+                         const omen_cg_opts* opts, omen_solve_info* info);
+
+/* n_atom_dev[i] += weight * sum_n occ_host[n] * sum_o |psi_n(o*natoms + i)|^2 for nstates FP64
+ * (double or complex128) vectors psi_dev [nstates][nrows] of ham (paper: charge from the
+ * filled states, Section III-A item 2). */
+omen_status omen_density_accum(omen_ctx* ctx, const omen_ham* ham, const void* psi_dev, int nstates,
+                               const double* occ_host, double weight, double* n_atom_dev);
+
+/* Cloud-in-cell (trilinear) deposit of per-atom charge q_atom_dev (C) onto the grid nodes,
+ * divided by the cell volume: rho_dev (C/m^3) is overwritten.  Charge landing on the z = 0 or
+ * z = Lz planes is dropped (grounded).  Atom positions come from the structure. */
+omen_status omen_deposit(omen_ctx* ctx, const omen_lattice* lat, const omen_grid* grid,
+                         const double* q_atom_dev, double* rho_dev);
+/* Trilinear interpolation of phi (boundary planes at 0 V) to every atom: phi_atom_dev [natoms]. */
+omen_status omen_gather(omen_ctx* ctx, const omen_lattice* lat, const omen_grid* grid,
+                        const double* phi_dev, double* phi_atom_dev);
+
+/* Fermi level by bisection: sum_i g_i f((E_i - E_F)/kT) = n_target with g_i = level_weight[i]
+ * (k weight times spin degeneracy).  Host only; no device use.  EINVAL if n_target is not
+ * reachable with the given levels. */
+omen_status omen_fermi_level(const double* E, const double* level_weight, int n, double n_target,
+                             double kT, double* E_F);
+
+typedef struct {
+  const omen_lattice* lat;
+  const omen_tb_params* params;
+  int precision;             /* eigen-solve precision (OMEN_F64 or OMEN_F32_REFINE64) */
+  const omen_grid* grid;
+  const double* donor_rho_dev; /* fixed positive charge density on the grid (C/m^3) */
+  double n_electrons;        /* electrons per supercell (charge neutrality) */
+  double kT;                 /* eV */
+  int nk;                    /* k points (supercell Bloch vectors, 1/nm) and weights (sum 1) */
+  const double* k_host;      /* [nk][3] */
+  const double* kw_host;     /* [nk] */
+  int nev;                   /* states per k nearest sigma (folded spectrum) */
+  double sigma;              /* eV */
+  double e_cut;              /* only states above e_cut hold electrons (conduction band) */
+  double eig_tol;
+  int eig_block, eig_basis, eig_max_iter;
+  double mix;                /* linear mixing: phi <- phi + mix (phi_out - phi) */
+  double tol_V;              /* stop when max |phi_out - phi| < tol_V */
+  int max_iter;
+  omen_cg_opts cg;
+} omen_scf_desc;
+
+typedef struct {
+  int iterations;
+  int converged;
+  double dV_inf;             /* last max |phi_out - phi| (V) */
+  double E_F;                /* eV */
+  long long hx_count;        /* H·X products over all eigen-solves */
+  double seconds;
+  double eig_seconds, poisson_seconds;
+} omen_scf_info;
+
+/* Self-consistent Schrödinger–Poisson loop (paper Section III-A): potential -> onsite
+ * U = -phi at the atoms -> eigenstates per k -> Fermi level by neutrality -> electron charge
+ * -> Poisson -> linear mixing, until max |phi_out - phi| < tol_V.  phi_dev: grid potential, start
+ * value in (zeros = zero-field start), converged potential out.  ENOCONV at max_iter;
+ * ENUMERIC if the highest computed state of some k is occupied above 1e-12 (nev too small). */
+omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* desc, double* phi_dev, omen_scf_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,199 @@
+// Finite-difference Poisson solver (paper Section III-A item 3: "finite difference method"
+// with an iterative linear solver; Aztec there, conjugate gradients here).
+//
+// -div(eps0 eps_r grad phi) = rho on a uniform grid: 7-point stencil, periodic along x and y,
+// phi = 0 on the z = 0 and z = Lz planes.  The operator is symmetric positive definite, so
+// plain CG (Hestenes & Stiefel 1952) applies.  The whole iteration runs in one cooperative
+// launch: three grid-wide barriers per iteration, block partial sums reduced by every block in
+// the same order, so all blocks see bit-identical scalars and leave the loop together.
+#include <cooperative_groups.h>
+
+#include <chrono>
+#include <cmath>
+
+#include "omen_internal.h"
+
+namespace cgr = cooperative_groups;
+
+static constexpr double kEps0 = 8.8541878128e-12;  // F/m
+
+struct PGrid {
+  int nx, ny, nzi;           // nzi = nz - 1 interior planes
+  double cx, cy, cz;         // 1/h^2 (1/m^2)
+  long long n;
+};
+
+__device__ __forceinline__ double stencil(const double* __restrict__ v, const PGrid& g, long long idx) {
+  const int i = (int)(idx % g.nx);
+  const int j = (int)((idx / g.nx) % g.ny);
+  const int k = (int)(idx / ((long long)g.nx * g.ny));
+  const long long plane = (long long)g.nx * g.ny;
+  const double c = v[idx];
+  const int ip = (i + 1 == g.nx) ? 0 : i + 1, im = (i == 0) ? g.nx - 1 : i - 1;
+  const int jp = (j + 1 == g.ny) ? 0 : j + 1, jm = (j == 0) ? g.ny - 1 : j - 1;
+  const long long row = idx - i - (long long)j * g.nx;
+  double s = g.cx * (2.0 * c - v[row + (long long)j * g.nx + ip] - v[row + (long long)j * g.nx + im]);
+  s += g.cy * (2.0 * c - v[row + (long long)jp * g.nx + i] - v[row + (long long)jm * g.nx + i]);
+  const double up = (k + 1 < g.nzi) ? v[idx + plane] : 0.0;
+  const double dn = (k > 0) ? v[idx - plane] : 0.0;
+  s += g.cz * (2.0 * c - up - dn);
+  return s;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  return t;  // valid in thread 0
+}
+
+// every block sums the partials of all blocks in index order (same result everywhere)
+__device__ __forceinline__ double grid_total(const double* __restrict__ part, double* sh) {
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += part[b];
+  // ordered: reduce within the block deterministically
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = t;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+  __syncthreads();
+  return s;
+}
+
+struct CGOut {
+  int iterations;
+  int converged;
+  double rel;
+};
+
+__global__ void __launch_bounds__(256) cg_kernel(PGrid g, const double* __restrict__ rho, double scale,
+                                                 double* __restrict__ x, double* __restrict__ r,
+                                                 double* __restrict__ p, double* __restrict__ q,
+                                                 double* __restrict__ part, double rtol, int max_iter,
+                                                 CGOut* __restrict__ out) {
+  cgr::grid_group grid = cgr::this_grid();
+  __shared__ double sh[32];
+  const long long n = g.n;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double* part0 = part;
+  double* part1 = part + gridDim.x;
+  double* part2 = part + 2 * gridDim.x;
+  // r = b - A x, p = r
+  double lrr = 0.0, lbb = 0.0;
+  for (long long i = t0; i < n; i += stride) {
+    const double b = scale * rho[i];
+    const double ri = b - stencil(x, g, i);
+    r[i] = ri;
+    p[i] = ri;
+    lrr += ri * ri;
+    lbb += b * b;
+  }
+  double v = block_sum(lrr, sh);
+  if (threadIdx.x == 0) part0[blockIdx.x] = v;
+  v = block_sum(lbb, sh);
+  if (threadIdx.x == 0) part2[blockIdx.x] = v;
+  grid.sync();
+  double rr = grid_total(part0, sh);
+  const double bb = grid_total(part2, sh);
+  const double stop = rtol * rtol * bb;
+  int it = 0;
+  while (rr > stop && it < max_iter && bb > 0.0) {
+    double lpq = 0.0;
+    for (long long i = t0; i < n; i += stride) {
+      const double qi = stencil(p, g, i);
+      q[i] = qi;
+      lpq += p[i] * qi;
+    }
+    v = block_sum(lpq, sh);
+    if (threadIdx.x == 0) part0[blockIdx.x] = v;
+    grid.sync();
+    const double pq = grid_total(part0, sh);
+    const double alpha = rr / pq;
+    double lr = 0.0;
+    for (long long i = t0; i < n; i += stride) {
+      x[i] += alpha * p[i];
+      const double ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      lr += ri * ri;
+    }
+    v = block_sum(lr, sh);
+    if (threadIdx.x == 0) part1[blockIdx.x] = v;
+    grid.sync();
+    const double rr_new = grid_total(part1, sh);
+    const double beta = rr_new / rr;
+    rr = rr_new;
+    for (long long i = t0; i < n; i += stride) p[i] = r[i] + beta * p[i];
+    grid.sync();
+    ++it;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out->iterations = it;
+    out->converged = (rr <= stop) || bb == 0.0;
+    out->rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  }
+}
+
+extern "C" omen_status omen_poisson(omen_ctx* ctx, const omen_grid* gr, const double* rho, double* phi,
+                                    const omen_cg_opts* o, omen_solve_info* info) {
+  if (!ctx || !gr || !rho || !phi || !o) return set_err(ctx, OMEN_EINVAL, "null argument");
+  if (gr->nx < 1 || gr->ny < 1 || gr->nz < 2) return set_err(ctx, OMEN_EINVAL, "grid needs nx, ny >= 1 and nz >= 2");
+  if (!(gr->Lx_nm > 0 && gr->Ly_nm > 0 && gr->Lz_nm > 0 && gr->eps_r > 0)) return set_err(ctx, OMEN_EINVAL, "grid lengths and eps_r must be > 0");
+  if (!(o->rtol > 0) || o->max_iter < 1) return set_err(ctx, OMEN_EINVAL, "cg options");
+  OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
+  auto t0 = std::chrono::steady_clock::now();
+  PGrid g;
+  g.nx = gr->nx;
+  g.ny = gr->ny;
+  g.nzi = gr->nz - 1;
+  const double hx = gr->Lx_nm / gr->nx * 1e-9, hy = gr->Ly_nm / gr->ny * 1e-9, hz = gr->Lz_nm / gr->nz * 1e-9;
+  // a periodic direction with one point has no second difference
+  g.cx = gr->nx > 1 ? 1.0 / (hx * hx) : 0.0;
+  g.cy = gr->ny > 1 ? 1.0 / (hy * hy) : 0.0;
+  g.cz = 1.0 / (hz * hz);
+  g.n = (long long)g.nx * g.ny * g.nzi;
+  int dev_sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  OMEN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, 256, 0));
+  long long want = (g.n + 255) / 256;
+  int blocks = (int)std::min<long long>(want, (long long)dev_sms * std::max(1, per_sm));
+  blocks = std::max(blocks, 1);
+  double* buf = nullptr;
+  const size_t vec = (size_t)g.n * sizeof(double);
+  if (cudaMallocAsync(&buf, 3 * vec + 3 * blocks * sizeof(double) + sizeof(CGOut) + 64, ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, OMEN_ENOMEM, "CG work vectors");
+  }
+  double* r = buf;
+  double* p = r + g.n;
+  double* q = p + g.n;
+  double* part = q + g.n;
+  CGOut* out = reinterpret_cast<CGOut*>(part + 3 * blocks);
+  double scale = 1.0 / (kEps0 * gr->eps_r);
+  double rtol = o->rtol;
+  int max_iter = o->max_iter;
+  void* args[] = {&g, &rho, &scale, &phi, &r, &p, &q, &part, &rtol, &max_iter, &out};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(blocks), dim3(256), args, 0, ctx->stream);
+  CGOut ho{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ho, out, sizeof(CGOut), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(buf, ctx->stream);
+  cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return set_err(ctx, OMEN_ECUDA, "Poisson CG: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  if (info) {
+    info->iterations = ho.iterations;
+    info->converged = ho.converged;
+    info->rel_residual = ho.rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!ho.converged) return set_err(ctx, OMEN_ENOCONV, "CG stopped at %d iterations, relative residual %.3e", ho.iterations, ho.rel);
+  return OMEN_OK;
+}

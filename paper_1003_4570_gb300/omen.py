@@ -58,6 +58,40 @@ class EigInfo(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("Lx_nm", C.c_double), ("Ly_nm", C.c_double),
+                ("Lz_nm", C.c_double), ("eps_r", C.c_double)]
+
+
+class CGOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SCFDesc(C.Structure):
+    _fields_ = [("lat", C.c_void_p), ("params", C.c_void_p), ("precision", C.c_int), ("grid", C.c_void_p),
+                ("donor_rho_dev", C.c_void_p), ("n_electrons", C.c_double), ("kT", C.c_double), ("nk", C.c_int),
+                ("k_host", C.c_void_p), ("kw_host", C.c_void_p), ("nev", C.c_int), ("sigma", C.c_double),
+                ("e_cut", C.c_double), ("eig_tol", C.c_double), ("eig_block", C.c_int), ("eig_basis", C.c_int),
+                ("eig_max_iter", C.c_int), ("mix", C.c_double), ("tol_V", C.c_double), ("max_iter", C.c_int),
+                ("cg", CGOpts)]
+
+
+class SCFInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("dV_inf", C.c_double), ("E_F", C.c_double),
+                ("hx_count", C.c_longlong), ("seconds", C.c_double), ("eig_seconds", C.c_double),
+                ("poisson_seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -84,6 +118,12 @@ def lib():
             "omen_hx": (i, [vp, vp, vp, vp, i, d]),
             "omen_hx_host": (i, [vp, vp, vp, vp, i, d]),
             "omen_eigs": (i, [vp, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
+            "omen_poisson": (i, [vp, C.POINTER(Grid), vp, vp, C.POINTER(CGOpts), C.POINTER(SolveInfo)]),
+            "omen_density_accum": (i, [vp, vp, vp, i, vp, d, vp]),
+            "omen_deposit": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
+            "omen_gather": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
+            "omen_fermi_level": (i, [vp, vp, i, d, d, C.POINTER(d)]),
+            "omen_scf": (i, [vp, C.POINTER(SCFDesc), vp, C.POINTER(SCFInfo)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -245,3 +285,64 @@ def omen_eigs(ctx: Context, ham: Hamiltonian, nev, which=OMEN_LOWEST, sigma=0.0,
     if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
         ctx.check(s)
     return ev, info.as_dict(), s
+
+
+def grid_struct(g) -> Grid:
+    """g: nx, ny, nz, Lx_nm, Ly_nm, Lz_nm, eps_r (e.g. oracle.poisson.Grid or any namespace)."""
+    return Grid(int(g.nx), int(g.ny), int(g.nz), float(g.Lx_nm), float(g.Ly_nm), float(g.Lz_nm), float(g.eps_r))
+
+
+def omen_poisson(ctx: Context, grid, rho_dev, phi_dev, rtol=1e-12, max_iter=100000):
+    """CG solve in place on phi_dev (initial guess in).  Returns the solve info dict."""
+    g = grid_struct(grid)
+    o = CGOpts(float(rtol), int(max_iter))
+    info = SolveInfo()
+    ctx.check(lib().omen_poisson(ctx.handle, C.byref(g), _ptr(rho_dev), _ptr(phi_dev), C.byref(o), C.byref(info)))
+    return info.as_dict()
+
+
+def omen_density_accum(ctx: Context, ham: Hamiltonian, psi_dev, nstates, occ, weight, n_atom_dev):
+    occ = np.ascontiguousarray(occ, dtype=np.float64)
+    ctx.check(lib().omen_density_accum(ctx.handle, ham.handle, _ptr(psi_dev), int(nstates), occ.ctypes.data,
+                                       float(weight), _ptr(n_atom_dev)))
+
+
+def omen_deposit(ctx: Context, lat: Lattice, grid, q_atom_dev, rho_dev):
+    g = grid_struct(grid)
+    ctx.check(lib().omen_deposit(ctx.handle, lat.handle, C.byref(g), _ptr(q_atom_dev), _ptr(rho_dev)))
+
+
+def omen_gather(ctx: Context, lat: Lattice, grid, phi_dev, phi_atom_dev):
+    g = grid_struct(grid)
+    ctx.check(lib().omen_gather(ctx.handle, lat.handle, C.byref(g), _ptr(phi_dev), _ptr(phi_atom_dev)))
+
+
+def omen_fermi_level(E, level_weight, n_target, kT):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    w = np.ascontiguousarray(level_weight, dtype=np.float64)
+    ef = C.c_double()
+    s = lib().omen_fermi_level(E.ctypes.data, w.ctypes.data, len(E), float(n_target), float(kT), C.byref(ef))
+    if s != OMEN_OK:
+        raise OmenError(s, "omen_fermi_level: target not reachable or bad arguments")
+    return ef.value
+
+
+def omen_scf(ctx: Context, lat: Lattice, params, grid, phi_dev, donor_rho_dev, n_electrons, kT, kpts, kweights,
+             nev, sigma, e_cut, precision=OMEN_F64, eig_tol=1e-9, eig_block=1, eig_basis=None, eig_max_iter=20000,
+             mix=0.1, tol_V=1e-6, max_iter=300, cg_rtol=1e-13, cg_max_iter=100000, raise_on_noconv=True):
+    """Self-consistent loop in place on phi_dev.  Returns (info dict, status)."""
+    tp = tb_params_struct(params)
+    g = grid_struct(grid)
+    k = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 3)
+    kw = np.ascontiguousarray(kweights, dtype=np.float64)
+    if eig_basis is None:
+        eig_basis = max(4 * eig_block, ((2 * nev + 2 * eig_block + eig_block - 1) // eig_block) * eig_block)
+    d = SCFDesc(lat.handle, C.addressof(tp), int(precision), C.addressof(g), _ptr(donor_rho_dev), float(n_electrons),
+                float(kT), len(kw), k.ctypes.data, kw.ctypes.data, int(nev), float(sigma), float(e_cut), float(eig_tol),
+                int(eig_block), int(eig_basis), int(eig_max_iter), float(mix), float(tol_V), int(max_iter),
+                CGOpts(float(cg_rtol), int(cg_max_iter)))
+    info = SCFInfo()
+    s = lib().omen_scf(ctx.handle, C.byref(d), _ptr(phi_dev), C.byref(info))
+    if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
+        ctx.check(s)
+    return info.as_dict(), s

@@ -151,3 +151,44 @@ def config_sige_alloy(n: int = 50, seed: int = 2, spin_orbit: bool = False):
     (1,000,000 atoms at n=50)."""
     lat = lattice_spec(n, n, n, (0, 0, 0), seed, alloy_fraction=0.3, strain_amp=0.02)
     return lat, draw_tb_params(seed, SP3D5S, 2)
+
+
+# Delta-doped Si ------------------------------------------------------------------------------
+# First seeded sp3d5s* Si draw with a bulk gap >= 0.5 eV, found by
+# tests/golden/make_gapped_si_params.py (stored in tests/golden/gapped_si_params.json).
+GAPPED_SI_SEED = 163
+GAPPED_SI_EV, GAPPED_SI_EC = -2.627017511981574, -1.6808215901542354
+Q_E = 1.602176634e-19
+
+
+def gapped_si_params() -> TBParams:
+    return draw_tb_params(GAPPED_SI_SEED, SP3D5S, 1)
+
+
+def draw_doping(seed: int, ns_range=(1e13, 2e14), w_range=(0.5, 2.0)):
+    """Sheet density N_s (cm^-2, log-uniform) and FWHM w (nm, uniform), stream 6."""
+    g = rng(seed, STREAM_DOPING)
+    ns = 10 ** g.uniform(np.log10(ns_range[0]), np.log10(ns_range[1]))
+    w = g.uniform(*w_range)
+    return float(ns), float(w)
+
+
+def donor_rho_on_grid(ns_cm2, fwhm_nm, nx, ny, nz, Lz_nm, z0_nm=None):
+    """Laterally uniform Gaussian sheet of ionised donors, charge density (C/m^3) on the
+    interior grid planes z_k = k Lz/nz, k = 1..nz-1, normalised so that sum_k rho_k h_z equals
+    e N_s exactly (shape (nz-1, ny, nx))."""
+    z0 = 0.5 * Lz_nm if z0_nm is None else z0_nm
+    hz = Lz_nm / nz
+    z = np.arange(1, nz) * hz
+    s = fwhm_nm / (2.0 * np.sqrt(2.0 * np.log(2.0)))
+    prof = np.exp(-0.5 * ((z - z0) / s) ** 2)
+    prof /= prof.sum() * hz * 1e-9                       # 1/m
+    rho_z = Q_E * ns_cm2 * 1e4 * prof                    # C/m^3
+    return np.broadcast_to(rho_z[:, None, None], (nz - 1, ny, nx)).copy()
+
+
+def delta_layer(nxy: int, nz_cells: int, seed: int = 5):
+    """Si slab of nxy x nxy x nz_cells cells, periodic with a Bloch phase in x and y, hard walls
+    in z, gapped sp3d5s* Si parameters; returns (spec, params, (N_s, w))."""
+    spec = lattice_spec(nxy, nxy, nz_cells, (2, 2, 0), seed)
+    return spec, gapped_si_params(), draw_doping(seed)

@@ -1,0 +1,83 @@
+"""Parity of the Schrödinger–Poisson pieces on the GPU against the oracle.
+
+Poisson CG against the oracle's sparse direct solve (1e-10 of max |phi|, including the
+11 x 11 x 217 grid of the 4x4x80-cell delta layer); cloud-in-cell deposit and gather
+(1e-12 relative); electrons per atom from eigenvectors; Fermi level; and the full
+self-consistent loop against the oracle loop (converged potentials within 1e-6 V).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import charge, poisson, scf  # noqa: E402
+from test_oracle_scf import small_delta_case  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1003_4570_gb300 import omen
+    return omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.mark.parametrize("dims", [(11, 11, 217, 2.1724, 2.1724, 43.448), (5, 3, 40, 1.0, 0.7, 8.0), (1, 1, 9, 0.5, 0.5, 3.0)])
+def test_poisson_cg_matches_direct(ctx, dims):
+    from paper_1003_4570_gb300 import omen
+    g = poisson.Grid(*dims)
+    rho = np.random.default_rng(3).normal(size=g.shape) * 1e6
+    ref = poisson.solve_direct(g, rho)
+    phi = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    info = omen.omen_poisson(ctx, g, torch.from_numpy(rho).cuda(), phi, rtol=1e-13)
+    assert info["converged"] == 1
+    np.testing.assert_allclose(phi.cpu().numpy(), ref, atol=1e-10 * np.abs(ref).max(), rtol=0)
+
+
+def test_deposit_gather_density_fermi(ctx):
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(2, 3, 4, (2, 2, 0), seed=9)
+    a = spec.a_nm
+    g = poisson.Grid(5, 7, 21, 2 * a, 3 * a, 4 * a)
+    lat = omen.omen_build_lattice(ctx, spec)
+    pos = scf.atom_positions_nm(spec)
+    q = np.random.default_rng(1).normal(size=spec.natoms) * 1e-19
+    rho = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+    omen.omen_deposit(ctx, lat, g, torch.from_numpy(q).cuda(), rho)
+    ref = charge.deposit(g, pos, q)
+    np.testing.assert_allclose(rho.cpu().numpy(), ref, atol=1e-12 * np.abs(ref).max(), rtol=0)
+    phi = np.random.default_rng(2).normal(size=g.shape)
+    out = torch.empty(spec.natoms, dtype=torch.float64, device="cuda")
+    omen.omen_gather(ctx, lat, g, torch.from_numpy(phi).cuda(), out)
+    np.testing.assert_allclose(out.cpu().numpy(), charge.gather(g, phi, pos), atol=1e-12, rtol=0)
+    # electrons per atom from complex eigenvector-like columns
+    p = synth.draw_tb_params(9, 10, 1)
+    ham = omen.omen_assemble_H(ctx, lat, p, k=(0.3, 0.1, 0.0))
+    rng = np.random.default_rng(4)
+    psi = rng.normal(size=(3, ham.nrows)) + 1j * rng.normal(size=(3, ham.nrows))
+    occ = np.array([1.0, 0.5, 0.0])
+    n = torch.zeros(spec.natoms, dtype=torch.float64, device="cuda")
+    omen.omen_density_accum(ctx, ham, torch.from_numpy(psi).cuda(), 3, occ, 2.0, n)
+    np.testing.assert_allclose(n.cpu().numpy(), 2.0 * charge.atom_density(psi.T, occ, spec.natoms), rtol=1e-13)
+    E = np.sort(rng.uniform(-1, 1, 40))
+    W = rng.uniform(0.5, 2, 40)
+    ef = omen.omen_fermi_level(E, W, 13.7, 0.01)
+    assert abs((W * charge.fermi(E, ef, 0.01)).sum() - 13.7) < 1e-9
+
+
+def test_scf_matches_oracle(ctx):
+    from paper_1003_4570_gb300 import omen
+    c = small_delta_case()
+    phi_ref, info_ref = scf.scf(c["spec"], c["params"], c["grid"], c["donor_rho"], c["n_electrons"], c["kT"],
+                                c["kpts"], c["kweights"], c["nev"], c["sigma"], c["e_cut"], mix=0.3, tol_V=1e-6,
+                                max_iter=200)
+    lat = omen.omen_build_lattice(ctx, c["spec"])
+    phi = torch.zeros(c["grid"].shape, dtype=torch.float64, device="cuda")
+    info, st = omen.omen_scf(ctx, lat, c["params"], c["grid"], phi, torch.from_numpy(c["donor_rho"]).cuda(),
+                             c["n_electrons"], c["kT"], c["kpts"], c["kweights"], c["nev"], c["sigma"], c["e_cut"],
+                             eig_tol=1e-10, eig_block=4, eig_basis=48, mix=0.3, tol_V=1e-6, max_iter=200)
+    assert info["converged"] == 1, info
+    assert abs(info["iterations"] - info_ref["iterations"]) <= 1
+    np.testing.assert_allclose(phi.cpu().numpy(), phi_ref, atol=1e-6, rtol=0)
+    assert abs(info["E_F"] - info_ref["E_F"]) < 1e-6
