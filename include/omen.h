@@ -203,6 +203,28 @@ typedef struct {
 omen_status omen_poisson(omen_ctx* ctx, const omen_grid* grid, const double* rho_dev, double* phi_dev,
                          const omen_cg_opts* opts, omen_solve_info* info);
 
+/* The same solve for callers that must not allocate device memory (the paper has no
+ * counterpart).  Some applications own all device memory through their own allocator, or
+ * forbid any allocation once their run has started, so a library may not call cudaMalloc
+ * behind their back.  This entry point allocates nothing: its CG work vectors live in one
+ * statically sized device array that every GPU loading the library holds until the process
+ * exits (OMEN_POISSON_STATIC_MAX_UNKNOWNS unknowns, about 6.4 MB).  The caller still passes
+ * rho_dev and phi_dev (initial guess in, solution out) and the stream to work on; the
+ * current device is used.
+ *  - The first call on a device looks up the array's device address once (with that device
+ *    current); make that first call before any stream capture.
+ *  - Grids with more than OMEN_POISSON_STATIC_MAX_UNKNOWNS interior unknowns
+ *    (nx*ny*(nz-1)) are rejected with OMEN_EINVAL; other argument errors also return
+ *    OMEN_EINVAL, CUDA failures OMEN_ECUDA, hitting max_iter OMEN_ENOCONV.  No message
+ *    is recorded (there is no context).
+ *  - All calls share the one array, which keeps the last call's contents; every word is
+ *    written before it is read, so nothing carries over.  Calls whose work overlaps on the
+ *    GPU (other streams or threads) race on the array and must be serialised by the caller.
+ *  - The call waits for its stream before returning (it reads the iteration count back). */
+#define OMEN_POISSON_STATIC_MAX_UNKNOWNS 262144
+omen_status omen_poisson_static(const omen_grid* grid, const double* rho_dev, double* phi_dev,
+                                const omen_cg_opts* opts, omen_solve_info* info, void* cuda_stream);
+
 /* n_atom_dev[i] += weight * sum_n occ_host[n] * sum_o |psi_n(o*natoms + i)|^2 for nstates FP64
  * (double or complex128) vectors psi_dev [nstates][nrows] of ham (paper: charge from the
  * filled states, Section III-A item 2). */

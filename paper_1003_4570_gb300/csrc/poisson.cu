@@ -8,8 +8,10 @@
 // the same order, so all blocks see bit-identical scalars and leave the loop together.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 
 #include "omen_internal.h"
 
@@ -196,4 +198,103 @@ extern "C" omen_status omen_poisson(omen_ctx* ctx, const omen_grid* gr, const do
   }
   if (!ho.converged) return set_err(ctx, OMEN_ENOCONV, "CG stopped at %d iterations, relative residual %.3e", ho.iterations, ho.rel);
   return OMEN_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Poisson solve that allocates nothing.
+//
+// Some host programs cannot let a library call cudaMalloc: the application may have reserved
+// the device memory for its own allocator up front, or its rules forbid allocation once the
+// solve loop is running (a fixed memory budget checked at start-up, a plugin sandbox).  For
+// them the CG work vectors live in the statically sized device array below instead.  Every
+// GPU that loads this library holds the array (about 6.4 MB) until the process exits.
+// The array's name in host code is only a host-side stand-in for the symbol, so the device
+// address is looked up with cudaGetSymbolAddress, once per device, with that device current,
+// the first time the entry point runs there.
+static constexpr long long kStaticMaxUnknowns = 1ll << 18;   // nx*ny*(nz-1) limit
+static constexpr int kStaticMaxBlocks = 4096;
+static constexpr long long kStaticWords = 3 * kStaticMaxUnknowns + 3 * kStaticMaxBlocks + 8;
+static __device__ __align__(256) double g_poisson_scratch[kStaticWords];
+
+static std::mutex g_scratch_mu;
+static double* g_scratch_addr[128] = {};
+
+static omen_status scratch_address(int dev, double** out) {
+  if (dev < 0 || dev >= 128) return OMEN_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_poisson_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return OMEN_ECUDA;
+    }
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return OMEN_OK;
+}
+
+extern "C" omen_status omen_poisson_static(const omen_grid* gr, const double* rho, double* phi,
+                                           const omen_cg_opts* o, omen_solve_info* info, void* cuda_stream) {
+  if (!gr || !rho || !phi || !o) return OMEN_EINVAL;
+  if (gr->nx < 1 || gr->ny < 1 || gr->nz < 2) return OMEN_EINVAL;
+  if (!(gr->Lx_nm > 0 && gr->Ly_nm > 0 && gr->Lz_nm > 0 && gr->eps_r > 0)) return OMEN_EINVAL;
+  if (!(o->rtol > 0) || o->max_iter < 1) return OMEN_EINVAL;
+  const long long n = (long long)gr->nx * gr->ny * (gr->nz - 1);
+  if (n > kStaticMaxUnknowns) return OMEN_EINVAL;   // grid larger than the static work area
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  auto t0 = std::chrono::steady_clock::now();
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return OMEN_ECUDA;
+  }
+  double* base = nullptr;
+  const omen_status s = scratch_address(dev, &base);
+  if (s != OMEN_OK) return s;
+  PGrid g;
+  g.nx = gr->nx;
+  g.ny = gr->ny;
+  g.nzi = gr->nz - 1;
+  const double hx = gr->Lx_nm / gr->nx * 1e-9, hy = gr->Ly_nm / gr->ny * 1e-9, hz = gr->Lz_nm / gr->nz * 1e-9;
+  g.cx = gr->nx > 1 ? 1.0 / (hx * hx) : 0.0;
+  g.cy = gr->ny > 1 ? 1.0 / (hy * hy) : 0.0;
+  g.cz = 1.0 / (hz * hz);
+  g.n = n;
+  int sms = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return OMEN_ECUDA;
+  }
+  long long want = (n + 255) / 256;
+  int blocks = (int)std::min<long long>(want, (long long)sms * std::max(1, per_sm));
+  blocks = std::max(1, std::min(blocks, kStaticMaxBlocks));
+  // every word of the work area is written by the kernel before it is read, so nothing has
+  // to be cleared between calls
+  double* r = base;
+  double* p = r + kStaticMaxUnknowns;
+  double* q = p + kStaticMaxUnknowns;
+  double* part = q + kStaticMaxUnknowns;
+  CGOut* out = reinterpret_cast<CGOut*>(part + 3 * kStaticMaxBlocks);
+  double scale = 1.0 / (kEps0 * gr->eps_r);
+  double rtol = o->rtol;
+  int max_iter = o->max_iter;
+  void* args[] = {&g, &rho, &scale, &phi, &r, &p, &q, &part, &rtol, &max_iter, &out};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(blocks), dim3(256), args, 0, stream);
+  CGOut ho{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ho, out, sizeof(CGOut), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return OMEN_ECUDA;
+  }
+  if (info) {
+    info->iterations = ho.iterations;
+    info->converged = ho.converged;
+    info->rel_residual = ho.rel;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return ho.converged ? OMEN_OK : OMEN_ENOCONV;
 }
