@@ -58,7 +58,7 @@ enum {
                             eigenproblem in FP64 */
   OMEN_F32_REFINE64 = 2  /* OMEN_F32 solve, then an FP64 Rayleigh–Ritz refinement */
 };
-enum { OMEN_LOWEST = 0, OMEN_NEAREST = 1 };                  /* which eigenvalues */
+enum { OMEN_LOWEST = 0, OMEN_NEAREST = 1, OMEN_HIGHEST = 2 };  /* which eigenvalues */
 
 typedef struct omen_ctx omen_ctx;
 typedef struct omen_lattice omen_lattice;
@@ -142,8 +142,9 @@ omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* ham, const void* x_host,
 
 typedef struct {
   int nev;                   /* wanted eigenpairs (>= 1) */
-  int which;                 /* OMEN_LOWEST, or OMEN_NEAREST (folded spectrum: Lanczos on
-                                (H - sigma)^2, eigenvalues by Rayleigh quotients on H) */
+  int which;                 /* OMEN_LOWEST, OMEN_HIGHEST (Lanczos on -H), or OMEN_NEAREST
+                                (folded spectrum: Lanczos on (H - sigma)^2, eigenvalues by
+                                Rayleigh quotients on H) */
   double sigma;              /* shift for OMEN_NEAREST (eV) */
   double tol;                /* target bound on each eigenvalue's error (eV), from its FP64
                                 residual r: min(r, r^2/gap) (Weyl / Kato–Temple) */
@@ -152,6 +153,8 @@ typedef struct {
   int basis;                 /* maximum basis size m (a multiple of b, > nev + b) */
   const void* v0_host;       /* [block][nrows] start block in the vector type of the
                                 Hamiltonian's precision, or NULL for a fixed default */
+  const void* v0_dev;        /* the same on the device (takes precedence over v0_host), e.g.
+                                a combination of the previous solve's eigenvectors */
 } omen_eig_opts;
 
 typedef struct {

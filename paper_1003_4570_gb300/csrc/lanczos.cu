@@ -17,6 +17,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "dense_eig.h"
@@ -111,6 +112,179 @@ __global__ void reduce_partial_kernel(const double2* __restrict__ P, int nchunks
   }
 }
 
+// Projections onto one vector, P[chunk][i] = sum_r conj(A_i[r]) b[r], for the common case of a
+// single right-hand vector.  CTA (g, c) handles basis vectors 16g..16g+15 over row chunk c;
+// each thread keeps 16 independent loads in flight per row.  Consecutive CTAs share a chunk,
+// so b stays in L2 across the basis groups.  FP64 vectors accumulate in FP64; FP32 vectors
+// accumulate each thread's rows in compensated FP32 (Kahan) before the FP64 block sum.
+static constexpr int kIG = 16;
+template <typename T, bool C>
+__global__ void __launch_bounds__(256) dots1_kernel(const void* Av, long long lda, int na, const void* Bv,
+                                                    long long n, int rows_per_cta, double2* __restrict__ P) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  using Acc = std::conditional_t<sizeof(T) == 8, double, float>;
+  const V* A = static_cast<const V*>(Av);
+  const V* B = static_cast<const V*>(Bv);
+  const int i0 = blockIdx.x * kIG;
+  const int ni = min(kIG, na - i0);
+  const long long r0 = (long long)blockIdx.y * rows_per_cta;
+  const long long r1 = min(n, r0 + rows_per_cta);
+  Acc sr[kIG], si[kIG], cr[kIG], ci[kIG];
+#pragma unroll
+  for (int i = 0; i < kIG; ++i) { sr[i] = 0; si[i] = 0; cr[i] = 0; ci[i] = 0; }
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const V bv = B[r];
+    V av[kIG];
+#pragma unroll
+    for (int i = 0; i < kIG; ++i)
+      if (i < ni) av[i] = A[(size_t)(i0 + i) * lda + r];
+#pragma unroll
+    for (int i = 0; i < kIG; ++i) {
+      if (i < ni) {
+        Acc pr, pi = 0;
+        if constexpr (C) {
+          pr = (Acc)av[i].x * (Acc)bv.x + (Acc)av[i].y * (Acc)bv.y;
+          pi = (Acc)av[i].x * (Acc)bv.y - (Acc)av[i].y * (Acc)bv.x;
+        } else {
+          pr = (Acc)av[i] * (Acc)bv;
+        }
+        if constexpr (sizeof(T) == 8) {
+          sr[i] += pr;
+          si[i] += pi;
+        } else {  // Kahan-compensated FP32 sums
+          const Acc yr = pr - cr[i], tr = sr[i] + yr;
+          cr[i] = (tr - sr[i]) - yr;
+          sr[i] = tr;
+          const Acc yi = pi - ci[i], ti = si[i] + yi;
+          ci[i] = (ti - si[i]) - yi;
+          si[i] = ti;
+        }
+      }
+    }
+  }
+  __shared__ double red[8][kIG][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kIG; ++i) {
+    double vr = (double)sr[i] - (double)cr[i], vi = (double)si[i] - (double)ci[i];
+    for (int o = 16; o > 0; o >>= 1) {
+      vr += __shfl_xor_sync(0xffffffffu, vr, o);
+      if constexpr (C) vi += __shfl_xor_sync(0xffffffffu, vi, o);
+    }
+    if (lane == 0) { red[warp][i][0] = vr; red[warp][i][1] = vi; }
+  }
+  __syncthreads();
+  if (threadIdx.x < ni) {
+    double vr = 0.0, vi = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { vr += red[w][threadIdx.x][0]; vi += red[w][threadIdx.x][1]; }
+    P[(size_t)blockIdx.y * na + i0 + threadIdx.x] = make_double2(vr, C ? vi : 0.0);
+  }
+}
+
+// y = beta*y + alpha * sum_i A_i m_i for one output vector, 8 basis loads in flight per row.
+template <typename T, bool C>
+__global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M,
+                                                       void* Yv, long long n, double alpha, double beta) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Ms = reinterpret_cast<double2*>(smem_raw);
+  for (int t = threadIdx.x; t < na; t += blockDim.x) Ms[t] = M[t];
+  __syncthreads();
+  const V* A = static_cast<const V*>(Av);
+  V* Y = static_cast<V*>(Yv);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double yr = 0.0, yi = 0.0;
+    int i = 0;
+    for (; i + 8 <= na; i += 8) {
+      V av[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) av[k] = A[(size_t)(i + k) * lda + r];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const double2 m = Ms[i + k];
+        const double xr = E::re(av[k]), xi = E::im(av[k]);
+        yr = fma(xr, m.x, yr);
+        if constexpr (C) {
+          yr = fma(-xi, m.y, yr);
+          yi = fma(xr, m.y, yi);
+          yi = fma(xi, m.x, yi);
+        }
+      }
+    }
+    for (; i < na; ++i) {
+      const V a = A[(size_t)i * lda + r];
+      const double2 m = Ms[i];
+      const double xr = E::re(a), xi = E::im(a);
+      yr = fma(xr, m.x, yr);
+      if constexpr (C) {
+        yr = fma(-xi, m.y, yr);
+        yi = fma(xr, m.y, yi);
+        yi = fma(xi, m.x, yi);
+      }
+    }
+    double orr = alpha * yr, oi = alpha * yi;
+    if (beta != 0.0) {
+      orr += beta * E::re(Y[r]);
+      oi += beta * E::im(Y[r]);
+    }
+    Y[r] = E::make(orr, oi);
+  }
+}
+
+// Device-side reduction of the partials into out (na x nb, column-major) and, optionally,
+// into columns col0.. of the projected matrix T (ldT x ldT, column-major).
+__global__ void reduce_dev_kernel(const double2* __restrict__ P, int nchunks, int na, int nb, double2* __restrict__ out,
+                                  double2* __restrict__ accT, int ldT, int col0) {
+  const int e = blockIdx.x;
+  const int count = na * nb;
+  double sr = 0.0, si = 0.0;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    const double2 v = P[(size_t)c * count + e];
+    sr += v.x;
+    si += v.y;
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sr = 0.0;
+    si = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += red[0][w]; si += red[1][w]; }
+    const int i = e / nb, j = e % nb;
+    out[i + (size_t)j * na] = make_double2(sr, si);
+    if (accT) {
+      double2* t = accT + i + (size_t)(col0 + j) * ldT;
+      t->x += sr;
+      t->y += si;
+    }
+  }
+}
+
+// V = W / ||W|| with ||W||^2 read from the device; the norm goes into T[row, col].
+template <typename T, bool C>
+__global__ void normalize_kernel(const void* Wv, void* Vv, long long n, const double2* __restrict__ nrm2,
+                                 double2* __restrict__ Tm, int ldT, int row, int col, int* __restrict__ flag) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  const double b = sqrt(fmax(nrm2->x, 0.0));
+  const double inv = (b > 1e-300) ? 1.0 / b : 0.0;
+  const V* W = static_cast<const V*>(Wv);
+  V* Vo = static_cast<V*>(Vv);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+    Vo[r] = E::make(E::re(W[r]) * inv, E::im(W[r]) * inv);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (Tm) Tm[row + (size_t)col * ldT] = make_double2(b, 0.0);
+    if (!(b > 1e-300) || !isfinite(b)) *flag = 1;
+  }
+}
+
 // Y_j[r] = beta * Y_j[r] + alpha * sum_i A_i[r] M[i + j*na]   (M complex FP64, column-major)
 template <typename T, bool C>
 __global__ void combine_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M, int nb,
@@ -127,18 +301,26 @@ __global__ void combine_kernel(const void* Av, long long lda, int na, const doub
     double yr[kMaxBlockCols], yi[kMaxBlockCols];
 #pragma unroll
     for (int j = 0; j < kMaxBlockCols; ++j) { yr[j] = 0.0; yi[j] = 0.0; }
-    for (int i = 0; i < na; ++i) {
-      const V a = A[i * lda + r];
-      const double xr = E::re(a), xi = E::im(a);
+    for (int i0 = 0; i0 < na; i0 += 4) {
+      V av[4];
 #pragma unroll
-      for (int j = 0; j < kMaxBlockCols; ++j) {
-        if (j < nb) {
-          const double2 m = Ms[i + j * na];
-          yr[j] = fma(xr, m.x, yr[j]);
-          if constexpr (C) {
-            yr[j] = fma(-xi, m.y, yr[j]);
-            yi[j] = fma(xr, m.y, yi[j]);
-            yi[j] = fma(xi, m.x, yi[j]);
+      for (int k = 0; k < 4; ++k)
+        if (i0 + k < na) av[k] = A[(size_t)(i0 + k) * lda + r];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (i0 + k >= na) break;
+        const int i = i0 + k;
+        const double xr = E::re(av[k]), xi = E::im(av[k]);
+#pragma unroll
+        for (int j = 0; j < kMaxBlockCols; ++j) {
+          if (j < nb) {
+            const double2 m = Ms[i + j * na];
+            yr[j] = fma(xr, m.x, yr[j]);
+            if constexpr (C) {
+              yr[j] = fma(-xi, m.y, yr[j]);
+              yi[j] = fma(xr, m.y, yi[j]);
+              yi[j] = fma(xi, m.x, yi[j]);
+            }
           }
         }
       }
@@ -231,6 +413,16 @@ struct KrylovOps {
   // out (host, na x nb column-major complex) = A^H B   (A: na columns, B: nb columns)
   omen_status dots(const void* A, int na, const void* B, int nb, std::vector<cd>& out) {
     out.assign((size_t)na * nb, cd(0));
+    if (nb == 1 && (size_t)na <= small_cap) {
+      omen_status s1 = dots_dev(A, na, B, 1, d_small, nullptr, 0, 0);
+      if (s1 != OMEN_OK) return s1;
+      OMEN_CUDA(ctx, cudaMemcpyAsync(out.data(), d_small, na * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      for (const cd& v : out)
+        if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+          return set_err(ctx, OMEN_ENUMERIC, "non-finite value in a Krylov inner product");
+      return OMEN_OK;
+    }
     for (int j0 = 0; j0 < nb; j0 += kMaxBlockCols) {
       const int nbj = std::min(kMaxBlockCols, nb - j0);
       const int CH = chunk_rows(nbj);
@@ -301,6 +493,105 @@ struct KrylovOps {
     return OMEN_OK;
   }
 
+  omen_status ensure_partial(size_t need) {
+    if (need <= partial_cap) return OMEN_OK;
+    cudaFree(d_partial);
+    d_partial = nullptr;
+    partial_cap = 0;
+    if (cudaMalloc(&d_partial, need * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, OMEN_ENOMEM, "partial-sum buffer");
+    }
+    partial_cap = need;
+    return OMEN_OK;
+  }
+
+  // out_dev (na x nb, column-major) = A^H B on the device, optionally added into T columns;
+  // nothing is copied to the host and the stream is not synchronised.
+  omen_status dots_dev(const void* A, int na, const void* B, int nb, double2* out_dev, double2* accT, int ldT, int col0) {
+    if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "dots_dev: too many columns");
+    if (nb == 1) {
+      int rows = 8192;
+      while ((n + rows - 1) / rows > 65535) rows *= 2;
+      const long long nchunks = (n + rows - 1) / rows;
+      omen_status s1 = ensure_partial((size_t)nchunks * na);
+      if (s1 != OMEN_OK) return s1;
+      dim3 grid((na + kIG - 1) / kIG, (unsigned)nchunks);
+      if (prec == OMEN_F64) {
+        if (cplx) dots1_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
+        else dots1_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
+      } else {
+        if (cplx) dots1_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
+        else dots1_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
+      }
+      reduce_dev_kernel<<<na, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, 1, out_dev, accT, ldT, col0);
+      OMEN_CHECK_LAUNCH(ctx);
+      return OMEN_OK;
+    }
+    const int CH = chunk_rows(nb);
+    const long long nchunks = (n + CH - 1) / CH;
+    omen_status s = ensure_partial((size_t)nchunks * na * nb);
+    if (s != OMEN_OK) return s;
+    const size_t shm = (size_t)nb * CH * el;
+#define DOTS_LAUNCH2(T, Cc)                                                                         \
+  do {                                                                                              \
+    cudaFuncSetAttribute(dots_partial_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+    dots_partial_kernel<T, Cc><<<(unsigned)nchunks, kDotThreads, shm, ctx->stream>>>(A, n, na, B, n, nb, n, CH, d_partial); \
+  } while (0)
+    if (prec == OMEN_F64) { if (cplx) DOTS_LAUNCH2(double, true); else DOTS_LAUNCH2(double, false); }
+    else { if (cplx) DOTS_LAUNCH2(float, true); else DOTS_LAUNCH2(float, false); }
+#undef DOTS_LAUNCH2
+    reduce_dev_kernel<<<na * nb, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, nb, out_dev, accT, ldT, col0);
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+
+  // Y = beta*Y + alpha * A M with M (na x nb, column-major) already on the device
+  omen_status combine_dev(const void* A, int na, const double2* M_dev, int nb, void* Y, double alpha, double beta) {
+    if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "combine_dev: too many columns");
+    if (nb == 1) {
+      const size_t shm1 = (size_t)na * sizeof(double2);
+      const unsigned grid1 = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+#define COMB1(T, Cc)                                                                                  \
+  do {                                                                                                \
+    if (shm1 > 48 * 1024)                                                                              \
+      cudaFuncSetAttribute(combine1_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm1); \
+    combine1_kernel<T, Cc><<<grid1, 256, shm1, ctx->stream>>>(A, n, na, M_dev, Y, n, alpha, beta);       \
+  } while (0)
+      if (prec == OMEN_F64) { if (cplx) COMB1(double, true); else COMB1(double, false); }
+      else { if (cplx) COMB1(float, true); else COMB1(float, false); }
+#undef COMB1
+      OMEN_CHECK_LAUNCH(ctx);
+      return OMEN_OK;
+    }
+    const size_t shm = (size_t)na * nb * sizeof(double2);
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+#define COMB_LAUNCH2(T, Cc)                                                                          \
+  do {                                                                                               \
+    cudaFuncSetAttribute(combine_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+    combine_kernel<T, Cc><<<grid, 256, shm, ctx->stream>>>(A, n, na, M_dev, nb, Y, n, n, alpha, beta); \
+  } while (0)
+    if (prec == OMEN_F64) { if (cplx) COMB_LAUNCH2(double, true); else COMB_LAUNCH2(double, false); }
+    else { if (cplx) COMB_LAUNCH2(float, true); else COMB_LAUNCH2(float, false); }
+#undef COMB_LAUNCH2
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+
+  omen_status normalize_dev(const void* W, void* V, const double2* nrm2, double2* Tm, int ldT, int row, int col) {
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+    int* flag = ctx->d_status + 1;
+    if (prec == OMEN_F64) {
+      if (cplx) normalize_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(W, V, n, nrm2, Tm, ldT, row, col, flag);
+      else normalize_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(W, V, n, nrm2, Tm, ldT, row, col, flag);
+    } else {
+      if (cplx) normalize_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(W, V, n, nrm2, Tm, ldT, row, col, flag);
+      else normalize_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(W, V, n, nrm2, Tm, ldT, row, col, flag);
+    }
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+
   omen_status random_fill(void* X, int ncols, unsigned long long seed) {
     const long long total = n * ncols;
     const unsigned grid = (unsigned)std::min<long long>((total + 255) / 256, (long long)sm_count * 8);
@@ -316,10 +607,18 @@ struct KrylovOps {
   }
 
   // operator: W = A X, A = H (folded = false) or (H - sigma)^2
+  bool negate = false;   // operator -H (highest eigenvalues)
+
   omen_status apply(const void* X, void* W, void* tmp, int nb, bool folded, double sigma, long long& count) {
     if (!folded) {
       count += nb;
-      return launch_hx(ctx, ham, X, W, nb, 0.0, prec);
+      omen_status s = launch_hx(ctx, ham, X, W, nb, 0.0, prec);
+      if (s != OMEN_OK || !negate) return s;
+      std::vector<cd> m1((size_t)nb * nb, cd(0));
+      for (int j = 0; j < nb; ++j) m1[j + (size_t)j * nb] = cd(-1.0);
+      // W = -W via a copy: W <- 0*W + (-1) * tmp where tmp holds H X
+      OMEN_CUDA(ctx, cudaMemcpyAsync(tmp, W, (size_t)nb * n * el, cudaMemcpyDeviceToDevice, ctx->stream));
+      return combine(tmp, nb, m1, nb, W, 1.0, 0.0);
     }
     omen_status s = launch_hx(ctx, ham, X, tmp, nb, sigma, prec);
     if (s != OMEN_OK) return s;
@@ -402,6 +701,8 @@ struct KrylovOps {
 };
 
 // ---------------------------------------------------------------------------------------
+static int max_iter_of(const omen_eig_opts* o) { return o->max_iter; }
+
 struct RitzResult {
   std::vector<double> lam;   // eigenvalues of H (ascending)
   std::vector<double> res;   // FP64 ||H x - lam x||
@@ -475,7 +776,9 @@ static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X,
   void* W = Wb.p;
   void* tmp = Tb.p;
   // start block
-  if (v0_host) {
+  if (o->v0_dev) {
+    OMEN_CUDA(ctx, cudaMemcpyAsync(V, o->v0_dev, (size_t)b * vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else if (v0_host) {
     OMEN_CUDA(ctx, cudaMemcpyAsync(V, v0_host, (size_t)b * vbytes, cudaMemcpyHostToDevice, ctx->stream));
   } else {
     omen_status s = op.random_fill(V, b, 0x5EEDull);
@@ -650,6 +953,180 @@ static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X,
   return OMEN_OK;
 }
 
+// Single-vector thick-restart Lanczos with the recurrence kept on the device: the
+// projection coefficients accumulate into a device copy of T and the norm of the new
+// direction is applied from device memory, so a step issues kernels only and the host
+// synchronises once per convergence check (every few steps / at each restart).
+static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, void* X, int k_out,
+                                        omen_eig_info* info, bool& converged) {
+  omen_ctx* ctx = op.ctx;
+  const int m = o->basis;
+  const bool folded = (o->which == OMEN_NEAREST);
+  const size_t vbytes = (size_t)op.n * op.el;
+  const int ldT = m + 1;
+  DevBuf Vb, Wb, Tb, Xb, Td, Hd;
+  if (cudaMalloc(&Vb.p, (size_t)(m + 1) * vbytes) != cudaSuccess || cudaMalloc(&Wb.p, vbytes) != cudaSuccess ||
+      cudaMalloc(&Tb.p, std::max<size_t>(1, k_out) * vbytes) != cudaSuccess ||
+      cudaMalloc(&Xb.p, (size_t)m * vbytes) != cudaSuccess ||
+      cudaMalloc(&Td.p, sizeof(double2) * ldT * ldT) != cudaSuccess ||
+      cudaMalloc(&Hd.p, sizeof(double2) * (ldT + 2)) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, OMEN_ENOMEM, "Lanczos basis (%d vectors of %lld rows)", m + 1, op.n);
+  }
+  void* V = Vb.p;
+  void* W = Wb.p;
+  void* tmp = Tb.p;
+  double2* dT = static_cast<double2*>(Td.p);
+  double2* dh = static_cast<double2*>(Hd.p);
+  double2* dn = dh + ldT;
+  OMEN_CUDA(ctx, cudaMemsetAsync(dT, 0, sizeof(double2) * ldT * ldT, ctx->stream));
+  OMEN_CUDA(ctx, cudaMemsetAsync(ctx->d_status + 1, 0, sizeof(int), ctx->stream));
+  if (o->v0_dev) {
+    OMEN_CUDA(ctx, cudaMemcpyAsync(W, o->v0_dev, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else if (o->v0_host) {
+    OMEN_CUDA(ctx, cudaMemcpyAsync(W, o->v0_host, vbytes, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    omen_status s = op.random_fill(W, 1, 0x5EEDull);
+    if (s != OMEN_OK) return s;
+  }
+  omen_status s = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
+  if (s != OMEN_OK) return s;
+  s = op.normalize_dev(W, V, dn, nullptr, 0, 0, 0);
+  if (s != OMEN_OK) return s;
+
+  std::vector<cd> Th((size_t)ldT * ldT);
+  int jstart = 0, nbas = 1;
+  long long hx = 0;
+  int iter = 0, restarts = 0, since_check = 0;
+  const int check_every = std::max(4, std::min(32, m / 4));
+  double gateA = -1.0;
+  converged = false;
+  std::vector<double> theta;
+  std::vector<cd> Y;
+  auto t_start = std::chrono::steady_clock::now();
+  while (true) {
+    s = op.apply(op.col(V, jstart), W, tmp, 1, folded, o->sigma, hx);
+    if (s != OMEN_OK) return s;
+    for (int pass = 0; pass < 2; ++pass) {
+      s = op.dots_dev(V, nbas, W, 1, dh, dT, ldT, jstart);
+      if (s != OMEN_OK) return s;
+      s = op.combine_dev(V, nbas, dh, 1, W, -1.0, 1.0);
+      if (s != OMEN_OK) return s;
+    }
+    s = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
+    if (s != OMEN_OK) return s;
+    s = op.normalize_dev(W, op.col(V, nbas), dn, dT, ldT, nbas, jstart);
+    if (s != OMEN_OK) return s;
+    ++iter;
+    ++since_check;
+    const bool full = nbas + 1 > m;
+    const bool check = full || iter >= max_iter_of(o) || (since_check >= check_every && nbas >= o->nev + 1);
+    if (check && nbas >= o->nev) {
+      since_check = 0;
+      OMEN_CUDA(ctx, cudaMemcpyAsync(Th.data(), dT, sizeof(double2) * ldT * ldT, cudaMemcpyDeviceToHost, ctx->stream));
+      int flag = 0;
+      OMEN_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->d_status + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      if (flag) return set_err(ctx, OMEN_ENUMERIC, "Lanczos breakdown or non-finite value (zero or NaN norm)");
+      // Hermitian projected matrix from the column data (row i <= column j)
+      std::vector<cd> Tn((size_t)nbas * nbas);
+      for (int j = 0; j < nbas; ++j)
+        for (int i = 0; i <= j; ++i) {
+          cd v = Th[i + (size_t)j * ldT];
+          if (i == j) v = cd(std::real(v), 0.0);
+          Tn[i + (size_t)j * nbas] = v;
+          Tn[j + (size_t)i * nbas] = std::conj(v);
+        }
+      for (const cd& v : Tn)
+        if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return set_err(ctx, OMEN_ENUMERIC, "non-finite projected matrix");
+      const double beta = std::real(Th[nbas + (size_t)jstart * ldT]);
+      theta.assign(nbas, 0.0);
+      Y.assign((size_t)nbas * nbas, cd(0));
+      if (hermitian_eig(nbas, Tn.data(), theta.data(), Y.data()))
+        return set_err(ctx, OMEN_ENUMERIC, "projected eigenproblem did not converge");
+      std::vector<double> resA(nbas);
+      for (int i = 0; i < nbas; ++i) resA[i] = std::fabs(beta) * std::abs(Y[jstart + (size_t)i * nbas]);
+      const int nev = o->nev;
+      bool done = false;
+      if (!folded) {
+        std::vector<double> lam(theta.begin(), theta.begin() + nev), res(resA.begin(), resA.begin() + nev), bd;
+        error_bounds(theta, lam, res, bd);
+        done = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+      } else {
+        const double rmax = *std::max_element(resA.begin(), resA.begin() + nev);
+        if (gateA < 0) gateA = std::max(o->tol, 1e-12) * 1e3;
+        if (rmax <= gateA || iter >= max_iter_of(o)) {
+          const int kc = std::min(nbas, nev + 1);
+          std::vector<cd> Yk((size_t)nbas * kc);
+          for (int j = 0; j < kc; ++j)
+            for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
+          s = op.combine(V, nbas, Yk, kc, Xb.p, 1.0, 0.0);
+          if (s != OMEN_OK) return s;
+          DevBuf HXb, Rb;
+          if (cudaMalloc(&HXb.p, (size_t)kc * vbytes) != cudaSuccess || cudaMalloc(&Rb.p, (size_t)kc * vbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(ctx, OMEN_ENOMEM, "Ritz check vectors");
+          }
+          s = launch_hx(ctx, op.ham, Xb.p, HXb.p, kc, 0.0, op.prec);
+          if (s != OMEN_OK) return s;
+          hx += kc;
+          std::vector<double> lamk, resk, bd;
+          s = rayleigh_residuals(op, Xb.p, HXb.p, Rb.p, kc, lamk, resk);
+          if (s != OMEN_OK) return s;
+          std::vector<double> lam(lamk.begin(), lamk.begin() + nev), res(resk.begin(), resk.begin() + nev);
+          error_bounds(lamk, lam, res, bd);
+          done = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+          if (!done) gateA = std::min(gateA, rmax) * 0.01;
+        }
+      }
+      if (done || iter >= max_iter_of(o)) {
+        converged = done;
+        break;
+      }
+      if (full) {
+        const int kk = std::min(m - 1, std::max(o->nev + 1, nbas / 2));
+        std::vector<cd> Yk((size_t)nbas * kk);
+        for (int j = 0; j < kk; ++j)
+          for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
+        s = op.combine(V, nbas, Yk, kk, Xb.p, 1.0, 0.0);
+        if (s != OMEN_OK) return s;
+        OMEN_CUDA(ctx, cudaMemcpyAsync(V, Xb.p, (size_t)kk * vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(V, kk), op.col(V, nbas), vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        std::fill(Th.begin(), Th.end(), cd(0));
+        for (int i = 0; i < kk; ++i) Th[i + (size_t)i * ldT] = theta[i];
+        for (int i = 0; i < kk; ++i) {
+          const cd c = beta * Y[jstart + (size_t)i * nbas];
+          Th[kk + (size_t)i * ldT] = c;
+          Th[i + (size_t)kk * ldT] = std::conj(c);
+        }
+        // column kk is accumulated again by the next projection: start it at zero
+        for (int i = 0; i <= kk; ++i) Th[i + (size_t)kk * ldT] = cd(0);
+        OMEN_CUDA(ctx, cudaMemcpyAsync(dT, Th.data(), sizeof(double2) * ldT * ldT, cudaMemcpyHostToDevice, ctx->stream));
+        OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        jstart = kk;
+        nbas = kk + 1;
+        ++restarts;
+        continue;
+      }
+    }
+    jstart = nbas;
+    nbas += 1;
+  }
+  const int kc = std::min(nbas, k_out);
+  std::vector<cd> Yk((size_t)nbas * kc);
+  for (int j = 0; j < kc; ++j)
+    for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
+  s = op.combine(V, nbas, Yk, kc, X, 1.0, 0.0);
+  if (s != OMEN_OK) return s;
+  if (info) {
+    info->iterations = iter;
+    info->hx_count = hx;
+    info->restarts = restarts;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return OMEN_OK;
+}
+
 // Sort the k columns of X (and HX) by the key and permute lam/res accordingly.
 static omen_status sort_columns(KrylovOps& op, void* X, int k, std::vector<double>& key, std::vector<double>* a1,
                                 std::vector<double>* a2) {
@@ -740,6 +1217,8 @@ static omen_status refine64(KrylovOps& op, void* X, int k, const omen_eig_opts* 
     for (int i = 0; i < ns; ++i) ord[i] = i;
     if (nearest)
       std::stable_sort(ord.begin(), ord.end(), [&](int a, int b2) { return std::fabs(w[a] - o->sigma) < std::fabs(w[b2] - o->sigma); });
+    else if (o->which == OMEN_HIGHEST)
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b2) { return w[a] > w[b2]; });
     std::vector<cd> Zk((size_t)ns * k);
     std::vector<int> pick(ord.begin(), ord.begin() + k);
     std::sort(pick.begin(), pick.end(), [&](int a, int b2) { return w[a] < w[b2]; });
@@ -758,6 +1237,30 @@ static omen_status refine64(KrylovOps& op, void* X, int k, const omen_eig_opts* 
   return OMEN_OK;
 }
 
+// out[j] = sum_n c_jn X[n], j < nout, with fixed pseudo-random coefficients c_jn in +-[0.5, 1]:
+// a start block that lies (nearly) in the span of the k given vectors, e.g. the eigenvectors
+// of the previous self-consistent iteration.
+omen_status krylov_start_from(omen_ctx* ctx, const omen_ham* ham, int prec, const void* X, int k, void* out, int nout,
+                              unsigned long long seed) {
+  KrylovOps op{ctx, ham, prec, (bool)ham->is_complex, ham->nrows};
+  omen_status s = op.init();
+  if (s != OMEN_OK) return s;
+  std::vector<cd> M((size_t)k * nout);
+  unsigned long long z = seed;
+  for (auto& c : M) {
+    z += 0x9E3779B97F4A7C15ull;
+    unsigned long long t = z;
+    t = (t ^ (t >> 30)) * 0xBF58476D1CE4E5B9ull;
+    t = (t ^ (t >> 27)) * 0x94D049BB133111EBull;
+    t ^= t >> 31;
+    const double u = (double)(t >> 11) * (1.0 / 9007199254740992.0);
+    c = cd((u < 0.5 ? -1.0 : 1.0) * (0.5 + std::fabs(u - 0.5)), 0.0);
+  }
+  s = op.combine(X, k, M, nout, out, 1.0, 0.0);
+  op.release();
+  return s;
+}
+
 extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_eig_opts* o, double* evals_host,
                                  void* evecs_dev, omen_eig_info* info) {
   if (!ctx || !ham || !o || !evals_host) return set_err(ctx, OMEN_EINVAL, "null argument");
@@ -766,7 +1269,8 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   if (b < 1 || b > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "block must be 1..%d", kMaxBlockCols);
   if (o->basis % b != 0 || o->basis < o->nev + 2 * b) return set_err(ctx, OMEN_EINVAL, "basis must be a multiple of block and >= nev + 2*block");
   if (o->basis > 2048) return set_err(ctx, OMEN_EINVAL, "basis must be <= 2048");
-  if (o->which != OMEN_LOWEST && o->which != OMEN_NEAREST) return set_err(ctx, OMEN_EINVAL, "which must be LOWEST or NEAREST");
+  if (o->which != OMEN_LOWEST && o->which != OMEN_NEAREST && o->which != OMEN_HIGHEST)
+    return set_err(ctx, OMEN_EINVAL, "which must be LOWEST, NEAREST or HIGHEST");
   if (!(o->tol > 0)) return set_err(ctx, OMEN_EINVAL, "tol must be > 0");
   if (o->max_iter < 1 || (long long)o->max_iter * b < o->nev)
     return set_err(ctx, OMEN_EINVAL, "max_iter * block must be >= nev");
@@ -781,6 +1285,7 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   KrylovOps op{ctx, ham, solve_prec, (bool)ham->is_complex, ham->nrows};
   omen_status s = op.init();
   if (s != OMEN_OK) return s;
+  op.negate = (o->which == OMEN_HIGHEST);
   const int kout = std::min<long long>(o->nev + b, o->basis);
   DevBuf Xb;
   if (cudaMalloc(&Xb.p, (size_t)kout * ham->nrows * op.el) != cudaSuccess) {
@@ -790,7 +1295,7 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   }
   RitzResult rr;
   bool conv = false;
-  s = lanczos_solve(op, o, Xb.p, kout, rr, inf, o->v0_host, conv);
+  s = (b == 1) ? lanczos_solve_single(op, o, Xb.p, kout, inf, conv) : lanczos_solve(op, o, Xb.p, kout, rr, inf, o->v0_host, conv);
   if (s != OMEN_OK) { op.release(); return s; }
   // evaluate the kout Ritz vectors in the solve precision
   DevBuf HXb, Rb;
@@ -807,7 +1312,8 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   // the nev wanted among the kout: lowest, or nearest sigma (Ritz vectors are ordered by
   // theta of A, which for the folded operator is (lambda - sigma)^2)
   std::vector<double> key(kout);
-  for (int i = 0; i < kout; ++i) key[i] = (o->which == OMEN_NEAREST) ? std::fabs(rr.lam[i] - o->sigma) : rr.lam[i];
+  for (int i = 0; i < kout; ++i)
+    key[i] = (o->which == OMEN_NEAREST) ? std::fabs(rr.lam[i] - o->sigma) : (o->which == OMEN_HIGHEST ? -rr.lam[i] : rr.lam[i]);
   s = sort_columns(op, Xb.p, kout, key, &rr.lam, &rr.res);
   if (s != OMEN_OK) { op.release(); return s; }
   error_bounds(rr.lam, rr.lam, rr.res, rr.bound);

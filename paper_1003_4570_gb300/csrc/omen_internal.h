@@ -81,5 +81,7 @@ omen_status launch_assemble(omen_ctx* ctx, omen_ham* ham, const omen_tb_params* 
 omen_status launch_hx(omen_ctx* ctx, const omen_ham* ham, const void* x, void* y, int nvec,
                       double sigma, int vec_precision);
 
-// Krylov helper kernels (lanczos.cu)
+// Krylov helpers (lanczos.cu)
 size_t vec_elem_bytes(const omen_ham* ham, int precision);
+omen_status krylov_start_from(omen_ctx* ctx, const omen_ham* ham, int prec, const void* X, int k, void* out, int nout,
+                              unsigned long long seed);

@@ -98,11 +98,12 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
   }
   const long long nrows = hams[0]->nrows;
   const size_t elem = hams[0]->is_complex ? 16 : 8;
-  DevVec phi_atom, U, n_atom, q, rho, phi_out, part, psi;
+  DevVec phi_atom, U, n_atom, q, rho, phi_out, part, psi, v0;
   const int nblk = 256;
   if (!phi_atom.alloc(sizeof(double) * N) || !U.alloc(sizeof(double) * N) || !n_atom.alloc(sizeof(double) * N) ||
       !q.alloc(sizeof(double) * N) || !rho.alloc(sizeof(double) * ng) || !phi_out.alloc(sizeof(double) * ng) ||
-      !part.alloc(sizeof(double) * nblk) || !psi.alloc(elem * nrows * (size_t)d->nev * d->nk)) {
+      !part.alloc(sizeof(double) * nblk) || !psi.alloc(elem * nrows * (size_t)d->nev * d->nk) ||
+      !v0.alloc(elem * nrows * (size_t)std::max(1, d->eig_block))) {
     free_hams();
     return set_err(ctx, OMEN_ENOMEM, "SCF work buffers");
   }
@@ -131,6 +132,14 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
       eo.block = d->eig_block;
       eo.basis = d->eig_basis;
       eo.v0_host = nullptr;
+      eo.v0_dev = nullptr;
+      if (it > 1 && d->precision == OMEN_F64) {
+        // warm start: the previous iteration's eigenvectors of this k span the new ones closely
+        st = krylov_start_from(ctx, hams[k], OMEN_F64, static_cast<char*>(psi.p) + elem * nrows * (size_t)d->nev * k,
+                               d->nev, v0.p, d->eig_block, 0x1234ull + (unsigned long long)(it * 131 + k));
+        if (st != OMEN_OK) break;
+        eo.v0_dev = v0.p;
+      }
       omen_eig_info ei{};
       st = omen_eigs(ctx, hams[k], &eo, evals.data() + (size_t)k * d->nev,
                      static_cast<char*>(psi.p) + elem * nrows * (size_t)d->nev * k, &ei);

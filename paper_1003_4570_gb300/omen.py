@@ -20,7 +20,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOCONV", "ENUMERIC", "ETIMEOUT", "EC
 OMEN_SP3S, OMEN_SP3D5S = 5, 10
 OMEN_HARD_WALL, OMEN_PERIODIC, OMEN_BLOCH = 0, 1, 2
 OMEN_F64, OMEN_F32, OMEN_F32_REFINE64 = 0, 1, 2
-OMEN_LOWEST, OMEN_NEAREST = 0, 1
+OMEN_LOWEST, OMEN_NEAREST, OMEN_HIGHEST = 0, 1, 2
 
 
 class OmenError(RuntimeError):
@@ -46,7 +46,8 @@ class HamOpts(C.Structure):
 
 class EigOpts(C.Structure):
     _fields_ = [("nev", C.c_int), ("which", C.c_int), ("sigma", C.c_double), ("tol", C.c_double),
-                ("max_iter", C.c_int), ("block", C.c_int), ("basis", C.c_int), ("v0_host", C.c_void_p)]
+                ("max_iter", C.c_int), ("block", C.c_int), ("basis", C.c_int), ("v0_host", C.c_void_p),
+                ("v0_dev", C.c_void_p)]
 
 
 class EigInfo(C.Structure):
@@ -270,7 +271,7 @@ def omen_hx_host(ctx: Context, ham: Hamiltonian, x: np.ndarray, sigma=0.0) -> np
 
 
 def omen_eigs(ctx: Context, ham: Hamiltonian, nev, which=OMEN_LOWEST, sigma=0.0, tol=1e-9, max_iter=1000,
-              block=1, basis=None, v0=None, evecs_dev=None, raise_on_noconv=True):
+              block=1, basis=None, v0=None, evecs_dev=None, raise_on_noconv=True, v0_dev=None):
     """Eigenpairs by thick-restart block Lanczos.  Returns (evals ndarray, info dict, status)."""
     if basis is None:
         basis = max(4 * block, ((2 * nev + 2 * block + block - 1) // block) * block, 32 // block * block)
@@ -278,7 +279,7 @@ def omen_eigs(ctx: Context, ham: Hamiltonian, nev, which=OMEN_LOWEST, sigma=0.0,
     if v0 is not None:
         v0a = np.ascontiguousarray(v0, dtype=ham.numpy_dtype)
     o = EigOpts(int(nev), int(which), float(sigma), float(tol), int(max_iter), int(block), int(basis),
-                None if v0a is None else v0a.ctypes.data)
+                None if v0a is None else v0a.ctypes.data, _ptr(v0_dev))
     ev = np.zeros(nev)
     info = EigInfo()
     s = lib().omen_eigs(ctx.handle, ham.handle, C.byref(o), ev.ctypes.data, _ptr(evecs_dev), C.byref(info))
