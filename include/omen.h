@@ -176,6 +176,24 @@ typedef struct {
 omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_eig_opts* opts,
                       double* evals_host, void* evecs_dev, omen_eig_info* info);
 
+/* ---- k batching (paper Section II-C: k-space grouping) ---------------------------------- */
+
+/* y_k = (H(k) - sigma) x_k for nk Bloch wave vectors k_host [nk][3] (1/nm) in one launch; the
+ * Hamiltonian's bond blocks (stored, no spin-orbit, Bloch-periodic structure) are shared by
+ * all k, only the phase on bonds that wrap a Bloch face differs.  x_dev, y_dev: [nk][nrows]
+ * complex vectors of the Hamiltonian's precision. */
+omen_status omen_hx_kbatch(omen_ctx* ctx, const omen_ham* ham, int nk, const double* k_host,
+                           const void* x_dev, void* y_dev, double sigma);
+
+/* nev eigenpairs for each of nk wave vectors, all solved in lockstep (single-vector thick-
+ * restart Lanczos, one k-batched H·X launch per step).  opts as for omen_eigs with block = 1
+ * and which LOWEST or NEAREST; for NEAREST, tol bounds the H residual estimated from the
+ * folded residual.  evals_host [nk][nev] ascending per k; evecs_dev [nk][nev][nrows] or NULL;
+ * info aggregates over k (max residual and bound).  ENOCONV if some k did not converge. */
+omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int nk, const double* k_host,
+                             const omen_eig_opts* opts, double* evals_host, void* evecs_dev,
+                             omen_eig_info* info);
+
 /* ---- charge, Poisson, self-consistency (paper Section III-A items 2-3) ------------------- */
 
 typedef struct {

@@ -13,7 +13,9 @@
 // Bloch phase: a neighbour reached across the high (low) face of a Bloch-periodic direction d
 // is its periodic image shifted by +L_d (-L_d); its amplitude is multiplied by
 // exp(+i k_d L_d) (resp. the conjugate).
+#include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "omen_internal.h"
 #include "sk_device.cuh"
@@ -229,6 +231,103 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
     for (int o = 0; o < NORB; ++o) y[(size_t)(q * NORB + o) * N + atom] = acc[q][o];
 }
 
+// ---------------------------------------------------------------------------------------
+// k-batched product: y_k = (H(k) - sigma) x_k for nk Bloch wave vectors in one launch.  The real
+// bond blocks are the same for every k (the phase sits only on bonds that wrap a Bloch face),
+// so each thread loads a block entry once and applies it to KB vectors; grid.z runs over
+// batches of KB wave vectors.  phases[k*3 + d] = exp(i k_d L_d).  Vectors are [nk][nrows].
+template <typename T, int NORB, int KB>
+__global__ void __launch_bounds__(128) hx_kbatch_kernel(HxArgs<T> a, const double2* __restrict__ phases, int nk) {
+  using V = typename Cx<T>::t;
+  const Geo& g = a.g;
+  const int b = blockIdx.x & 7;
+  const int cell = (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
+  if (cell >= g.ncells) return;
+  const int N = g.natoms;
+  const int atom = b * g.ncells + cell;
+  const int ix = cell % g.nx, iy = (cell / g.nx) % g.ny, iz = cell / (g.nx * g.ny);
+  const int k0 = blockIdx.z * KB;
+  const int nkb = min(KB, nk - k0);
+  const V* __restrict__ x = static_cast<const V*>(a.x);
+  V* __restrict__ y = static_cast<V*>(a.y);
+  const int sp = a.species[atom];
+  V acc[KB][NORB];
+  {
+    const T u = (T)(a.U[atom] - a.sigma);
+#pragma unroll
+    for (int q = 0; q < KB; ++q)
+#pragma unroll
+      for (int o = 0; o < NORB; ++o) {
+        acc[q][o].x = (T)0;
+        acc[q][o].y = (T)0;
+        if (q < nkb) {
+          const T d = (T)a.onsite[sp * NORB + o] + u;
+          const V xv = x[(size_t)(k0 + q) * a.nrows + (size_t)o * N + atom];
+          acc[q][o].x = d * xv.x;
+          acc[q][o].y = d * xv.y;
+        }
+      }
+  }
+  const bool is_a = b < 4;
+  const int s = is_a ? b : b - 4;
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    int ox, oy, oz, site2;
+    if (is_a) {
+      ox = a.nt.a_to_b_off[s][k][0]; oy = a.nt.a_to_b_off[s][k][1]; oz = a.nt.a_to_b_off[s][k][2];
+      site2 = a.nt.a_to_b_site[s][k];
+    } else {
+      ox = a.nt.b_to_a_off[s][k][0]; oy = a.nt.b_to_a_off[s][k][1]; oz = a.nt.b_to_a_off[s][k][2];
+      site2 = a.nt.b_to_a_site[s][k];
+    }
+    int cell2, wrap[3];
+    if (!shift_cell(g, ix, iy, iz, ox, oy, oz, cell2, wrap)) continue;
+    const int atom2 = site2 * g.ncells + cell2;
+    V xn[KB][NORB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      V f;
+      f.x = (T)1;
+      f.y = (T)0;
+      if (q < nkb && (wrap[0] | wrap[1] | wrap[2])) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if (wrap[d]) {
+            const double2 ph = phases[(size_t)(k0 + q) * 3 + d];
+            V p;
+            p.x = (T)ph.x;
+            p.y = (T)(wrap[d] > 0 ? ph.y : -ph.y);
+            f = cmul<T>(f, p);
+          }
+      }
+#pragma unroll
+      for (int o = 0; o < NORB; ++o) {
+        if (q < nkb) xn[q][o] = cmul<T>(x[(size_t)(k0 + q) * a.nrows + (size_t)o * N + atom2], f);
+        else { xn[q][o].x = (T)0; xn[q][o].y = (T)0; }
+      }
+    }
+    const size_t ks = is_a ? (size_t)(k * 4 + s) : (size_t)(k * 4 + site2);
+    const size_t pidx = ks * a.slot_stride + (is_a ? cell : cell2);
+    const T* __restrict__ hb = a.blk + ((pidx >> 5) * (NORB * NORB)) * 32 + (pidx & 31);
+#pragma unroll
+    for (int o1 = 0; o1 < NORB; ++o1)
+#pragma unroll
+      for (int o2 = 0; o2 < NORB; ++o2) {
+        const T h = __ldg(hb + (size_t)(o1 * NORB + o2) * 32);
+#pragma unroll
+        for (int q = 0; q < KB; ++q) {
+          if (is_a) fma_c(acc[q][o1], h, xn[q][o2]);
+          else fma_c(acc[q][o2], h, xn[q][o1]);
+        }
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < KB; ++q)
+    if (q < nkb)
+#pragma unroll
+      for (int o = 0; o < NORB; ++o) y[(size_t)(k0 + q) * a.nrows + (size_t)o * N + atom] = acc[q][o];
+}
+
 size_t vec_elem_bytes(const omen_ham* h, int precision) {
   const size_t r = (precision == OMEN_F64) ? 8 : 4;
   return h->is_complex ? 2 * r : r;
@@ -318,4 +417,79 @@ extern "C" omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* h, const void
   if (e != cudaSuccess || e2 != cudaSuccess)
     return set_err(ctx, OMEN_ECUDA, "host H·X failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
   return OMEN_OK;
+}
+
+static constexpr int kKB = 2;   // wave vectors per thread (register budget: 2 x 10 complex amplitudes per bond)
+
+template <typename T>
+static cudaError_t launch_kbatch_prec(const omen_ham* h, const T* blk, const double2* phases, int nk, const void* x,
+                                      void* y, double sigma, cudaStream_t st) {
+  const omen_lattice* L = h->lat;
+  HxArgs<T> a;
+  a.g = Geo{L->nx, L->ny, L->nz, L->ncells, L->natoms, {L->periodic[0], L->periodic[1], L->periodic[2]}};
+  a.nt = host_neighbour_tables();
+  a.blk = blk;
+  a.b0 = nullptr;
+  a.strain = L->d_strain;
+  a.species = L->d_species;
+  a.onsite = h->d_onsite;
+  a.U = h->d_U;
+  a.lambda = h->d_lambda;
+  a.x = x;
+  a.y = y;
+  a.nrows = h->nrows;
+  a.sigma = sigma;
+  a.eta = h->eta;
+  for (int d = 0; d < 3; ++d) a.phase[d] = h->phase[d];
+  a.ns = h->nspecies;
+  a.slot_stride = h->slot_stride;
+  dim3 grid(((a.g.ncells + 127) / 128) * 8, 1, (nk + kKB - 1) / kKB);
+  if (h->norb == 10) hx_kbatch_kernel<T, 10, kKB><<<grid, 128, 0, st>>>(a, phases, nk);
+  else hx_kbatch_kernel<T, 5, kKB><<<grid, 128, 0, st>>>(a, phases, nk);
+  return cudaGetLastError();
+}
+
+omen_status launch_hx_kbatch(omen_ctx* ctx, const omen_ham* h, int nk, const double2* phases_dev, const void* x, void* y,
+                             double sigma, int vec_precision) {
+  if (h->matrix_free || h->spin_orbit) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch needs stored blocks without spin-orbit");
+  if ((long long)(nk + kKB - 1) / kKB > 65535) return set_err(ctx, OMEN_EINVAL, "too many wave vectors");
+  cudaError_t e;
+  if (vec_precision == OMEN_F64) {
+    if (!h->d_blk64) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP64 blocks");
+    e = launch_kbatch_prec<double>(h, h->d_blk64, phases_dev, nk, x, y, sigma, ctx->stream);
+  } else {
+    if (!h->d_blk32) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP32 blocks");
+    e = launch_kbatch_prec<float>(h, h->d_blk32, phases_dev, nk, x, y, sigma, ctx->stream);
+  }
+  if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "k-batched H·X launch: %s", cudaGetErrorString(e));
+  return OMEN_OK;
+}
+
+omen_status make_phases(omen_ctx* ctx, const omen_ham* h, int nk, const double* k_host, double2** out) {
+  const omen_lattice* L = h->lat;
+  std::vector<double2> ph((size_t)nk * 3);
+  const int nc[3] = {L->nx, L->ny, L->nz};
+  for (int q = 0; q < nk; ++q)
+    for (int d = 0; d < 3; ++d) {
+      const double t = (L->periodic[d] == OMEN_BLOCH) ? k_host[q * 3 + d] * nc[d] * L->a_nm : 0.0;
+      ph[(size_t)q * 3 + d] = make_double2(cos(t), sin(t));
+    }
+  if (cudaMallocAsync(out, sizeof(double2) * ph.size(), ctx->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, OMEN_ENOMEM, "phase table");
+  }
+  OMEN_CUDA(ctx, cudaMemcpyAsync(*out, ph.data(), sizeof(double2) * ph.size(), cudaMemcpyHostToDevice, ctx->stream));
+  return OMEN_OK;
+}
+
+extern "C" omen_status omen_hx_kbatch(omen_ctx* ctx, const omen_ham* h, int nk, const double* k_host, const void* x,
+                                      void* y, double sigma) {
+  if (!ctx || !h || !k_host || !x || !y || nk < 1) return set_err(ctx, OMEN_EINVAL, "null argument or nk < 1");
+  if (!h->bloch) return set_err(ctx, OMEN_EINVAL, "k batch needs a structure with Bloch-periodic directions");
+  double2* ph = nullptr;
+  omen_status s = make_phases(ctx, h, nk, k_host, &ph);
+  if (s != OMEN_OK) return s;
+  s = launch_hx_kbatch(ctx, h, nk, ph, x, y, sigma, native_precision(h));
+  cudaFreeAsync(ph, ctx->stream);
+  return s;
 }

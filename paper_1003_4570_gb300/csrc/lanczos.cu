@@ -120,12 +120,15 @@ __global__ void reduce_partial_kernel(const double2* __restrict__ P, int nchunks
 static constexpr int kIG = 16;
 template <typename T, bool C>
 __global__ void __launch_bounds__(256) dots1_kernel(const void* Av, long long lda, int na, const void* Bv,
-                                                    long long n, int rows_per_cta, double2* __restrict__ P) {
+                                                    long long n, int rows_per_cta, double2* __restrict__ P,
+                                                    long long a_ps = 0, long long b_ps = 0, long long p_ps = 0) {
   using E = Elem<T, C>;
   using V = typename E::V;
   using Acc = std::conditional_t<sizeof(T) == 8, double, float>;
-  const V* A = static_cast<const V*>(Av);
-  const V* B = static_cast<const V*>(Bv);
+  // grid.z = independent problems (batched Lanczos), offsets a_ps, b_ps (elements), p_ps (partials)
+  const V* A = static_cast<const V*>(Av) + blockIdx.z * a_ps;
+  const V* B = static_cast<const V*>(Bv) + blockIdx.z * b_ps;
+  P += blockIdx.z * p_ps;
   const int i0 = blockIdx.x * kIG;
   const int ni = min(kIG, na - i0);
   const long long r0 = (long long)blockIdx.y * rows_per_cta;
@@ -185,15 +188,17 @@ __global__ void __launch_bounds__(256) dots1_kernel(const void* Av, long long ld
 // y = beta*y + alpha * sum_i A_i m_i for one output vector, 8 basis loads in flight per row.
 template <typename T, bool C>
 __global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M,
-                                                       void* Yv, long long n, double alpha, double beta) {
+                                                       void* Yv, long long n, double alpha, double beta,
+                                                       long long a_ps = 0, long long m_ps = 0, long long y_ps = 0) {
   using E = Elem<T, C>;
   using V = typename E::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* Ms = reinterpret_cast<double2*>(smem_raw);
+  M += blockIdx.y * m_ps;
   for (int t = threadIdx.x; t < na; t += blockDim.x) Ms[t] = M[t];
   __syncthreads();
-  const V* A = static_cast<const V*>(Av);
-  V* Y = static_cast<V*>(Yv);
+  const V* A = static_cast<const V*>(Av) + blockIdx.y * a_ps;
+  V* Y = static_cast<V*>(Yv) + blockIdx.y * y_ps;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
     double yr = 0.0, yi = 0.0;
     int i = 0;
@@ -236,8 +241,12 @@ __global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long
 // Device-side reduction of the partials into out (na x nb, column-major) and, optionally,
 // into columns col0.. of the projected matrix T (ldT x ldT, column-major).
 __global__ void reduce_dev_kernel(const double2* __restrict__ P, int nchunks, int na, int nb, double2* __restrict__ out,
-                                  double2* __restrict__ accT, int ldT, int col0) {
+                                  double2* __restrict__ accT, int ldT, int col0, long long p_ps = 0,
+                                  long long out_ps = 0, long long t_ps = 0) {
   const int e = blockIdx.x;
+  P += blockIdx.y * p_ps;
+  out += blockIdx.y * out_ps;
+  if (accT) accT += blockIdx.y * t_ps;
   const int count = na * nb;
   double sr = 0.0, si = 0.0;
   for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
@@ -270,13 +279,16 @@ __global__ void reduce_dev_kernel(const double2* __restrict__ P, int nchunks, in
 // V = W / ||W|| with ||W||^2 read from the device; the norm goes into T[row, col].
 template <typename T, bool C>
 __global__ void normalize_kernel(const void* Wv, void* Vv, long long n, const double2* __restrict__ nrm2,
-                                 double2* __restrict__ Tm, int ldT, int row, int col, int* __restrict__ flag) {
+                                 double2* __restrict__ Tm, int ldT, int row, int col, int* __restrict__ flag,
+                                 long long w_ps = 0, long long v_ps = 0, long long n_ps = 0, long long t_ps = 0) {
   using E = Elem<T, C>;
   using V = typename E::V;
+  nrm2 += blockIdx.y * n_ps;
+  if (Tm) Tm += blockIdx.y * t_ps;
   const double b = sqrt(fmax(nrm2->x, 0.0));
   const double inv = (b > 1e-300) ? 1.0 / b : 0.0;
-  const V* W = static_cast<const V*>(Wv);
-  V* Vo = static_cast<V*>(Vv);
+  const V* W = static_cast<const V*>(Wv) + blockIdx.y * w_ps;
+  V* Vo = static_cast<V*>(Vv) + blockIdx.y * v_ps;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
     Vo[r] = E::make(E::re(W[r]) * inv, E::im(W[r]) * inv);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -587,6 +599,64 @@ struct KrylovOps {
     } else {
       if (cplx) normalize_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(W, V, n, nrm2, Tm, ldT, row, col, flag);
       else normalize_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(W, V, n, nrm2, Tm, ldT, row, col, flag);
+    }
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+
+  // ---- batched (P independent problems of n rows each, problem p at offset p*n) ----
+  // A: na basis vectors with stride lda between vectors; B, out, T per problem.
+  omen_status dots_dev_batch(int P, const void* A, long long lda, int na, const void* B, double2* out_dev,
+                             long long out_ps, double2* accT, int ldT, long long t_ps, int col0) {
+    int rows = 8192;
+    while ((n + rows - 1) / rows > 65535) rows *= 2;
+    const long long nchunks = (n + rows - 1) / rows;
+    const long long pps = nchunks * na;
+    omen_status s1 = ensure_partial((size_t)pps * P);
+    if (s1 != OMEN_OK) return s1;
+    dim3 grid((na + kIG - 1) / kIG, (unsigned)nchunks, P);
+    if (prec == OMEN_F64) {
+      if (cplx) dots1_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, n, rows, d_partial, n, n, pps);
+      else dots1_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, n, rows, d_partial, n, n, pps);
+    } else {
+      if (cplx) dots1_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, n, rows, d_partial, n, n, pps);
+      else dots1_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, n, rows, d_partial, n, n, pps);
+    }
+    reduce_dev_kernel<<<dim3(na, P), 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, 1, out_dev, accT, ldT, col0, pps,
+                                                            out_ps, t_ps);
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+
+  omen_status combine_dev_batch(int P, const void* A, long long lda, int na, const double2* M_dev, long long m_ps, void* Y,
+                                double alpha, double beta) {
+    const size_t shm1 = (size_t)na * sizeof(double2);
+    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)sm_count * 8 / std::max(1, P) + 1));
+    dim3 grid(gx, P);
+#define COMB1B(T, Cc)                                                                                 \
+  do {                                                                                                \
+    if (shm1 > 48 * 1024)                                                                              \
+      cudaFuncSetAttribute(combine1_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm1); \
+    combine1_kernel<T, Cc><<<grid, 256, shm1, ctx->stream>>>(A, lda, na, M_dev, Y, n, alpha, beta, n, m_ps, n); \
+  } while (0)
+    if (prec == OMEN_F64) { if (cplx) COMB1B(double, true); else COMB1B(double, false); }
+    else { if (cplx) COMB1B(float, true); else COMB1B(float, false); }
+#undef COMB1B
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+
+  omen_status normalize_dev_batch(int P, const void* W, void* Vo, const double2* nrm2, double2* Tm, int ldT,
+                                  long long t_ps, int row, int col) {
+    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)sm_count * 8 / std::max(1, P) + 1));
+    dim3 grid(gx, P);
+    int* flag = ctx->d_status + 1;
+    if (prec == OMEN_F64) {
+      if (cplx) normalize_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(W, Vo, n, nrm2, Tm, ldT, row, col, flag, n, n, 1, t_ps);
+      else normalize_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(W, Vo, n, nrm2, Tm, ldT, row, col, flag, n, n, 1, t_ps);
+    } else {
+      if (cplx) normalize_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(W, Vo, n, nrm2, Tm, ldT, row, col, flag, n, n, 1, t_ps);
+      else normalize_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(W, Vo, n, nrm2, Tm, ldT, row, col, flag, n, n, 1, t_ps);
     }
     OMEN_CHECK_LAUNCH(ctx);
     return OMEN_OK;
@@ -1371,5 +1441,273 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   inf->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (!inf->converged) return set_err(ctx, OMEN_ENOCONV, "not converged: error bound %.3e > tol %.3e after %d block steps",
                                       inf->max_error_bound, o->tol, inf->iterations);
+  return OMEN_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// k-batched eigen-solve (paper Section II-C: k-space grouping; here all k of one structure in
+// lockstep on one GPU).  nk independent single-vector thick-restart Lanczos recurrences, one per
+// Bloch wave vector, advance together: every step is one k-batched H·X launch (bond blocks
+// shared by all k) plus batched projection / update / normalisation launches.  Vectors are laid
+// out [basis vector][k][row], so the current Lanczos vectors of all k are contiguous.
+// Convergence (checked per k on the host): LOWEST - the Weyl / Kato–Temple bound on the Ritz
+// values; NEAREST - the H residual estimated from the folded residual, r_A / (2 sqrt(theta)).
+extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int nk, const double* k_host,
+                                        const omen_eig_opts* o, double* evals_host, void* evecs_dev,
+                                        omen_eig_info* info) {
+  if (!ctx || !ham || !k_host || !o || !evals_host || nk < 1) return set_err(ctx, OMEN_EINVAL, "null argument or nk < 1");
+  if (!ham->bloch || ham->spin_orbit || ham->matrix_free) return set_err(ctx, OMEN_EINVAL, "k batch needs a Bloch Hamiltonian with stored blocks and no spin-orbit");
+  if (ham->precision == OMEN_F32_REFINE64) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs in F64 or F32");
+  if (o->block != 1) return set_err(ctx, OMEN_EINVAL, "k batch uses block size 1");
+  if (o->which != OMEN_LOWEST && o->which != OMEN_NEAREST) return set_err(ctx, OMEN_EINVAL, "which must be LOWEST or NEAREST");
+  if (o->nev < 1 || o->basis < o->nev + 2 || o->basis > 2048 || !(o->tol > 0) || o->max_iter < o->nev)
+    return set_err(ctx, OMEN_EINVAL, "invalid eigen options");
+  if ((long long)o->basis + 1 > ham->nrows) return set_err(ctx, OMEN_EINVAL, "basis larger than the problem");
+  OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
+  auto t0 = std::chrono::steady_clock::now();
+  const int P = nk, m = o->basis, ldT = m + 1, nev = o->nev;
+  const bool folded = o->which == OMEN_NEAREST;
+  const int prec = ham->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64;
+  KrylovOps op{ctx, ham, prec, true, ham->nrows};
+  omen_status s = op.init();
+  if (s != OMEN_OK) return s;
+  const long long n = ham->nrows;
+  const size_t vb = (size_t)n * op.el;               // one vector
+  const size_t blk = vb * P;                          // one basis slot for all k
+  double2* ph = nullptr;
+  s = make_phases(ctx, ham, nk, k_host, &ph);
+  if (s != OMEN_OK) { op.release(); return s; }
+  DevBuf Vb, Wb, Tb, Xb, Td, Hd;
+  if (cudaMalloc(&Vb.p, (size_t)(m + 1) * blk) != cudaSuccess || cudaMalloc(&Wb.p, blk) != cudaSuccess ||
+      cudaMalloc(&Tb.p, blk) != cudaSuccess || cudaMalloc(&Xb.p, (size_t)m * blk) != cudaSuccess ||
+      cudaMalloc(&Td.p, sizeof(double2) * ldT * ldT * P) != cudaSuccess ||
+      cudaMalloc(&Hd.p, sizeof(double2) * (ldT + 1) * P) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(ph, ctx->stream);
+    op.release();
+    return set_err(ctx, OMEN_ENOMEM, "k-batched Lanczos basis (%d x %d vectors of %lld rows)", m + 1, P, n);
+  }
+  char* V = static_cast<char*>(Vb.p);
+  auto slot = [&](int j) { return V + (size_t)j * blk; };
+  double2* dT = static_cast<double2*>(Td.p);
+  double2* dh = static_cast<double2*>(Hd.p);
+  double2* dn = dh + (size_t)ldT * P;
+  const long long tps = (long long)ldT * ldT;
+  const long long lda = (long long)P * n;   // stride between basis vectors of one problem
+  OMEN_CUDA(ctx, cudaMemsetAsync(dT, 0, sizeof(double2) * tps * P, ctx->stream));
+  OMEN_CUDA(ctx, cudaMemsetAsync(ctx->d_status + 1, 0, sizeof(int), ctx->stream));
+  long long hx = 0;
+  auto apply = [&](const void* X, void* Y) -> omen_status {
+    if (!folded) { hx += P; return launch_hx_kbatch(ctx, ham, P, ph, X, Y, 0.0, prec); }
+    omen_status s2 = launch_hx_kbatch(ctx, ham, P, ph, X, Tb.p, o->sigma, prec);
+    if (s2 != OMEN_OK) return s2;
+    hx += 2 * P;
+    return launch_hx_kbatch(ctx, ham, P, ph, Tb.p, Y, o->sigma, prec);
+  };
+  if (o->v0_dev) OMEN_CUDA(ctx, cudaMemcpyAsync(Wb.p, o->v0_dev, blk, cudaMemcpyDeviceToDevice, ctx->stream));
+  else if ((s = op.random_fill(Wb.p, P, 0x5EEDull)) != OMEN_OK) return s;
+  s = op.dots_dev_batch(P, Wb.p, n, 1, Wb.p, dn, 1, nullptr, 0, 0, 0);
+  if (s == OMEN_OK) s = op.normalize_dev_batch(P, Wb.p, slot(0), dn, nullptr, 0, 0, 0, 0);
+  if (s != OMEN_OK) { cudaFreeAsync(ph, ctx->stream); op.release(); return s; }
+
+  std::vector<cd> Th((size_t)tps * P);
+  std::vector<std::vector<double>> theta(P);
+  std::vector<std::vector<cd>> Y(P);
+  std::vector<char> conv(P, 0);
+  int jstart = 0, nbas = 1, iter = 0, restarts = 0, since = 0;
+  const int check_every = std::max(4, std::min(32, m / 4));
+  while (true) {
+    s = apply(slot(jstart), Wb.p);
+    for (int pass = 0; pass < 2 && s == OMEN_OK; ++pass) {
+      s = op.dots_dev_batch(P, V, lda, nbas, Wb.p, dh, ldT, dT, ldT, tps, jstart);
+      if (s == OMEN_OK) s = op.combine_dev_batch(P, V, lda, nbas, dh, ldT, Wb.p, -1.0, 1.0);
+    }
+    if (s == OMEN_OK) s = op.dots_dev_batch(P, Wb.p, n, 1, Wb.p, dn, 1, nullptr, 0, 0, 0);
+    if (s == OMEN_OK) s = op.normalize_dev_batch(P, Wb.p, slot(nbas), dn, dT, ldT, tps, nbas, jstart);
+    if (s != OMEN_OK) break;
+    ++iter;
+    ++since;
+    const bool full = nbas + 1 > m;
+    if (!(full || iter >= o->max_iter || (since >= check_every && nbas >= nev + 1)) || nbas < nev) {
+      jstart = nbas;
+      nbas += 1;
+      continue;
+    }
+    since = 0;
+    OMEN_CUDA(ctx, cudaMemcpyAsync(Th.data(), dT, sizeof(double2) * tps * P, cudaMemcpyDeviceToHost, ctx->stream));
+    int flag = 0;
+    OMEN_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->d_status + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (flag) { s = set_err(ctx, OMEN_ENUMERIC, "Lanczos breakdown or non-finite value in the k batch"); break; }
+    bool all = true;
+    std::vector<double> betas(P);
+    for (int p = 0; p < P; ++p) {
+      const cd* T = Th.data() + (size_t)p * tps;
+      std::vector<cd> Tn((size_t)nbas * nbas);
+      for (int j = 0; j < nbas; ++j)
+        for (int i = 0; i <= j; ++i) {
+          cd v = T[i + (size_t)j * ldT];
+          if (i == j) v = cd(std::real(v), 0.0);
+          Tn[i + (size_t)j * nbas] = v;
+          Tn[j + (size_t)i * nbas] = std::conj(v);
+        }
+      betas[p] = std::real(T[nbas + (size_t)jstart * ldT]);
+      theta[p].assign(nbas, 0.0);
+      Y[p].assign((size_t)nbas * nbas, cd(0));
+      if (hermitian_eig(nbas, Tn.data(), theta[p].data(), Y[p].data())) { s = set_err(ctx, OMEN_ENUMERIC, "projected eigenproblem"); break; }
+      std::vector<double> lam(nev), res(nev), bd;
+      for (int i = 0; i < nev; ++i) {
+        const double rA = std::fabs(betas[p]) * std::abs(Y[p][jstart + (size_t)i * nbas]);
+        lam[i] = theta[p][i];
+        res[i] = folded ? rA / (2.0 * std::sqrt(std::max(theta[p][i], 0.0)) + 1e-300) : rA;
+      }
+      if (folded) {
+        bd = res;
+      } else {
+        error_bounds(theta[p], lam, res, bd);
+      }
+      conv[p] = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+      all = all && conv[p];
+    }
+    if (s != OMEN_OK) break;
+    if (all || iter >= o->max_iter) break;
+    if (full) {
+      const int kk = std::min(m - 1, std::max(nev + 1, nbas / 2));
+      for (int p = 0; p < P && s == OMEN_OK; ++p) {
+        for (int j0 = 0; j0 < kk; j0 += kMaxBlockCols) {
+          const int nbj = std::min(kMaxBlockCols, kk - j0);
+          std::vector<cd> M((size_t)nbas * nbj);
+          for (int j = 0; j < nbj; ++j)
+            for (int i = 0; i < nbas; ++i) M[i + (size_t)j * nbas] = Y[p][i + (size_t)(j0 + j) * nbas];
+          OMEN_CUDA(ctx, cudaMemcpyAsync(op.d_small, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+          const size_t shm = M.size() * sizeof(double2);
+          const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)op.sm_count * 8);
+          char* Yout = static_cast<char*>(Xb.p) + (size_t)j0 * blk + (size_t)p * vb;
+          const char* Ain = V + (size_t)p * vb;
+          if (prec == OMEN_F64) {
+            cudaFuncSetAttribute(combine_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            combine_kernel<double, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
+          } else {
+            cudaFuncSetAttribute(combine_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            combine_kernel<float, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
+          }
+          OMEN_CHECK_LAUNCH(ctx);
+          OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        }
+      }
+      if (s != OMEN_OK) break;
+      OMEN_CUDA(ctx, cudaMemcpyAsync(V, Xb.p, (size_t)kk * blk, cudaMemcpyDeviceToDevice, ctx->stream));
+      OMEN_CUDA(ctx, cudaMemcpyAsync(slot(kk), slot(nbas), blk, cudaMemcpyDeviceToDevice, ctx->stream));
+      std::fill(Th.begin(), Th.end(), cd(0));
+      for (int p = 0; p < P; ++p) {
+        cd* T = Th.data() + (size_t)p * tps;
+        for (int i = 0; i < kk; ++i) T[i + (size_t)i * ldT] = theta[p][i];
+        for (int i = 0; i < kk; ++i) T[kk + (size_t)i * ldT] = betas[p] * Y[p][jstart + (size_t)i * nbas];
+      }
+      OMEN_CUDA(ctx, cudaMemcpyAsync(dT, Th.data(), sizeof(double2) * tps * P, cudaMemcpyHostToDevice, ctx->stream));
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      jstart = kk;
+      nbas = kk + 1;
+      ++restarts;
+      continue;
+    }
+    jstart = nbas;
+    nbas += 1;
+  }
+  if (s != OMEN_OK) { cudaFreeAsync(ph, ctx->stream); op.release(); return s; }
+  // Ritz vectors (nev per k) into Xb with layout [i][k][row], then H X and Rayleigh quotients
+  for (int p = 0; p < P && s == OMEN_OK; ++p)
+    for (int j0 = 0; j0 < nev; j0 += kMaxBlockCols) {
+      const int nbj = std::min(kMaxBlockCols, nev - j0);
+      std::vector<cd> M((size_t)nbas * nbj);
+      for (int j = 0; j < nbj; ++j)
+        for (int i = 0; i < nbas; ++i) M[i + (size_t)j * nbas] = Y[p][i + (size_t)(j0 + j) * nbas];
+      OMEN_CUDA(ctx, cudaMemcpyAsync(op.d_small, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+      const size_t shm = M.size() * sizeof(double2);
+      const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)op.sm_count * 8);
+      char* Yout = static_cast<char*>(Xb.p) + (size_t)j0 * blk + (size_t)p * vb;
+      const char* Ain = V + (size_t)p * vb;
+      if (prec == OMEN_F64) {
+        cudaFuncSetAttribute(combine_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        combine_kernel<double, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
+      } else {
+        cudaFuncSetAttribute(combine_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        combine_kernel<float, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
+      }
+      OMEN_CHECK_LAUNCH(ctx);
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+  // evaluate: lam = <x,Hx>/<x,x>, r = ||Hx - lam x|| / ||x||
+  std::vector<double> lam((size_t)P * nev), res((size_t)P * nev);
+  double2* dq = dh;  // reuse: P values
+  std::vector<double2> hq(P), hn(P), hr(P);
+  for (int i = 0; i < nev && s == OMEN_OK; ++i) {
+    char* Xi = static_cast<char*>(Xb.p) + (size_t)i * blk;
+    s = launch_hx_kbatch(ctx, ham, P, ph, Xi, Wb.p, 0.0, prec);
+    hx += P;
+    if (s == OMEN_OK) s = op.dots_dev_batch(P, Xi, n, 1, Wb.p, dq, 1, nullptr, 0, 0, 0);
+    if (s == OMEN_OK) {
+      OMEN_CUDA(ctx, cudaMemcpyAsync(hq.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
+      s = op.dots_dev_batch(P, Xi, n, 1, Xi, dq, 1, nullptr, 0, 0, 0);
+    }
+    if (s == OMEN_OK) {
+      OMEN_CUDA(ctx, cudaMemcpyAsync(hn.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      std::vector<double2> mlam(P);
+      for (int p = 0; p < P; ++p) {
+        lam[(size_t)p * nev + i] = hq[p].x / hn[p].x;
+        mlam[p] = make_double2(lam[(size_t)p * nev + i], 0.0);
+      }
+      OMEN_CUDA(ctx, cudaMemcpyAsync(dq, mlam.data(), sizeof(double2) * P, cudaMemcpyHostToDevice, ctx->stream));
+      s = op.combine_dev_batch(P, Xi, n, 1, dq, 1, Wb.p, -1.0, 1.0);  // W = HX - lam X
+    }
+    if (s == OMEN_OK) s = op.dots_dev_batch(P, Wb.p, n, 1, Wb.p, dq, 1, nullptr, 0, 0, 0);
+    if (s == OMEN_OK) {
+      OMEN_CUDA(ctx, cudaMemcpyAsync(hr.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      for (int p = 0; p < P; ++p) res[(size_t)p * nev + i] = std::sqrt(std::max(0.0, hr[p].x) / hn[p].x);
+    }
+  }
+  double maxres = 0.0, maxbd = 0.0;
+  for (int p = 0; p < P && s == OMEN_OK; ++p) {
+    std::vector<int> ord(nev);
+    for (int i = 0; i < nev; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return lam[(size_t)p * nev + a] < lam[(size_t)p * nev + b]; });
+    std::vector<double> lp(nev), rp(nev), bd;
+    for (int i = 0; i < nev; ++i) {
+      lp[i] = lam[(size_t)p * nev + ord[i]];
+      rp[i] = res[(size_t)p * nev + ord[i]];
+      evals_host[(size_t)p * nev + i] = lp[i];
+    }
+    error_bounds(lp, lp, rp, bd);
+    for (int i = 0; i < nev; ++i) {
+      maxres = std::max(maxres, rp[i]);
+      maxbd = std::max(maxbd, bd[i]);
+    }
+    if (evecs_dev)
+      for (int i = 0; i < nev; ++i)
+        OMEN_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(evecs_dev) + ((size_t)p * nev + i) * vb,
+                                       static_cast<char*>(Xb.p) + (size_t)ord[i] * blk + (size_t)p * vb, vb,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  cudaFreeAsync(ph, ctx->stream);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  op.release();
+  if (s != OMEN_OK) return s;
+  if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "k batch: %s", cudaGetErrorString(e));
+  bool allc = true;
+  for (char c : conv) allc = allc && c;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iterations = iter;
+    info->hx_count = hx;
+    info->restarts = restarts;
+    info->converged = allc;
+    info->max_residual = maxres;
+    info->max_error_bound = maxbd;
+    info->max_residual_raw = maxres;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!allc) return set_err(ctx, OMEN_ENOCONV, "k batch: not every wave vector converged in %d steps", iter);
   return OMEN_OK;
 }

@@ -80,6 +80,9 @@ omen_status upload_neighbour_tables(omen_ctx* ctx);
 omen_status launch_assemble(omen_ctx* ctx, omen_ham* ham, const omen_tb_params* p);
 omen_status launch_hx(omen_ctx* ctx, const omen_ham* ham, const void* x, void* y, int nvec,
                       double sigma, int vec_precision);
+omen_status launch_hx_kbatch(omen_ctx* ctx, const omen_ham* h, int nk, const double2* phases_dev, const void* x, void* y,
+                             double sigma, int vec_precision);
+omen_status make_phases(omen_ctx* ctx, const omen_ham* h, int nk, const double* k_host, double2** out);
 
 // Krylov helpers (lanczos.cu)
 size_t vec_elem_bytes(const omen_ham* ham, int precision);

@@ -119,6 +119,8 @@ def lib():
             "omen_hx": (i, [vp, vp, vp, vp, i, d]),
             "omen_hx_host": (i, [vp, vp, vp, vp, i, d]),
             "omen_eigs": (i, [vp, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
+            "omen_hx_kbatch": (i, [vp, vp, i, vp, vp, vp, d]),
+            "omen_eigs_kbatch": (i, [vp, vp, i, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
             "omen_poisson": (i, [vp, C.POINTER(Grid), vp, vp, C.POINTER(CGOpts), C.POINTER(SolveInfo)]),
             "omen_density_accum": (i, [vp, vp, vp, i, vp, d, vp]),
             "omen_deposit": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
@@ -347,3 +349,25 @@ def omen_scf(ctx: Context, lat: Lattice, params, grid, phi_dev, donor_rho_dev, n
     if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
         ctx.check(s)
     return info.as_dict(), s
+
+
+def omen_hx_kbatch(ctx: Context, ham: Hamiltonian, kpts, x_dev, y_dev, sigma=0.0):
+    """y_k = (H(k) - sigma) x_k for every wave vector (device buffers [nk][nrows])."""
+    k = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 3)
+    ctx.check(lib().omen_hx_kbatch(ctx.handle, ham.handle, len(k), k.ctypes.data, _ptr(x_dev), _ptr(y_dev), float(sigma)))
+
+
+def omen_eigs_kbatch(ctx: Context, ham: Hamiltonian, kpts, nev, which=OMEN_LOWEST, sigma=0.0, tol=1e-9,
+                     max_iter=1000, basis=None, evecs_dev=None, raise_on_noconv=True):
+    """nev eigenpairs per wave vector, all k in lockstep.  Returns (evals [nk, nev], info, status)."""
+    k = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 3)
+    if basis is None:
+        basis = max(32, 2 * nev + 4)
+    o = EigOpts(int(nev), int(which), float(sigma), float(tol), int(max_iter), 1, int(basis), None, None)
+    ev = np.zeros((len(k), nev))
+    info = EigInfo()
+    s = lib().omen_eigs_kbatch(ctx.handle, ham.handle, len(k), k.ctypes.data, C.byref(o), ev.ctypes.data,
+                               _ptr(evecs_dev), C.byref(info))
+    if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
+        ctx.check(s)
+    return ev, info.as_dict(), s
