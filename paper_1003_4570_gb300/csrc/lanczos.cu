@@ -13,6 +13,8 @@
 // values) are accumulated and kept in FP64.  OMEN_F32_REFINE64 finishes with FP64
 // Rayleigh–Ritz steps on span{X, H X - X Lambda}.
 #include <algorithm>
+#include <omp.h>
+
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -1515,7 +1517,7 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
   std::vector<std::vector<cd>> Y(P);
   std::vector<char> conv(P, 0);
   int jstart = 0, nbas = 1, iter = 0, restarts = 0, since = 0;
-  const int check_every = std::max(4, std::min(32, m / 4));
+  const int check_every = std::max(8, m / 2);
   while (true) {
     s = apply(slot(jstart), Wb.p);
     for (int pass = 0; pass < 2 && s == OMEN_OK; ++pass) {
@@ -1541,6 +1543,9 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
     if (flag) { s = set_err(ctx, OMEN_ENUMERIC, "Lanczos breakdown or non-finite value in the k batch"); break; }
     bool all = true;
     std::vector<double> betas(P);
+    std::vector<int> bad(P, 0);
+    // the P projected eigenproblems are independent: one host thread each
+#pragma omp parallel for schedule(dynamic)
     for (int p = 0; p < P; ++p) {
       const cd* T = Th.data() + (size_t)p * tps;
       std::vector<cd> Tn((size_t)nbas * nbas);
@@ -1554,7 +1559,7 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
       betas[p] = std::real(T[nbas + (size_t)jstart * ldT]);
       theta[p].assign(nbas, 0.0);
       Y[p].assign((size_t)nbas * nbas, cd(0));
-      if (hermitian_eig(nbas, Tn.data(), theta[p].data(), Y[p].data())) { s = set_err(ctx, OMEN_ENUMERIC, "projected eigenproblem"); break; }
+      if (hermitian_eig(nbas, Tn.data(), theta[p].data(), Y[p].data())) { bad[p] = 1; continue; }
       std::vector<double> lam(nev), res(nev), bd;
       for (int i = 0; i < nev; ++i) {
         const double rA = std::fabs(betas[p]) * std::abs(Y[p][jstart + (size_t)i * nbas]);
@@ -1567,6 +1572,9 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
         error_bounds(theta[p], lam, res, bd);
       }
       conv[p] = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+    }
+    for (int p = 0; p < P; ++p) {
+      if (bad[p]) s = set_err(ctx, OMEN_ENUMERIC, "projected eigenproblem of k %d did not converge", p);
       all = all && conv[p];
     }
     if (s != OMEN_OK) break;

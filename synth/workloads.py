@@ -192,3 +192,46 @@ def delta_layer(nxy: int, nz_cells: int, seed: int = 5):
     in z, gapped sp3d5s* Si parameters; returns (spec, params, (N_s, w))."""
     spec = lattice_spec(nxy, nxy, nz_cells, (2, 2, 0), seed)
     return spec, gapped_si_params(), draw_doping(seed)
+
+
+def donor_sheet_potential(spec: LatticeSpec, seed: int, lam_tf_nm: float, eps_r: float = 11.7,
+                          frac: float = 0.25):
+    """Onsite potential energy (eV per atom) of a seeded donor sheet: a fraction `frac` of the
+    atoms of the (001) atomic plane nearest mid-z (stream 4) carry +e, screened Coulomb
+    U(r) = -(e^2 / (4 pi eps0 eps_r r)) exp(-r / lam_TF), summed over the donors and their
+    lateral periodic images with r <= 8 lam_TF; r is clamped at the bond length a sqrt(3)/4."""
+    g = rng(seed, STREAM_DONOR)
+    a = spec.a_nm
+    iz, iy, ix = np.meshgrid(np.arange(spec.nz), np.arange(spec.ny), np.arange(spec.nx), indexing="ij")
+    cells = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1) * 4
+    sites = np.array([[0, 0, 0], [0, 2, 2], [2, 0, 2], [2, 2, 0], [1, 1, 1], [1, 3, 3], [3, 1, 3], [3, 3, 1]])
+    pos = ((sites[:, None, :] + cells[None, :, :]).reshape(-1, 3)) * (a / 4.0)
+    zmid = 0.5 * spec.nz * a
+    zs = np.unique(pos[:, 2])
+    zplane = zs[np.argmin(np.abs(zs - zmid))]
+    plane = np.nonzero(np.abs(pos[:, 2] - zplane) < 1e-9)[0]
+    nd = max(1, int(round(frac * len(plane))))
+    donors = pos[g.choice(plane, size=nd, replace=False)]
+    Lx, Ly = spec.nx * a, spec.ny * a
+    rc = 8.0 * lam_tf_nm
+    nix, niy = int(np.ceil(rc / Lx)) + 1, int(np.ceil(rc / Ly)) + 1
+    coul = 1.439964547 / eps_r           # e^2 / (4 pi eps0) in eV nm, screened by eps_r
+    rmin = a * np.sqrt(3.0) / 4.0
+    U = np.zeros(len(pos))
+    for sx in range(-nix, nix + 1):
+        for sy in range(-niy, niy + 1):
+            img = donors + np.array([sx * Lx, sy * Ly, 0.0])
+            for d in img:
+                r = np.linalg.norm(pos - d[None, :], axis=1)
+                m = r <= rc
+                rr = np.maximum(r[m], rmin)
+                U[m] -= coul * np.exp(-rr / lam_tf_nm) / rr
+    return U
+
+
+def draw_kbatch_instances(seed: int, n_instances: int = 8, sizes=(2, 3, 4, 6, 8), nz: int = 80):
+    """Instance lateral sizes (stream 1) and Thomas–Fermi lengths U[1, 5] nm (stream 4)."""
+    g = rng(seed, STREAM_SPECIES)
+    lat_sizes = [int(g.choice(sizes)) for _ in range(n_instances)]
+    lam = rng(seed + 1000, STREAM_DONOR).uniform(1.0, 5.0, size=n_instances)
+    return [(s, nz, float(l)) for s, l in zip(lat_sizes, lam)]
