@@ -283,7 +283,9 @@ typedef struct {
   double e_cut;              /* only states above e_cut hold electrons (conduction band) */
   double eig_tol;
   int eig_block, eig_basis, eig_max_iter;
-  double mix;                /* linear mixing: phi <- phi + mix (phi_out - phi) */
+  double mix;                /* mixing weight beta */
+  int mix_history;           /* 0: linear mixing phi <- phi + beta F, F = phi_out - phi;
+                                m > 0: Anderson mixing over the last m iterations */
   double tol_V;              /* stop when max |phi_out - phi| < tol_V */
   int max_iter;
   omen_cg_opts cg;
@@ -301,10 +303,52 @@ typedef struct {
 
 /* Self-consistent Schrödinger–Poisson loop (paper Section III-A): potential -> onsite
  * U = -phi at the atoms -> eigenstates per k -> Fermi level by neutrality -> electron charge
- * -> Poisson -> linear mixing, until max |phi_out - phi| < tol_V.  phi_dev: grid potential, start
+ * -> Poisson -> mixing (linear or Anderson), until max |phi_out - phi| < tol_V.  phi_dev: grid potential, start
  * value in (zeros = zero-field start), converged potential out.  ENOCONV at max_iter;
  * ENUMERIC if the highest computed state of some k is occupied above 1e-12 (nev too small). */
 omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* desc, double* phi_dev, omen_scf_info* info);
+
+/* ---- learned warm start (no counterpart in the paper) ------------------------------------ */
+/* A 3-layer perceptron maps the doping profile to the self-consistent potential, giving the
+ * Schrödinger–Poisson loop (Section III-A) a start closer to its fixed point than zero field.
+ * x (n_in) -> tanh(W1 x + b1) -> tanh(W2 . + b2) -> W3 . + b3 (n_out).  BF16 weight copies are
+ * used in every product with FP32 accumulation; FP32 master weights take Adam updates.
+ * Parameters on the host: W1 [n_hidden1][n_in], b1, W2 [n_hidden2][n_hidden1], b2,
+ * W3 [n_out][n_hidden2], b3, concatenated, FP32. */
+typedef struct omen_mlp omen_mlp;
+typedef struct {
+  int n_in, n_hidden1, n_hidden2, n_out;   /* 256, 512, 512, 256 */
+  double feat_log10_shift;   /* feature x_j = (log10(max(N_D(z_j), 1e15 m^-3)) - shift) / scale */
+  double feat_log10_scale;
+  double target_scale;       /* output y_j = phi(z_j) [V] / target_scale */
+} omen_mlp_desc;
+/* Profiles are sampled at z_j = (j + 1/2) Lz / n from the lateral mean of the grid planes
+ * (linear interpolation, 0 on the grounded planes). */
+
+omen_status omen_mlp_create(omen_ctx* ctx, const omen_mlp_desc* desc, const float* params_host, omen_mlp** out);
+void omen_mlp_free(omen_mlp* mlp);
+long long omen_mlp_param_count(const omen_mlp* mlp);
+/* FP32 master parameters, or (bf16_rounded = 1) the weights as the products use them. */
+omen_status omen_mlp_get_params(omen_ctx* ctx, const omen_mlp* mlp, float* params_host, int bf16_rounded);
+/* Y_dev [batch][n_out] = network(X_dev [batch][n_in]). */
+omen_status omen_mlp_forward(omen_ctx* ctx, omen_mlp* mlp, const float* X_dev, int batch, float* Y_dev);
+/* Gradients of the mean squared error w.r.t. every parameter (host, parameter layout) and the
+ * loss, without updating. */
+omen_status omen_mlp_gradients(omen_ctx* ctx, omen_mlp* mlp, const float* X_dev, const float* T_dev, int batch,
+                               float* grad_host, float* loss_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error. */
+omen_status omen_mlp_train_step(omen_ctx* ctx, omen_mlp* mlp, const float* X_dev, const float* T_dev, int batch,
+                                double lr, float* loss_host);
+/* Features of a donor density on the grid (C/m^3) -> x_dev [n_in]; targets of a potential on
+ * the grid (V) -> t_dev [n_out]. */
+omen_status omen_mlp_features(omen_ctx* ctx, const omen_mlp* mlp, const omen_grid* grid, const double* donor_rho_dev,
+                              float* x_dev);
+omen_status omen_mlp_targets(omen_ctx* ctx, const omen_mlp* mlp, const omen_grid* grid, const double* phi_dev,
+                             float* t_dev);
+/* Start potential for omen_scf: network(features(donor_rho)) interpolated onto the grid planes
+ * (0 V on the grounded planes), the same on every lateral point: phi_dev [(nz-1)*ny*nx]. */
+omen_status omen_mlp_warm_start(omen_ctx* ctx, omen_mlp* mlp, const omen_grid* grid, const double* donor_rho_dev,
+                                double* phi_dev);
 
 #ifdef __cplusplus
 }

@@ -3,8 +3,8 @@
 Paper Section III-A: eigenstates of the tight-binding Hamiltonian -> charge (Fermi level by
 neutrality) -> finite-difference Poisson -> potential back into the Hamiltonian, repeated
 until self-consistent.  The paper's outer iteration is Newton–Raphson; this loop uses linear
-mixing phi <- phi + mix (phi_out - phi) and stops when max |phi_out - phi| < tol_V, the
-reading the GPU path follows.  Electron potential energy U = -phi (eV per V).  Only states
+mixing phi <- phi + mix (phi_out - phi), or Anderson mixing over the last mix_history iterates,
+and stops when max |phi_out - phi| < tol_V, the reading the GPU path follows.  Electron potential energy U = -phi (eV per V).  Only states
 above e_cut (mid-gap) hold electrons; g_s = 2.
 """
 from __future__ import annotations
@@ -30,13 +30,30 @@ def nearest_states(H, sigma, nev, dense_limit=2500):
     return eigs.nearest_shift_invert(H, sigma, nev)
 
 
+def anderson_update(phi, F, dX, dF, beta):
+    """Anderson mixing (Anderson, J. ACM 12, 547 (1965)): gamma minimises |F - sum_j gamma_j dF_j|,
+    phi_next = phi + beta F - sum_j gamma_j (dX_j + beta dF_j)."""
+    if not dF:
+        return phi + beta * F
+    A = np.stack([d.ravel() for d in dF], axis=1)
+    G = A.T @ A
+    G = G + 1e-12 * np.max(np.diag(G)) * np.eye(len(dF))
+    gamma = np.linalg.solve(G, A.T @ F.ravel())
+    out = phi + beta * F
+    for g, dx, df in zip(gamma, dX, dF):
+        out = out - g * (dx + beta * df)
+    return out
+
+
 def scf(spec, params, grid, donor_rho, n_electrons, kT, kpts, kweights, nev, sigma, e_cut,
-        mix=0.1, tol_V=1e-6, max_iter=300, phi0=None, gs=2.0):
+        mix=0.1, tol_V=1e-6, max_iter=300, phi0=None, gs=2.0, mix_history=0):
     pos = atom_positions_nm(spec)
     bonds = lattice.find_bonds(spec.nx, spec.ny, spec.nz, spec.periodic)
     phi = np.zeros(grid.shape) if phi0 is None else np.array(phi0, float).reshape(grid.shape)
     history = []
     EF = None
+    dX, dF = [], []
+    F_prev = X_prev = None
     for it in range(1, max_iter + 1):
         U = -charge.gather(grid, phi, pos)
         levels, weights, states = [], [], []
@@ -62,7 +79,18 @@ def scf(spec, params, grid, donor_rho, n_electrons, kT, kpts, kweights, nev, sig
         history.append(dV)
         if dV < tol_V:
             return phi, {"iterations": it, "E_F": EF, "dV_inf": dV, "history": history, "n_atom": n_atom}
-        phi = phi + mix * (phi_out - phi)
+        if mix_history <= 0:
+            phi = phi + mix * (phi_out - phi)
+            continue
+        F = phi_out - phi
+        if F_prev is not None:
+            dF.append(F - F_prev)
+            dX.append(phi - X_prev)
+            if len(dF) > mix_history:
+                dF.pop(0)
+                dX.pop(0)
+        F_prev, X_prev = F, phi
+        phi = anderson_update(phi, F, dX, dF, mix)
     return phi, {"iterations": max_iter, "E_F": EF, "dV_inf": history[-1], "history": history,
                  "converged": False}
 

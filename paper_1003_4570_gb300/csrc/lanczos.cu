@@ -398,6 +398,10 @@ struct KrylovOps {
   size_t partial_cap = 0;  // in double2
   double2* d_small = nullptr;  // reduced results / small matrices
   size_t small_cap = 0;
+  void* qr_tmp = nullptr;      // copy of a block during Cholesky QR
+  size_t qr_cap = 0;
+  double2* d_hs = nullptr;     // projection sums of the block path
+  size_t hs_cap = 0;
   int sm_count = 148;
 
   omen_status init() {
@@ -413,6 +417,8 @@ struct KrylovOps {
   void release() {
     cudaFree(d_partial);
     cudaFree(d_small);
+    cudaFree(qr_tmp);
+    cudaFree(d_hs);
   }
   char* col(void* base, long long j) const { return static_cast<char*>(base) + (size_t)j * n * el; }
 
@@ -731,15 +737,20 @@ struct KrylovOps {
         if (dmin < 1e-6 * dmax) { deficient = 1; return OMEN_OK; }
       }
       upper_inverse(nb, Rk.data(), Ri.data());
-      // W <- W Ri : combine into W itself is not allowed (aliasing) -> use R^-1 on a copy
-      void* tmpW = nullptr;
-      if (cudaMallocAsync(&tmpW, (size_t)nb * n * el, ctx->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return set_err(ctx, OMEN_ENOMEM, "QR work vectors");
+      // W <- W Ri from a copy of W (the combination may not alias its input)
+      const size_t need = (size_t)nb * n * el;
+      if (need > qr_cap) {
+        cudaFree(qr_tmp);
+        qr_tmp = nullptr;
+        qr_cap = 0;
+        if (cudaMalloc(&qr_tmp, need) != cudaSuccess) {
+          cudaGetLastError();
+          return set_err(ctx, OMEN_ENOMEM, "QR work vectors");
+        }
+        qr_cap = need;
       }
-      OMEN_CUDA(ctx, cudaMemcpyAsync(tmpW, W, (size_t)nb * n * el, cudaMemcpyDeviceToDevice, ctx->stream));
-      omen_status s2 = combine(tmpW, nb, Ri, nb, W, 1.0, 0.0);
-      cudaFreeAsync(tmpW, ctx->stream);
+      OMEN_CUDA(ctx, cudaMemcpyAsync(qr_tmp, W, need, cudaMemcpyDeviceToDevice, ctx->stream));
+      omen_status s2 = combine(qr_tmp, nb, Ri, nb, W, 1.0, 0.0);
       if (s2 != OMEN_OK) return s2;
       // R <- Rk R
       std::vector<cd> Rn((size_t)nb * nb, cd(0));
@@ -759,17 +770,37 @@ struct KrylovOps {
   omen_status orthogonalise(const void* V, int nv, void* W, int nb, std::vector<cd>* hsum) {
     if (hsum) hsum->assign((size_t)nv * nb, cd(0));
     if (nv == 0) return OMEN_OK;
-    std::vector<cd> h;
+    if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "orthogonalise: too many columns");
+    const size_t need = (size_t)nv * nb * 2;   // per-pass coefficients + running sums
+    if (need > hs_cap) {
+      cudaFree(d_hs);
+      d_hs = nullptr;
+      hs_cap = 0;
+      if (cudaMalloc(&d_hs, need * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, OMEN_ENOMEM, "projection sums");
+      }
+      hs_cap = need;
+    }
+    double2* h = d_hs;
+    double2* sum = d_hs + (size_t)nv * nb;
+    OMEN_CUDA(ctx, cudaMemsetAsync(sum, 0, sizeof(double2) * nv * nb, ctx->stream));
     for (int pass = 0; pass < 2; ++pass) {
-      omen_status s = dots(V, nv, W, nb, h);
+      omen_status s = dots_dev(V, nv, W, nb, h, sum, nv, 0);
       if (s != OMEN_OK) return s;
-      s = combine(V, nv, h, nb, W, -1.0, 1.0);
+      s = combine_dev(V, nv, h, nb, W, -1.0, 1.0);
       if (s != OMEN_OK) return s;
-      if (hsum)
-        for (size_t t = 0; t < h.size(); ++t) (*hsum)[t] += h[t];
+    }
+    if (hsum) {
+      OMEN_CUDA(ctx, cudaMemcpyAsync(hsum->data(), sum, sizeof(double2) * nv * nb, cudaMemcpyDeviceToHost, ctx->stream));
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      for (const cd& v : *hsum)
+        if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+          return set_err(ctx, OMEN_ENUMERIC, "non-finite value in a Krylov inner product");
     }
     return OMEN_OK;
   }
+
 };
 
 // ---------------------------------------------------------------------------------------

@@ -46,6 +46,41 @@ __global__ void mix_kernel(double* __restrict__ phi, const double* __restrict__ 
     phi[i] += mix * (out[i] - phi[i]);
 }
 
+// Anderson mixing (Anderson, J. ACM 12, 547 (1965)) on the grid potential.
+// F = phi_out - phi.  With the differences dX_j, dF_j of the last h iterates (slots in a ring),
+// gamma = argmin |F - dF gamma|, phi <- phi + beta F - sum_j gamma_j (dX_j + beta dF_j).
+// part[b * (h+1)^2 + ...]: per-block partial Gram sums of the vectors (dF_0..dF_{h-1}, F).
+__global__ void gram_kernel(const double* __restrict__ dF, long long ld, int h, const double* __restrict__ F, long long n,
+                            double* __restrict__ part) {
+  const int nv = h + 1;
+  extern __shared__ double sh[];
+  for (int e = threadIdx.x; e < nv * nv; e += blockDim.x) sh[e] = 0.0;
+  __syncthreads();
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double v[9];
+    for (int a = 0; a < nv; ++a) v[a] = (a < h) ? dF[a * ld + r] : F[r];
+    for (int a = 0; a < nv; ++a)
+      for (int b = a; b < nv; ++b) atomicAdd(&sh[a * nv + b], v[a] * v[b]);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nv * nv; e += blockDim.x) part[(size_t)blockIdx.x * nv * nv + e] = sh[e];
+}
+
+__global__ void anderson_kernel(double* __restrict__ phi, const double* __restrict__ F, const double* __restrict__ dX,
+                                const double* __restrict__ dF, long long ld, int h, const double* __restrict__ gamma,
+                                double beta, long long n) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double v = phi[r] + beta * F[r];
+    for (int j = 0; j < h; ++j) v -= gamma[j] * (dX[j * ld + r] + beta * dF[j * ld + r]);
+    phi[r] = v;
+  }
+}
+
+__global__ void diff_kernel(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out, long long n) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+    out[r] = a[r] - b[r];
+}
+
 static double fermi_occ(double x) {
   if (x > 0) {
     const double e = exp(-x);
@@ -98,12 +133,16 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
   }
   const long long nrows = hams[0]->nrows;
   const size_t elem = hams[0]->is_complex ? 16 : 8;
-  DevVec phi_atom, U, n_atom, q, rho, phi_out, part, psi, v0;
+  DevVec phi_atom, U, n_atom, q, rho, phi_out, part, psi, v0, Fcur, Fprev, Xprev, dXh, dFh, gpart, gam;
+  const int H = std::max(0, std::min(8, d->mix_history));
   const int nblk = 256;
   if (!phi_atom.alloc(sizeof(double) * N) || !U.alloc(sizeof(double) * N) || !n_atom.alloc(sizeof(double) * N) ||
       !q.alloc(sizeof(double) * N) || !rho.alloc(sizeof(double) * ng) || !phi_out.alloc(sizeof(double) * ng) ||
       !part.alloc(sizeof(double) * nblk) || !psi.alloc(elem * nrows * (size_t)d->nev * d->nk) ||
-      !v0.alloc(elem * nrows * (size_t)std::max(1, d->eig_block))) {
+      !v0.alloc(elem * nrows * (size_t)std::max(1, d->eig_block)) || !Fcur.alloc(sizeof(double) * ng) ||
+      !Fprev.alloc(sizeof(double) * ng) || !Xprev.alloc(sizeof(double) * ng) ||
+      !dXh.alloc(sizeof(double) * ng * std::max(1, H)) || !dFh.alloc(sizeof(double) * ng * std::max(1, H)) ||
+      !gpart.alloc(sizeof(double) * 81 * 256) || !gam.alloc(sizeof(double) * 8)) {
     free_hams();
     return set_err(ctx, OMEN_ENOMEM, "SCF work buffers");
   }
@@ -114,6 +153,7 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
   omen_status st = OMEN_OK;
   double EF = 0.0;
   int it = 0;
+  int nhist_total = 0;
   for (it = 1; it <= d->max_iter; ++it) {
     // potential at the atoms -> onsite energies
     st = omen_gather(ctx, L, G, phi, phi_atom.d());
@@ -127,7 +167,9 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
       eo.nev = d->nev;
       eo.which = OMEN_NEAREST;
       eo.sigma = d->sigma;
-      eo.tol = d->eig_tol;
+      // early iterations need eigenpairs only to the accuracy of the current potential error
+      eo.tol = (it == 1 || inf->dV_inf <= 0.0) ? std::max(d->eig_tol, 1e-6)
+                                                : std::max(d->eig_tol, std::min(1e-5, 1e-4 * inf->dV_inf));
       eo.max_iter = d->eig_max_iter;
       eo.block = d->eig_block;
       eo.basis = d->eig_basis;
@@ -207,7 +249,67 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
       inf->converged = 1;
       break;
     }
-    mix_kernel<<<gg, 256, 0, ctx->stream>>>(phi, phi_out.d(), d->mix, ng);
+    if (H == 0) {
+      mix_kernel<<<gg, 256, 0, ctx->stream>>>(phi, phi_out.d(), d->mix, ng);
+      continue;
+    }
+    // Anderson: F = phi_out - phi; history of differences in a ring of H slots
+    diff_kernel<<<gg, 256, 0, ctx->stream>>>(phi_out.d(), phi, Fcur.d(), ng);
+    if (nhist_total > 0) {
+      const int slot = (nhist_total - 1) % H;
+      diff_kernel<<<gg, 256, 0, ctx->stream>>>(Fcur.d(), Fprev.d(), dFh.d() + (size_t)slot * ng, ng);
+      diff_kernel<<<gg, 256, 0, ctx->stream>>>(phi, Xprev.d(), dXh.d() + (size_t)slot * ng, ng);
+    }
+    OMEN_CUDA(ctx, cudaMemcpyAsync(Fprev.p, Fcur.p, sizeof(double) * ng, cudaMemcpyDeviceToDevice, ctx->stream));
+    OMEN_CUDA(ctx, cudaMemcpyAsync(Xprev.p, phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, ctx->stream));
+    const int h = std::min(nhist_total, H);
+    ++nhist_total;
+    std::vector<double> gamma(8, 0.0);
+    if (h > 0) {
+      const int nv = h + 1;
+      const unsigned gb = (unsigned)std::min<long long>(256, (ng + 255) / 256);
+      gram_kernel<<<gb, 256, sizeof(double) * nv * nv, ctx->stream>>>(dFh.d(), ng, h, Fcur.d(), ng, gpart.d());
+      std::vector<double> hp((size_t)gb * nv * nv);
+      OMEN_CUDA(ctx, cudaMemcpyAsync(hp.data(), gpart.p, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      std::vector<double> G((size_t)nv * nv, 0.0);
+      for (unsigned b = 0; b < gb; ++b)
+        for (int e = 0; e < nv * nv; ++e) G[e] += hp[(size_t)b * nv * nv + e];
+      // normal equations (dF^T dF + tiny I) gamma = dF^T F, solved by Gaussian elimination
+      std::vector<double> A((size_t)h * h), rhs(h);
+      double diag = 0.0;
+      for (int a = 0; a < h; ++a) diag = std::max(diag, G[a * nv + a]);
+      for (int a = 0; a < h; ++a) {
+        for (int b2 = 0; b2 < h; ++b2) A[a * h + b2] = (a <= b2) ? G[a * nv + b2] : G[b2 * nv + a];
+        A[a * h + a] += 1e-12 * diag;
+        rhs[a] = G[a * nv + h];
+      }
+      for (int c = 0; c < h; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < h; ++r)
+          if (std::fabs(A[r * h + c]) > std::fabs(A[piv * h + c])) piv = r;
+        if (piv != c) {
+          for (int k2 = 0; k2 < h; ++k2) std::swap(A[c * h + k2], A[piv * h + k2]);
+          std::swap(rhs[c], rhs[piv]);
+        }
+        const double pv = A[c * h + c];
+        if (pv == 0.0) continue;
+        for (int r = c + 1; r < h; ++r) {
+          const double f = A[r * h + c] / pv;
+          for (int k2 = c; k2 < h; ++k2) A[r * h + k2] -= f * A[c * h + k2];
+          rhs[r] -= f * rhs[c];
+        }
+      }
+      for (int c = h - 1; c >= 0; --c) {
+        double v = rhs[c];
+        for (int k2 = c + 1; k2 < h; ++k2) v -= A[c * h + k2] * gamma[k2];
+        gamma[c] = (A[c * h + c] != 0.0) ? v / A[c * h + c] : 0.0;
+      }
+    }
+    // ring slots hold the differences in order slot = (iteration - 1) % H; gamma is in Gram order
+    // (slot order), which the update uses directly
+    OMEN_CUDA(ctx, cudaMemcpyAsync(gam.p, gamma.data(), sizeof(double) * 8, cudaMemcpyHostToDevice, ctx->stream));
+    anderson_kernel<<<gg, 256, 0, ctx->stream>>>(phi, Fcur.d(), dXh.d(), dFh.d(), ng, h, gam.d(), d->mix, ng);
   }
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   free_hams();

@@ -80,8 +80,8 @@ class SCFDesc(C.Structure):
                 ("donor_rho_dev", C.c_void_p), ("n_electrons", C.c_double), ("kT", C.c_double), ("nk", C.c_int),
                 ("k_host", C.c_void_p), ("kw_host", C.c_void_p), ("nev", C.c_int), ("sigma", C.c_double),
                 ("e_cut", C.c_double), ("eig_tol", C.c_double), ("eig_block", C.c_int), ("eig_basis", C.c_int),
-                ("eig_max_iter", C.c_int), ("mix", C.c_double), ("tol_V", C.c_double), ("max_iter", C.c_int),
-                ("cg", CGOpts)]
+                ("eig_max_iter", C.c_int), ("mix", C.c_double), ("mix_history", C.c_int), ("tol_V", C.c_double),
+                ("max_iter", C.c_int), ("cg", CGOpts)]
 
 
 class SCFInfo(C.Structure):
@@ -91,6 +91,11 @@ class SCFInfo(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MLPDesc(C.Structure):
+    _fields_ = [("n_in", C.c_int), ("n_hidden1", C.c_int), ("n_hidden2", C.c_int), ("n_out", C.c_int),
+                ("feat_log10_shift", C.c_double), ("feat_log10_scale", C.c_double), ("target_scale", C.c_double)]
 
 
 _lib = None
@@ -127,6 +132,16 @@ def lib():
             "omen_gather": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
             "omen_fermi_level": (i, [vp, vp, i, d, d, C.POINTER(d)]),
             "omen_scf": (i, [vp, C.POINTER(SCFDesc), vp, C.POINTER(SCFInfo)]),
+            "omen_mlp_create": (i, [vp, C.POINTER(MLPDesc), vp, C.POINTER(vp)]),
+            "omen_mlp_free": (None, [vp]),
+            "omen_mlp_param_count": (ll, [vp]),
+            "omen_mlp_get_params": (i, [vp, vp, vp, i]),
+            "omen_mlp_forward": (i, [vp, vp, vp, i, vp]),
+            "omen_mlp_gradients": (i, [vp, vp, vp, vp, i, vp, C.POINTER(C.c_float)]),
+            "omen_mlp_train_step": (i, [vp, vp, vp, vp, i, d, C.POINTER(C.c_float)]),
+            "omen_mlp_features": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
+            "omen_mlp_targets": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
+            "omen_mlp_warm_start": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -332,7 +347,8 @@ def omen_fermi_level(E, level_weight, n_target, kT):
 
 def omen_scf(ctx: Context, lat: Lattice, params, grid, phi_dev, donor_rho_dev, n_electrons, kT, kpts, kweights,
              nev, sigma, e_cut, precision=OMEN_F64, eig_tol=1e-9, eig_block=1, eig_basis=None, eig_max_iter=20000,
-             mix=0.1, tol_V=1e-6, max_iter=300, cg_rtol=1e-13, cg_max_iter=100000, raise_on_noconv=True):
+             mix=0.1, tol_V=1e-6, max_iter=300, cg_rtol=1e-13, cg_max_iter=100000, raise_on_noconv=True,
+             mix_history=0):
     """Self-consistent loop in place on phi_dev.  Returns (info dict, status)."""
     tp = tb_params_struct(params)
     g = grid_struct(grid)
@@ -342,8 +358,8 @@ def omen_scf(ctx: Context, lat: Lattice, params, grid, phi_dev, donor_rho_dev, n
         eig_basis = max(4 * eig_block, ((2 * nev + 2 * eig_block + eig_block - 1) // eig_block) * eig_block)
     d = SCFDesc(lat.handle, C.addressof(tp), int(precision), C.addressof(g), _ptr(donor_rho_dev), float(n_electrons),
                 float(kT), len(kw), k.ctypes.data, kw.ctypes.data, int(nev), float(sigma), float(e_cut), float(eig_tol),
-                int(eig_block), int(eig_basis), int(eig_max_iter), float(mix), float(tol_V), int(max_iter),
-                CGOpts(float(cg_rtol), int(cg_max_iter)))
+                int(eig_block), int(eig_basis), int(eig_max_iter), float(mix), int(mix_history), float(tol_V),
+                int(max_iter), CGOpts(float(cg_rtol), int(cg_max_iter)))
     info = SCFInfo()
     s = lib().omen_scf(ctx.handle, C.byref(d), _ptr(phi_dev), C.byref(info))
     if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
@@ -371,3 +387,66 @@ def omen_eigs_kbatch(ctx: Context, ham: Hamiltonian, kpts, nev, which=OMEN_LOWES
     if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
         ctx.check(s)
     return ev, info.as_dict(), s
+
+
+class MLP:
+    def __init__(self, ctx, handle, desc):
+        self.ctx, self.handle, self.desc = ctx, handle, desc
+
+    @property
+    def nparams(self):
+        return lib().omen_mlp_param_count(self.handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().omen_mlp_free(self.handle)
+            self.handle = None
+
+
+def omen_mlp_create(ctx: Context, params, sizes=(256, 512, 512, 256), feat_shift=21.0, feat_scale=6.0,
+                    target_scale=0.2) -> MLP:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    d = MLPDesc(*[int(v) for v in sizes], float(feat_shift), float(feat_scale), float(target_scale))
+    h = C.c_void_p()
+    ctx.check(lib().omen_mlp_create(ctx.handle, C.byref(d), p.ctypes.data, C.byref(h)))
+    return MLP(ctx, h, d)
+
+
+def omen_mlp_get_params(ctx: Context, mlp: MLP, bf16_rounded=False):
+    out = np.zeros(mlp.nparams, np.float32)
+    ctx.check(lib().omen_mlp_get_params(ctx.handle, mlp.handle, out.ctypes.data, int(bool(bf16_rounded))))
+    return out
+
+
+def omen_mlp_forward(ctx: Context, mlp: MLP, X_dev, batch, Y_dev):
+    ctx.check(lib().omen_mlp_forward(ctx.handle, mlp.handle, _ptr(X_dev), int(batch), _ptr(Y_dev)))
+
+
+def omen_mlp_gradients(ctx: Context, mlp: MLP, X_dev, T_dev, batch):
+    g = np.zeros(mlp.nparams, np.float32)
+    loss = C.c_float()
+    ctx.check(lib().omen_mlp_gradients(ctx.handle, mlp.handle, _ptr(X_dev), _ptr(T_dev), int(batch), g.ctypes.data,
+                                       C.byref(loss)))
+    return g, loss.value
+
+
+def omen_mlp_train_step(ctx: Context, mlp: MLP, X_dev, T_dev, batch, lr=1e-3, want_loss=True):
+    loss = C.c_float()
+    ctx.check(lib().omen_mlp_train_step(ctx.handle, mlp.handle, _ptr(X_dev), _ptr(T_dev), int(batch), float(lr),
+                                        C.byref(loss) if want_loss else None))
+    return loss.value
+
+
+def omen_mlp_features(ctx: Context, mlp: MLP, grid, donor_rho_dev, x_dev):
+    g = grid_struct(grid)
+    ctx.check(lib().omen_mlp_features(ctx.handle, mlp.handle, C.byref(g), _ptr(donor_rho_dev), _ptr(x_dev)))
+
+
+def omen_mlp_targets(ctx: Context, mlp: MLP, grid, phi_dev, t_dev):
+    g = grid_struct(grid)
+    ctx.check(lib().omen_mlp_targets(ctx.handle, mlp.handle, C.byref(g), _ptr(phi_dev), _ptr(t_dev)))
+
+
+def omen_mlp_warm_start(ctx: Context, mlp: MLP, grid, donor_rho_dev, phi_dev):
+    g = grid_struct(grid)
+    ctx.check(lib().omen_mlp_warm_start(ctx.handle, mlp.handle, C.byref(g), _ptr(donor_rho_dev), _ptr(phi_dev)))

@@ -235,3 +235,15 @@ def draw_kbatch_instances(seed: int, n_instances: int = 8, sizes=(2, 3, 4, 6, 8)
     lat_sizes = [int(g.choice(sizes)) for _ in range(n_instances)]
     lam = rng(seed + 1000, STREAM_DONOR).uniform(1.0, 5.0, size=n_instances)
     return [(s, nz, float(l)) for s, l in zip(lat_sizes, lam)]
+
+
+def mlp_init(seed: int, sizes=(256, 512, 512, 256)) -> np.ndarray:
+    """Glorot-uniform weights, zero biases, flat FP32 in the C-ABI layout (stream 7)."""
+    g = rng(seed, 7)
+    parts = []
+    for l in range(3):
+        fan_in, fan_out = sizes[l], sizes[l + 1]
+        a = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(g.uniform(-a, a, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)

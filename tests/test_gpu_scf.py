@@ -1,5 +1,7 @@
 """Parity of the Schrödinger–Poisson pieces on the GPU against the oracle.
 
+The self-consistent loop is compared with linear and with Anderson mixing.
+
 Poisson CG against the oracle's sparse direct solve (1e-10 of max |phi|, including the
 11 x 11 x 217 grid of the 4x4x80-cell delta layer); cloud-in-cell deposit and gather
 (1e-12 relative); electrons per atom from eigenvectors; Fermi level; and the full
@@ -66,17 +68,19 @@ def test_deposit_gather_density_fermi(ctx):
     assert abs((W * charge.fermi(E, ef, 0.01)).sum() - 13.7) < 1e-9
 
 
-def test_scf_matches_oracle(ctx):
+@pytest.mark.parametrize("hist", [0, 6])
+def test_scf_matches_oracle(ctx, hist):
     from paper_1003_4570_gb300 import omen
-    c = small_delta_case()
+    c = small_delta_case(ns=1e14 if hist == 0 else 1.7e14)
     phi_ref, info_ref = scf.scf(c["spec"], c["params"], c["grid"], c["donor_rho"], c["n_electrons"], c["kT"],
                                 c["kpts"], c["kweights"], c["nev"], c["sigma"], c["e_cut"], mix=0.3, tol_V=1e-6,
-                                max_iter=200)
+                                max_iter=200, mix_history=hist)
     lat = omen.omen_build_lattice(ctx, c["spec"])
     phi = torch.zeros(c["grid"].shape, dtype=torch.float64, device="cuda")
     info, st = omen.omen_scf(ctx, lat, c["params"], c["grid"], phi, torch.from_numpy(c["donor_rho"]).cuda(),
                              c["n_electrons"], c["kT"], c["kpts"], c["kweights"], c["nev"], c["sigma"], c["e_cut"],
-                             eig_tol=1e-10, eig_block=4, eig_basis=48, mix=0.3, tol_V=1e-6, max_iter=200)
+                             eig_tol=1e-10, eig_block=4, eig_basis=48, mix=0.3, tol_V=1e-6, max_iter=200,
+                             mix_history=hist)
     assert info["converged"] == 1, info
     assert abs(info["iterations"] - info_ref["iterations"]) <= 1
     np.testing.assert_allclose(phi.cpu().numpy(), phi_ref, atol=1e-6, rtol=0)

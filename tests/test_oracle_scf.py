@@ -60,3 +60,13 @@ def test_oracle_scf_fixed_point_and_neutrality():
     area = c["grid"].Lx_nm * c["grid"].Ly_nm * 1e-18
     donors = c["donor_rho"][:, 0, 0].sum() * hz * area
     assert abs(donors - synth.Q_E * c["n_electrons"]) < 1e-9 * donors
+
+
+def test_oracle_scf_anderson_reaches_same_fixed_point():
+    c = small_delta_case()
+    args = (c["spec"], c["params"], c["grid"], c["donor_rho"], c["n_electrons"], c["kT"], c["kpts"], c["kweights"],
+            c["nev"], c["sigma"], c["e_cut"])
+    phi_lin, _ = scf.scf(*args, mix=0.3, tol_V=1e-8, max_iter=300)
+    phi_and, info = scf.scf(*args, mix=0.3, tol_V=1e-8, max_iter=300, mix_history=5)
+    assert info["dV_inf"] < 1e-8
+    assert np.abs(phi_lin - phi_and).max() < 1e-7
