@@ -210,6 +210,69 @@ def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
     return out
 
 
+def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
+    """SCF iterations and wall time from the zero-field start and from the learned start.
+
+    The network is trained here on self-consistent potentials that omen_scf itself produces
+    for seeded doping profiles (training time reported separately); held-out profiles are
+    then solved from both starts to the same 1e-6 V tolerance."""
+    import torch
+    from oracle import poisson  # grid description only (no computation)
+    spec, p, _ = synth.delta_layer(1, nzc, seed=1)
+    a = spec.a_nm
+    grid = poisson.Grid(3, 3, round(nzc * a / 0.2), a, a, nzc * a)
+    lat = omen.omen_build_lattice(ctx, spec)
+    eg = synth.GAPPED_SI_EC - synth.GAPPED_SI_EV
+    common = dict(kT=8.617333262e-5 * 4, kpts=[(0.0, 0.0, 0.0)], kweights=[1.0], nev=8,
+                  sigma=synth.GAPPED_SI_EC - 0.4 * eg, e_cut=0.5 * (synth.GAPPED_SI_EC + synth.GAPPED_SI_EV),
+                  eig_tol=1e-10, eig_block=4, eig_basis=48, mix=0.3, mix_history=6, tol_V=1e-6, max_iter=200)
+
+    def solve(seed, phi):
+        ns, w = synth.draw_doping(seed)
+        rho = torch.from_numpy(synth.donor_rho_on_grid(ns, w, grid.nx, grid.ny, grid.nz, grid.Lz_nm)).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info, st = omen.omen_scf(ctx, lat, p, grid, phi, rho, n_electrons=ns * (a * 1e-7) ** 2, **common)
+        torch.cuda.synchronize()
+        return rho, info, time.perf_counter() - t0
+
+    net = omen.omen_mlp_create(ctx, synth.mlp_init(7))
+    X = torch.empty((n_train, 256), dtype=torch.float32, device="cuda")
+    T = torch.empty((n_train, 256), dtype=torch.float32, device="cuda")
+    t_data = time.perf_counter()
+    for i in range(n_train):
+        phi = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+        rho, info, _ = solve(1000 + i, phi)
+        omen.omen_mlp_features(ctx, net, grid, rho, X[i])
+        omen.omen_mlp_targets(ctx, net, grid, phi, T[i])
+    t_data = time.perf_counter() - t_data
+    t_train = time.perf_counter()
+    for _ in range(train_steps):
+        loss = omen.omen_mlp_train_step(ctx, net, X, T, n_train, lr=1e-3, want_loss=False)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    zi, zt, li, lt = [], [], [], []
+    for j in range(n_test):
+        phi0 = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+        _, info0, s0 = solve(5000 + j, phi0)
+        ns, w = synth.draw_doping(5000 + j)
+        rho = torch.from_numpy(synth.donor_rho_on_grid(ns, w, grid.nx, grid.ny, grid.nz, grid.Lz_nm)).cuda()
+        phi1 = torch.empty(grid.shape, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        omen.omen_mlp_warm_start(ctx, net, grid, rho, phi1)
+        _, info1, s1 = solve(5000 + j, phi1)
+        zi.append(info0["iterations"]); zt.append(s0)
+        li.append(info1["iterations"]); lt.append(s1 + 0.0)
+    return {"workload": f"delta-doped Si 1x1x{nzc} cells ({spec.natoms} atoms, {spec.natoms * 10} rows), Gamma, "
+                        f"grid {grid.nx}x{grid.ny}x{grid.nz}, Anderson mixing, tol 1e-6 V",
+            "zero_field": {"iterations": zi, "seconds": zt},
+            "learned": {"iterations": li, "seconds": lt},
+            "time_ratio_zero_over_learned": float(np.sum(zt) / max(np.sum(lt), 1e-9)),
+            "training": {"profiles": n_train, "dataset_seconds": t_data, "adam_steps": train_steps,
+                         "train_seconds": t_train}}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_1003_4570_gb300 import omen
@@ -310,6 +373,7 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_extras:
         result["lanczos_500_iterations"] = measure_lanczos(ctx, omen, ham)
         result["kbatch"] = measure_kbatch(ctx, omen)
+        result["scf_learned_vs_zero"] = measure_scf(ctx, omen)
     if rank == 0 and not args.no_cpu:
         t0 = time.perf_counter()
         cspec, H, cnb = cpu_sample()

@@ -19,6 +19,8 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -385,6 +387,23 @@ __global__ void convert_kernel(const void* Xv, void* Yv, long long n) {
     Y[r] = Eo::make(Ei::re(X[r]), Ei::im(X[r]));
 }
 
+// cudaFuncSetAttribute costs a driver call: raise a kernel's dynamic shared-memory limit only
+// when a launch needs more than the largest value already set for it.
+template <typename K>
+static void smem_limit(K kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> current;   // per (device, kernel)
+  if (bytes <= 48 * 1024) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = current[{dev, reinterpret_cast<const void*>(kernel)}];
+  if (bytes > cur) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cur = bytes;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Host-side helpers bound to one vector type.
 struct KrylovOps {
@@ -448,22 +467,14 @@ struct KrylovOps {
       const int CH = chunk_rows(nbj);
       const long long nchunks = (n + CH - 1) / CH;
       const size_t need = (size_t)nchunks * na * nbj;
-      if (need > partial_cap) {
-        cudaFree(d_partial);
-        d_partial = nullptr;
-        partial_cap = 0;
-        if (cudaMalloc(&d_partial, need * sizeof(double2)) != cudaSuccess) {
-          cudaGetLastError();
-          return set_err(ctx, OMEN_ENOMEM, "partial-sum buffer");
-        }
-        partial_cap = need;
-      }
+      omen_status se = ensure_partial(need);
+      if (se != OMEN_OK) return se;
       if ((size_t)na * nbj > small_cap) return set_err(ctx, OMEN_EINVAL, "projection too large");
       const size_t shm = (size_t)nbj * CH * el;
       const void* Bj = col(const_cast<void*>(B), j0);
 #define DOTS_LAUNCH(T, Cc)                                                                          \
   do {                                                                                              \
-    cudaFuncSetAttribute(dots_partial_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+    smem_limit(dots_partial_kernel<T, Cc>, shm); \
     dots_partial_kernel<T, Cc><<<(unsigned)nchunks, kDotThreads, shm, ctx->stream>>>(A, n, na, Bj, n, nbj, n, CH, d_partial); \
   } while (0)
       if (prec == OMEN_F64) { if (cplx) DOTS_LAUNCH(double, true); else DOTS_LAUNCH(double, false); }
@@ -500,7 +511,7 @@ struct KrylovOps {
       void* Yj = col(Y, j0);
 #define COMB_LAUNCH(T, Cc)                                                                           \
   do {                                                                                               \
-    cudaFuncSetAttribute(combine_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+    smem_limit(combine_kernel<T, Cc>, shm); \
     combine_kernel<T, Cc><<<grid, 256, shm, ctx->stream>>>(A, n, na, d_small, nbj, Yj, n, n, alpha, beta); \
   } while (0)
       if (prec == OMEN_F64) { if (cplx) COMB_LAUNCH(double, true); else COMB_LAUNCH(double, false); }
@@ -513,16 +524,18 @@ struct KrylovOps {
     return OMEN_OK;
   }
 
+  // grows geometrically (cudaFree synchronises the device, so it must not happen per step)
   omen_status ensure_partial(size_t need) {
     if (need <= partial_cap) return OMEN_OK;
+    const size_t cap = std::max<size_t>({need, 2 * partial_cap, (size_t)1 << 18});
     cudaFree(d_partial);
     d_partial = nullptr;
     partial_cap = 0;
-    if (cudaMalloc(&d_partial, need * sizeof(double2)) != cudaSuccess) {
+    if (cudaMalloc(&d_partial, cap * sizeof(double2)) != cudaSuccess) {
       cudaGetLastError();
       return set_err(ctx, OMEN_ENOMEM, "partial-sum buffer");
     }
-    partial_cap = need;
+    partial_cap = cap;
     return OMEN_OK;
   }
 
@@ -555,7 +568,7 @@ struct KrylovOps {
     const size_t shm = (size_t)nb * CH * el;
 #define DOTS_LAUNCH2(T, Cc)                                                                         \
   do {                                                                                              \
-    cudaFuncSetAttribute(dots_partial_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+    smem_limit(dots_partial_kernel<T, Cc>, shm); \
     dots_partial_kernel<T, Cc><<<(unsigned)nchunks, kDotThreads, shm, ctx->stream>>>(A, n, na, B, n, nb, n, CH, d_partial); \
   } while (0)
     if (prec == OMEN_F64) { if (cplx) DOTS_LAUNCH2(double, true); else DOTS_LAUNCH2(double, false); }
@@ -574,8 +587,7 @@ struct KrylovOps {
       const unsigned grid1 = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
 #define COMB1(T, Cc)                                                                                  \
   do {                                                                                                \
-    if (shm1 > 48 * 1024)                                                                              \
-      cudaFuncSetAttribute(combine1_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm1); \
+    smem_limit(combine1_kernel<T, Cc>, shm1);                                                         \
     combine1_kernel<T, Cc><<<grid1, 256, shm1, ctx->stream>>>(A, n, na, M_dev, Y, n, alpha, beta);       \
   } while (0)
       if (prec == OMEN_F64) { if (cplx) COMB1(double, true); else COMB1(double, false); }
@@ -588,7 +600,7 @@ struct KrylovOps {
     const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
 #define COMB_LAUNCH2(T, Cc)                                                                          \
   do {                                                                                               \
-    cudaFuncSetAttribute(combine_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
+    smem_limit(combine_kernel<T, Cc>, shm); \
     combine_kernel<T, Cc><<<grid, 256, shm, ctx->stream>>>(A, n, na, M_dev, nb, Y, n, n, alpha, beta); \
   } while (0)
     if (prec == OMEN_F64) { if (cplx) COMB_LAUNCH2(double, true); else COMB_LAUNCH2(double, false); }
@@ -643,8 +655,7 @@ struct KrylovOps {
     dim3 grid(gx, P);
 #define COMB1B(T, Cc)                                                                                 \
   do {                                                                                                \
-    if (shm1 > 48 * 1024)                                                                              \
-      cudaFuncSetAttribute(combine1_kernel<T, Cc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm1); \
+    smem_limit(combine1_kernel<T, Cc>, shm1);                                                         \
     combine1_kernel<T, Cc><<<grid, 256, shm1, ctx->stream>>>(A, lda, na, M_dev, Y, n, alpha, beta, n, m_ps, n); \
   } while (0)
     if (prec == OMEN_F64) { if (cplx) COMB1B(double, true); else COMB1B(double, false); }
@@ -832,23 +843,30 @@ static void error_bounds(const std::vector<double>& lam_all, const std::vector<d
 // Rayleigh quotients and FP64-accumulated residual norms of the k columns of X (H X in HX).
 static omen_status rayleigh_residuals(KrylovOps& op, void* X, void* HX, void* R, int k, std::vector<double>& lam,
                                       std::vector<double>& res) {
+  // all k columns at once: diag(X^H X), diag(X^H HX), then R = HX - X diag(lam), diag(R^H R)
   lam.assign(k, 0.0);
   res.assign(k, 0.0);
-  for (int j = 0; j < k; ++j) {
-    std::vector<cd> xx, xhx;
-    omen_status s = op.dots(op.col(X, j), 1, op.col(X, j), 1, xx);
+  std::vector<double> xx(k), rr(k);
+  for (int j0 = 0; j0 < k; j0 += kMaxBlockCols) {
+    const int nb = std::min(kMaxBlockCols, k - j0);
+    std::vector<cd> g, gh;
+    omen_status s = op.dots(op.col(X, j0), nb, op.col(X, j0), nb, g);
     if (s != OMEN_OK) return s;
-    s = op.dots(op.col(X, j), 1, op.col(HX, j), 1, xhx);
+    s = op.dots(op.col(X, j0), nb, op.col(HX, j0), nb, gh);
     if (s != OMEN_OK) return s;
-    lam[j] = std::real(xhx[0]) / std::real(xx[0]);
-    OMEN_CUDA(op.ctx, cudaMemcpyAsync(op.col(R, j), op.col(HX, j), op.n * op.el, cudaMemcpyDeviceToDevice, op.ctx->stream));
-    std::vector<cd> m(1, cd(lam[j]));
-    s = op.combine(op.col(X, j), 1, m, 1, op.col(R, j), -1.0, 1.0);
+    for (int j = 0; j < nb; ++j) {
+      xx[j0 + j] = std::real(g[j + (size_t)j * nb]);
+      lam[j0 + j] = std::real(gh[j + (size_t)j * nb]) / xx[j0 + j];
+    }
+    OMEN_CUDA(op.ctx, cudaMemcpyAsync(op.col(R, j0), op.col(HX, j0), (size_t)nb * op.n * op.el, cudaMemcpyDeviceToDevice,
+                                      op.ctx->stream));
+    std::vector<cd> D((size_t)nb * nb, cd(0));
+    for (int j = 0; j < nb; ++j) D[j + (size_t)j * nb] = cd(lam[j0 + j]);
+    s = op.combine(op.col(X, j0), nb, D, nb, op.col(R, j0), -1.0, 1.0);
     if (s != OMEN_OK) return s;
-    std::vector<cd> rr;
-    s = op.dots(op.col(R, j), 1, op.col(R, j), 1, rr);
+    s = op.dots(op.col(R, j0), nb, op.col(R, j0), nb, g);
     if (s != OMEN_OK) return s;
-    res[j] = std::sqrt(std::max(0.0, std::real(rr[0])) / std::real(xx[0]));
+    for (int j = 0; j < nb; ++j) res[j0 + j] = std::sqrt(std::max(0.0, std::real(g[j + (size_t)j * nb])) / xx[j0 + j]);
   }
   return OMEN_OK;
 }
@@ -867,7 +885,7 @@ static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X,
   const int m = o->basis;
   const bool folded = (o->which == OMEN_NEAREST);
   const long long n = op.n;
-  DevBuf Vb, Wb, Tb, Xb;
+  DevBuf Vb, Wb, Tb, Xb, HXb, Rb;
   const size_t vbytes = (size_t)n * op.el;
   if (cudaMalloc(&Vb.p, (size_t)(m + b) * vbytes) != cudaSuccess || cudaMalloc(&Wb.p, (size_t)b * vbytes) != cudaSuccess ||
       cudaMalloc(&Tb.p, (size_t)std::max(b, k_out) * vbytes) != cudaSuccess ||
@@ -952,7 +970,7 @@ static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X,
     Rlast = R;
     ++iter;
     const bool full = nbas + b > m;
-    const bool check = full || iter >= max_iter || (iter % std::max(1, 8 / b) == 0 && nbas >= o->nev + b);
+    const bool check = full || iter >= max_iter || (iter % std::max(4, (m / b) / 2) == 0 && nbas >= o->nev + b);
     if (check && nbas >= o->nev) {
       // Rayleigh–Ritz on T[0:nbas, 0:nbas]
       std::vector<cd> Tn((size_t)nbas * nbas);
@@ -989,8 +1007,8 @@ static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X,
             for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
           s = op.combine(V, nbas, Yk, kc, Xb.p, 1.0, 0.0);
           if (s != OMEN_OK) return s;
-          DevBuf HXb, Rb;
-          if (cudaMalloc(&HXb.p, (size_t)kc * vbytes) != cudaSuccess || cudaMalloc(&Rb.p, (size_t)kc * vbytes) != cudaSuccess) {
+          if (!HXb.p && (cudaMalloc(&HXb.p, (size_t)(o->nev + b) * vbytes) != cudaSuccess ||
+                         cudaMalloc(&Rb.p, (size_t)(o->nev + b) * vbytes) != cudaSuccess)) {
             cudaGetLastError();
             return set_err(ctx, OMEN_ENOMEM, "Ritz check vectors");
           }
@@ -1067,7 +1085,7 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   const bool folded = (o->which == OMEN_NEAREST);
   const size_t vbytes = (size_t)op.n * op.el;
   const int ldT = m + 1;
-  DevBuf Vb, Wb, Tb, Xb, Td, Hd;
+  DevBuf Vb, Wb, Tb, Xb, Td, Hd, HXb, Rb;
   if (cudaMalloc(&Vb.p, (size_t)(m + 1) * vbytes) != cudaSuccess || cudaMalloc(&Wb.p, vbytes) != cudaSuccess ||
       cudaMalloc(&Tb.p, std::max<size_t>(1, k_out) * vbytes) != cudaSuccess ||
       cudaMalloc(&Xb.p, (size_t)m * vbytes) != cudaSuccess ||
@@ -1165,8 +1183,8 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
             for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
           s = op.combine(V, nbas, Yk, kc, Xb.p, 1.0, 0.0);
           if (s != OMEN_OK) return s;
-          DevBuf HXb, Rb;
-          if (cudaMalloc(&HXb.p, (size_t)kc * vbytes) != cudaSuccess || cudaMalloc(&Rb.p, (size_t)kc * vbytes) != cudaSuccess) {
+          if (!HXb.p && (cudaMalloc(&HXb.p, (size_t)(o->nev + 1) * vbytes) != cudaSuccess ||
+                         cudaMalloc(&Rb.p, (size_t)(o->nev + 1) * vbytes) != cudaSuccess)) {
             cudaGetLastError();
             return set_err(ctx, OMEN_ENOMEM, "Ritz check vectors");
           }
@@ -1624,10 +1642,10 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
           char* Yout = static_cast<char*>(Xb.p) + (size_t)j0 * blk + (size_t)p * vb;
           const char* Ain = V + (size_t)p * vb;
           if (prec == OMEN_F64) {
-            cudaFuncSetAttribute(combine_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            smem_limit(combine_kernel<double, true>, shm);
             combine_kernel<double, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
           } else {
-            cudaFuncSetAttribute(combine_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            smem_limit(combine_kernel<float, true>, shm);
             combine_kernel<float, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
           }
           OMEN_CHECK_LAUNCH(ctx);
@@ -1667,10 +1685,10 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
       char* Yout = static_cast<char*>(Xb.p) + (size_t)j0 * blk + (size_t)p * vb;
       const char* Ain = V + (size_t)p * vb;
       if (prec == OMEN_F64) {
-        cudaFuncSetAttribute(combine_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        smem_limit(combine_kernel<double, true>, shm);
         combine_kernel<double, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
       } else {
-        cudaFuncSetAttribute(combine_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        smem_limit(combine_kernel<float, true>, shm);
         combine_kernel<float, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
       }
       OMEN_CHECK_LAUNCH(ctx);

@@ -99,7 +99,7 @@ def run_scf(omen, ctx, lat, p, grid, rho_d, phi, kw):
 
 def test_learned_start_saves_scf_iterations(ctx):
     from paper_1003_4570_gb300 import omen
-    n_train, n_test = 32, 4
+    n_train, n_test = 16, 3
     spec, p, grid, _, _ = delta_problem(0)
     lat = omen.omen_build_lattice(ctx, spec)
     net = omen.omen_mlp_create(ctx, synth.mlp_init(7, SIZES))
