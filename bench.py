@@ -161,6 +161,26 @@ def measure_lanczos(ctx, omen, ham, iters=500, basis=64):
             "hx_count": info["hx_count"]}
 
 
+def measure_eigs_1m(ctx, omen, lat, p, nev=16):
+    """Seconds to nev converged eigenpairs at 1M atoms (lowest end of the spectrum, where the
+    thick-restart Lanczos converges): FP64, and spin-orbit complex64 + FP64 refinement."""
+    import torch
+    out = {}
+    for name, so, prec, tol in (("f64", False, omen.OMEN_F64, 1e-9), ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)):
+        ham = omen.omen_assemble_H(ctx, lat, p, spin_orbit=so, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, info, st = omen.omen_eigs(ctx, ham, nev, omen.OMEN_LOWEST, tol=tol, block=1 if not so else 2,
+                                      basis=96, max_iter=4000, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "converged": info["converged"], "tol_eV": tol,
+                     "iterations": info["iterations"], "hx_count": info["hx_count"],
+                     "max_error_bound": info["max_error_bound"], "max_residual_raw": info["max_residual_raw"],
+                     "max_residual": info["max_residual"], "lowest": float(ev[0])}
+        del ham
+    return out
+
+
 def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
     """Bands/s of the lockstep k-batched solve against one solve per k (same solver, nk = 1)."""
     import torch
@@ -350,8 +370,11 @@ def run_gpu(args, rank, world, local_rank):
     if prec == omen.OMEN_F64:
         fl = flops_per_hx(nbonds, natoms)
         achieved_tf = fl / (launch_ms / 1e3) / 1e12
+        # DRAM bytes per launch of this kernel at this workload, from the ncu launch list in
+        # profiles/hx_kernel_sige_alloy.md (null for other workloads)
+        traffic = 2.552e9 if (args.cells == N_CELLS and not args.matrix_free) else None
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "hx_kernel<double,10,real,stored>", "hbm_achieved_gbs": achieved_gbs,
                 "hbm_frac_of_measured": achieved_gbs / hbm, "peak_source": "recipe nominal FP64"}
     else:
@@ -372,6 +395,9 @@ def run_gpu(args, rank, world, local_rank):
               "clocks": clk.summary()}
     if not args.no_extras:
         result["lanczos_500_iterations"] = measure_lanczos(ctx, omen, ham)
+        if args.cells == N_CELLS and prec == omen.OMEN_F64 and not args.matrix_free:
+            del ham
+            result["eigs_16_lowest_1M_atoms"] = measure_eigs_1m(ctx, omen, lat, p)
         result["kbatch"] = measure_kbatch(ctx, omen)
         result["scf_learned_vs_zero"] = measure_scf(ctx, omen)
     if rank == 0 and not args.no_cpu:
@@ -399,12 +425,23 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the Lanczos and k-batch side measurements")
     ap.add_argument("--cells", type=int, default=N_CELLS, help="cells per edge (50 = the 1M-atom workload; "
                     "smaller only for profiling captures)")
+    ap.add_argument("--lanczos-only", type=int, default=0, metavar="ITERS",
+                    help="profiling aid: run only ITERS Lanczos iterations (FP64, basis 64) and print their time")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.lanczos_only:
+        import torch
+        from paper_1003_4570_gb300 import omen
+        ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+        spec, p = synth.config_sige_alloy(args.cells, seed=2)
+        lat = omen.omen_build_lattice(ctx, spec)
+        ham = omen.omen_assemble_H(ctx, lat, p)
+        print(json.dumps({"lanczos": measure_lanczos(ctx, omen, ham, iters=args.lanczos_only), "cells": args.cells}))
         return
     run_gpu(args, rank, world, local_rank)
 
