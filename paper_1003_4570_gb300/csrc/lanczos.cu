@@ -190,21 +190,31 @@ __global__ void __launch_bounds__(256) dots1_kernel(const void* Av, long long ld
 }
 
 // y = beta*y + alpha * sum_i A_i m_i for one output vector, 8 basis loads in flight per row.
+// FP64 vectors accumulate in FP64; FP32 vectors in FP32 (coefficients rounded once from their
+// FP64 values; the result is stored in FP32), which keeps them off GB300's slow FP64 pipe.
 template <typename T, bool C>
 __global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M,
                                                        void* Yv, long long n, double alpha, double beta,
                                                        long long a_ps = 0, long long m_ps = 0, long long y_ps = 0) {
   using E = Elem<T, C>;
   using V = typename E::V;
+  using A2 = std::conditional_t<sizeof(T) == 8, double2, float2>;
+  using R = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* Ms = reinterpret_cast<double2*>(smem_raw);
+  A2* Ms = reinterpret_cast<A2*>(smem_raw);
   M += blockIdx.y * m_ps;
-  for (int t = threadIdx.x; t < na; t += blockDim.x) Ms[t] = M[t];
+  for (int t = threadIdx.x; t < na; t += blockDim.x) {
+    A2 m;
+    m.x = (R)(alpha * M[t].x);
+    m.y = (R)(alpha * M[t].y);
+    Ms[t] = m;
+  }
   __syncthreads();
   const V* A = static_cast<const V*>(Av) + blockIdx.y * a_ps;
   V* Y = static_cast<V*>(Yv) + blockIdx.y * y_ps;
+  const R rbeta = (R)beta;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-    double yr = 0.0, yi = 0.0;
+    R yr = 0, yi = 0;
     int i = 0;
     for (; i + 8 <= na; i += 8) {
       V av[8];
@@ -212,33 +222,42 @@ __global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long
       for (int k = 0; k < 8; ++k) av[k] = A[(size_t)(i + k) * lda + r];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const double2 m = Ms[i + k];
-        const double xr = E::re(av[k]), xi = E::im(av[k]);
-        yr = fma(xr, m.x, yr);
+        const A2 m = Ms[i + k];
         if constexpr (C) {
-          yr = fma(-xi, m.y, yr);
-          yi = fma(xr, m.y, yi);
-          yi = fma(xi, m.x, yi);
+          yr = fma(av[k].x, m.x, yr);
+          yr = fma(-av[k].y, m.y, yr);
+          yi = fma(av[k].x, m.y, yi);
+          yi = fma(av[k].y, m.x, yi);
+        } else {
+          yr = fma(av[k], m.x, yr);
         }
       }
     }
     for (; i < na; ++i) {
       const V a = A[(size_t)i * lda + r];
-      const double2 m = Ms[i];
-      const double xr = E::re(a), xi = E::im(a);
-      yr = fma(xr, m.x, yr);
+      const A2 m = Ms[i];
       if constexpr (C) {
-        yr = fma(-xi, m.y, yr);
-        yi = fma(xr, m.y, yi);
-        yi = fma(xi, m.x, yi);
+        yr = fma(a.x, m.x, yr);
+        yr = fma(-a.y, m.y, yr);
+        yi = fma(a.x, m.y, yi);
+        yi = fma(a.y, m.x, yi);
+      } else {
+        yr = fma(a, m.x, yr);
       }
     }
-    double orr = alpha * yr, oi = alpha * yi;
-    if (beta != 0.0) {
-      orr += beta * E::re(Y[r]);
-      oi += beta * E::im(Y[r]);
+    V out;
+    if constexpr (C) {
+      out.x = yr;
+      out.y = yi;
+      if (beta != 0.0) {
+        out.x = fma(rbeta, Y[r].x, out.x);
+        out.y = fma(rbeta, Y[r].y, out.y);
+      }
+    } else {
+      out = yr;
+      if (beta != 0.0) out = fma(rbeta, Y[r], out);
     }
-    Y[r] = E::make(orr, oi);
+    Y[r] = out;
   }
 }
 
@@ -452,10 +471,10 @@ struct KrylovOps {
   // out (host, na x nb column-major complex) = A^H B   (A: na columns, B: nb columns)
   omen_status dots(const void* A, int na, const void* B, int nb, std::vector<cd>& out) {
     out.assign((size_t)na * nb, cd(0));
-    if (nb == 1 && (size_t)na <= small_cap) {
-      omen_status s1 = dots_dev(A, na, B, 1, d_small, nullptr, 0, 0);
+    if (nb <= 4 && (size_t)na * nb <= small_cap) {
+      omen_status s1 = dots_dev(A, na, B, nb, d_small, nullptr, 0, 0);
       if (s1 != OMEN_OK) return s1;
-      OMEN_CUDA(ctx, cudaMemcpyAsync(out.data(), d_small, na * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
+      OMEN_CUDA(ctx, cudaMemcpyAsync(out.data(), d_small, (size_t)na * nb * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
       OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
       for (const cd& v : out)
         if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
@@ -499,6 +518,11 @@ struct KrylovOps {
 
   // Y = beta*Y + alpha * A M   (M host na x nb column-major)
   omen_status combine(const void* A, int na, const std::vector<cd>& M, int nb, void* Y, double alpha, double beta) {
+    if (nb <= 4 && (size_t)na * nb <= small_cap) {
+      // pageable source: the copy has consumed M when the call returns; stream order protects d_small
+      OMEN_CUDA(ctx, cudaMemcpyAsync(d_small, M.data(), (size_t)na * nb * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+      return combine_dev(A, na, d_small, nb, Y, alpha, beta);
+    }
     if ((size_t)na * kMaxBlockCols > small_cap) return set_err(ctx, OMEN_EINVAL, "combination too large");
     for (int j0 = 0; j0 < nb; j0 += kMaxBlockCols) {
       const int nbj = std::min(kMaxBlockCols, nb - j0);
@@ -543,6 +567,14 @@ struct KrylovOps {
   // nothing is copied to the host and the stream is not synchronised.
   omen_status dots_dev(const void* A, int na, const void* B, int nb, double2* out_dev, double2* accT, int ldT, int col0) {
     if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "dots_dev: too many columns");
+    if (nb > 1 && nb <= 4) {
+      // a few right-hand columns: the single-column kernel per column (fast path for small blocks)
+      for (int j = 0; j < nb; ++j) {
+        omen_status sj = dots_dev(A, na, col(const_cast<void*>(B), j), 1, out_dev + (size_t)j * na, accT, ldT, col0 + j);
+        if (sj != OMEN_OK) return sj;
+      }
+      return OMEN_OK;
+    }
     if (nb == 1) {
       int rows = 8192;
       while ((n + rows - 1) / rows > 65535) rows *= 2;
@@ -582,6 +614,13 @@ struct KrylovOps {
   // Y = beta*Y + alpha * A M with M (na x nb, column-major) already on the device
   omen_status combine_dev(const void* A, int na, const double2* M_dev, int nb, void* Y, double alpha, double beta) {
     if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "combine_dev: too many columns");
+    if (nb > 1 && nb <= 4) {
+      for (int j = 0; j < nb; ++j) {
+        omen_status sj = combine_dev(A, na, M_dev + (size_t)j * na, 1, col(Y, j), alpha, beta);
+        if (sj != OMEN_OK) return sj;
+      }
+      return OMEN_OK;
+    }
     if (nb == 1) {
       const size_t shm1 = (size_t)na * sizeof(double2);
       const unsigned grid1 = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
