@@ -149,6 +149,34 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def measure_variants(ctx, omen, lat, p, natoms, nbonds, reps=50):
+    """One H·X per variant (same workload): ms and algorithmic GB/s."""
+    import torch
+    out = {}
+    for name, prec, mf, so in (("f64", omen.OMEN_F64, False, False), ("f64_df", omen.OMEN_F64_DF, False, False),
+                               ("f32", omen.OMEN_F32, False, False), ("f32_matrix_free", omen.OMEN_F32, True, False),
+                               ("c64_spin_orbit", omen.OMEN_F32, False, True)):
+        ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, matrix_free=mf, spin_orbit=so)
+        el = 4 if prec == omen.OMEN_F32 else 8
+        vel = el * (2 if so else 1)
+        x = torch.zeros(ham.nrows * vel // 4, dtype=torch.float32, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            omen.omen_hx(ctx, ham, x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            omen.omen_hx(ctx, ham, x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        alg = alg_bytes_per_hx(nbonds, natoms, ham.nrows, el, vel, mf)
+        out[name] = {"ms": ms, "alg_GB": alg / 1e9, "GB_per_s": alg / ms / 1e6}
+        del ham, x, y
+    return out
+
+
 def measure_lanczos(ctx, omen, ham, iters=500, basis=64):
     """The paper's benchmark unit (Section II-B): wall time of 500 Lanczos iterations."""
     import torch
@@ -303,14 +331,21 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
     ctx = omen.omen_create(local_rank, stream.cuda_stream)
-    prec = {"f64": omen.OMEN_F64, "f32": omen.OMEN_F32}[args.precision]
+    prec = {"f64": omen.OMEN_F64, "f32": omen.OMEN_F32, "df": omen.OMEN_F64_DF}[args.precision]
     spec, p = synth.config_sige_alloy(args.cells, seed=2)
     lat = omen.omen_build_lattice(ctx, spec)
     natoms, nbonds = lat.counts()
     ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, matrix_free=args.matrix_free)
-    dt = torch.float64 if prec == omen.OMEN_F64 else torch.float32
-    el = 8 if prec == omen.OMEN_F64 else 4
-    x = (torch.rand(ham.nrows, dtype=torch.float64, device="cuda") * 2 - 1).to(dt)
+    el = 4 if prec == omen.OMEN_F32 else 8
+    if prec == omen.OMEN_F64_DF:   # double-float vectors: (hi, lo) FP32 pairs
+        x64 = torch.rand(ham.nrows, dtype=torch.float64, device="cuda") * 2 - 1
+        x = torch.empty((ham.nrows, 2), dtype=torch.float32, device="cuda")
+        ctx.check(omen.lib().omen_convert_vectors(ctx.handle, x64.data_ptr(), omen.OMEN_F64, x.data_ptr(),
+                                                  omen.OMEN_F64_DF, ham.nrows))
+        del x64
+    else:
+        dt = torch.float64 if prec == omen.OMEN_F64 else torch.float32
+        x = (torch.rand(ham.nrows, dtype=torch.float64, device="cuda") * 2 - 1).to(dt)
     t = torch.empty_like(x)
     y = torch.empty_like(x)
     sigma = 0.3
@@ -345,7 +380,7 @@ def run_gpu(args, rank, world, local_rank):
     launch_ms = ms / (2 * args.steps)
 
     # end to end through the host-buffer entry point (pinned host x, y; copies timed)
-    xh = x.cpu().pin_memory()
+    xh = (x if prec != omen.OMEN_F64_DF else x[:, 0].double()).cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     import ctypes
     L = omen.lib()
@@ -378,12 +413,14 @@ def run_gpu(args, rank, world, local_rank):
                 "kernel": "hx_kernel<double,10,real,stored>", "hbm_achieved_gbs": achieved_gbs,
                 "hbm_frac_of_measured": achieved_gbs / hbm, "peak_source": "recipe nominal FP64"}
     else:
+        kname = "hx_df_kernel<10>" if prec == omen.OMEN_F64_DF else "hx_kernel<float,10,real,stored>"
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": achieved_gbs / hbm, "traffic": None,
-                "kernel": "hx_kernel<float,10,real,stored>", "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+                "kernel": kname, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+              "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "df": "f32x2 (double-float)"}[args.precision],
+              "data": "synthetic",
               "config": {"workload": f"Si0.7Ge0.3 alloy {args.cells}^3 cells ({natoms:,} atoms), hard wall, 2% bond "
                                      "strain, sp3d5s*; step = folded operator (H-sigma)^2 x (two H·X)",
                          "atoms": natoms, "bonds": nbonds, "rows": ham.nrows,
@@ -394,6 +431,7 @@ def run_gpu(args, rank, world, local_rank):
                       "d2h_bytes_per_step": ham.nrows * el},
               "clocks": clk.summary()}
     if not args.no_extras:
+        result["hx_variants"] = measure_variants(ctx, omen, lat, p, natoms, nbonds)
         result["lanczos_500_iterations"] = measure_lanczos(ctx, omen, ham)
         if args.cells == N_CELLS and prec == omen.OMEN_F64 and not args.matrix_free:
             del ham
@@ -419,7 +457,8 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "df"],
+                    help="f64 native FP64; f32; df double-float (FP64-accurate on the FP32 pipe)")
     ap.add_argument("--matrix-free", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the Lanczos and k-batch side measurements")

@@ -56,7 +56,13 @@ enum {
   OMEN_F32 = 1,          /* FP32 bond blocks and Krylov vectors (complex64 when complex);
                             Lanczos dots, orthogonalisation coefficients and the projected
                             eigenproblem in FP64 */
-  OMEN_F32_REFINE64 = 2  /* OMEN_F32 solve, then an FP64 Rayleigh–Ritz refinement */
+  OMEN_F32_REFINE64 = 2, /* OMEN_F32 solve, then an FP64 Rayleigh–Ritz refinement */
+  OMEN_F64_DF = 3        /* FP64-accurate H·X on the FP32 pipe: blocks and vectors stored as
+                            double-float pairs (hi, lo) of FP32 (value = hi + lo, about 48
+                            significant bits), products and sums with error-free
+                            transformations (Dekker 1971; Knuth TwoSum).  Real Hamiltonians
+                            only; omen_hx / omen_hx_kbatch vectors are float2 (hi, lo) per
+                            element (see omen_convert_vectors); omen_hx_host takes FP64. */
 };
 enum { OMEN_LOWEST = 0, OMEN_NEAREST = 1, OMEN_HIGHEST = 2 };  /* which eigenvalues */
 
@@ -134,6 +140,11 @@ omen_status omen_ham_set_potential(omen_ctx* ctx, omen_ham* ham, const double* U
  * x and y must not overlap.  This is the operation the Lanczos recurrence repeats. */
 omen_status omen_hx(omen_ctx* ctx, const omen_ham* ham, const void* x_dev, void* y_dev,
                     int nvec, double sigma);
+/* Convert n vector elements between OMEN_F64 (double) and OMEN_F64_DF (float2 hi, lo) on the
+ * device (either direction; src and dst must not overlap). */
+omen_status omen_convert_vectors(omen_ctx* ctx, const void* src_dev, int src_precision, void* dst_dev,
+                                 int dst_precision, long long n);
+
 /* The same product with host buffers (copies in and out on the ctx stream; synchronous). */
 omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* ham, const void* x_host, void* y_host,
                          int nvec, double sigma);

@@ -35,7 +35,7 @@ __global__ void b0_table_kernel(const double* __restrict__ V, int ns, int norb, 
 __global__ void assemble_bonds_kernel(Geo g, NeighbourTables nt, const uint8_t* __restrict__ species,
                                       const double* __restrict__ strain, const double* __restrict__ b0,
                                       int ns, int norb, double eta, int slot_stride, double* __restrict__ blk64,
-                                      float* __restrict__ blk32) {
+                                      float* __restrict__ blk32, float2* __restrict__ blkdf) {
   const int npad = 16 * slot_stride;
   const int pidx = blockIdx.x * blockDim.x + threadIdx.x;   // padded slot index
   if (pidx >= npad) return;
@@ -47,6 +47,7 @@ __global__ void assemble_bonds_kernel(Geo g, NeighbourTables nt, const uint8_t* 
     for (int e = 0; e < ne; ++e) {
       if (blk64) blk64[base + (size_t)e * 32] = 0.0;
       if (blk32) blk32[base + (size_t)e * 32] = 0.0f;
+      if (blkdf) blkdf[base + (size_t)e * 32] = make_float2(0.f, 0.f);
     }
     return;
   }
@@ -60,6 +61,7 @@ __global__ void assemble_bonds_kernel(Geo g, NeighbourTables nt, const uint8_t* 
     for (int e = 0; e < ne; ++e) {
       if (blk64) blk64[base + (size_t)e * 32] = 0.0;
       if (blk32) blk32[base + (size_t)e * 32] = 0.0f;
+      if (blkdf) blkdf[base + (size_t)e * 32] = make_float2(0.f, 0.f);
     }
     return;
   }
@@ -71,6 +73,10 @@ __global__ void assemble_bonds_kernel(Geo g, NeighbourTables nt, const uint8_t* 
     const double v = f * tb[e];
     if (blk64) blk64[base + (size_t)e * 32] = v;
     if (blk32) blk32[base + (size_t)e * 32] = (float)v;
+    if (blkdf) {
+      const float hi = __double2float_rn(v);
+      blkdf[base + (size_t)e * 32] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
   }
 }
 
@@ -84,9 +90,11 @@ __global__ void max_species_kernel(const uint8_t* __restrict__ sp, int n, int* _
 static void free_ham_buffers(omen_ham* h) {
   cudaFree(h->d_blk64);
   cudaFree(h->d_blk32);
+  cudaFree(h->d_blkdf);
   cudaFree(h->d_b0_64);
   cudaFree(h->d_b0_32);
   cudaFree(h->d_onsite);
+  cudaFree(h->d_onsite_df);
   cudaFree(h->d_U);
   cudaFree(h->d_lambda);
 }
@@ -112,8 +120,10 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
   *out = nullptr;
   if (p->basis != OMEN_SP3S && p->basis != OMEN_SP3D5S) return set_err(ctx, OMEN_EINVAL, "basis must be 5 or 10");
   if (p->nspecies < 1 || p->nspecies > 4) return set_err(ctx, OMEN_EINVAL, "nspecies must be 1..4");
-  if (opts->precision < OMEN_F64 || opts->precision > OMEN_F32_REFINE64)
+  if (opts->precision < OMEN_F64 || opts->precision > OMEN_F64_DF)
     return set_err(ctx, OMEN_EINVAL, "unknown precision %d", opts->precision);
+  if (opts->precision == OMEN_F64_DF && (opts->spin_orbit || opts->matrix_free || (opts->k && (lat->periodic[0] == OMEN_BLOCH || lat->periodic[1] == OMEN_BLOCH || lat->periodic[2] == OMEN_BLOCH))))
+    return set_err(ctx, OMEN_EUNSUPPORTED, "double-float precision supports real stored Hamiltonians only");
   OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
   {  // species indices must be < nspecies
     int* d_m = (int*)ctx->d_status;
@@ -162,8 +172,10 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
   ALLOC_OR_FAIL(h->d_lambda, sizeof(double) * 4);
   const bool need64 = !h->matrix_free && (h->precision == OMEN_F64 || h->precision == OMEN_F32_REFINE64);
   const bool need32 = !h->matrix_free && (h->precision == OMEN_F32 || h->precision == OMEN_F32_REFINE64);
+  const bool needdf = h->precision == OMEN_F64_DF;
   if (need64) ALLOC_OR_FAIL(h->d_blk64, sizeof(double) * ne * nslots);
   if (need32) ALLOC_OR_FAIL(h->d_blk32, sizeof(float) * ne * nslots);
+  if (needdf) ALLOC_OR_FAIL(h->d_blkdf, sizeof(float2) * ne * nslots);
 
   // parameter tables
   std::vector<double> V(ns * ns * 14), on(ns * norb);
@@ -188,6 +200,20 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
     e = cudaMemcpyAsync(h->d_onsite, on.data(), sizeof(double) * on.size(), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_lambda, p->lambda_so, sizeof(double) * 4, cudaMemcpyHostToDevice, ctx->stream);
+  std::vector<float2> ondf(on.size());
+  if (e == cudaSuccess && needdf) {
+    for (size_t i = 0; i < on.size(); ++i) {
+      const float hi = (float)on[i];
+      ondf[i] = make_float2(hi, (float)(on[i] - (double)hi));
+    }
+    if (cudaMalloc(&h->d_onsite_df, sizeof(float2) * ondf.size()) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(d_V);
+      omen_free_ham(h);
+      return set_err(ctx, OMEN_ENOMEM, "device allocation failed");
+    }
+    e = cudaMemcpyAsync(h->d_onsite_df, ondf.data(), sizeof(float2) * ondf.size(), cudaMemcpyHostToDevice, ctx->stream);
+  }
   if (e == cudaSuccess) {
     if (opts->U_atom_dev)
       e = cudaMemcpyAsync(h->d_U, opts->U_atom_dev, sizeof(double) * lat->natoms, cudaMemcpyDeviceToDevice, ctx->stream);
@@ -198,11 +224,11 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
     b0_table_kernel<<<(unsigned)((ntab + 255) / 256), 256, 0, ctx->stream>>>(d_V, ns, norb, h->d_b0_64, h->d_b0_32);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && (need64 || need32)) {
+  if (e == cudaSuccess && (need64 || need32 || needdf)) {
     Geo g{lat->nx, lat->ny, lat->nz, lat->ncells, lat->natoms, {lat->periodic[0], lat->periodic[1], lat->periodic[2]}};
     assemble_bonds_kernel<<<(unsigned)((nslots + 255) / 256), 256, 0, ctx->stream>>>(
         g, host_neighbour_tables(), lat->d_species, lat->d_strain, h->d_b0_64, ns, norb, p->eta,
-        h->slot_stride, h->d_blk64, h->d_blk32);
+        h->slot_stride, h->d_blk64, h->d_blk32, h->d_blkdf);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

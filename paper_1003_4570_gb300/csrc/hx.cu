@@ -13,6 +13,7 @@
 // Bloch phase: a neighbour reached across the high (low) face of a Bloch-periodic direction d
 // is its periodic image shifted by +L_d (-L_d); its amplitude is multiplied by
 // exp(+i k_d L_d) (resp. the conjugate).
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -232,6 +233,161 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Double-float product (precision OMEN_F64_DF): every value is an FP32 pair (hi, lo) with
+// value = hi + lo.  A product a*b is formed exactly in its leading part (p = fl(a.hi b.hi),
+// e = fma(a.hi, b.hi, -p)) plus the cross terms; it is added to a running (S, C) pair with
+// Knuth's TwoSum, the error going into C.  The intrinsics (_rn) keep the compiler from fusing
+// the additions into FMAs, which would break the error-free transformations.  All arithmetic is
+// on the FP32 pipe (57x GB300's FP64 rate); the bytes moved equal those of FP64.
+__device__ __forceinline__ void df_mac(float& S, float& C, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float s = __fadd_rn(S, p);
+  const float bb = __fsub_rn(s, S);
+  const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  C = __fadd_rn(C, __fadd_rn(t, e));
+  S = s;
+}
+__device__ __forceinline__ float2 df_norm(float S, float C) {
+  const float h = __fadd_rn(S, C);
+  return make_float2(h, __fsub_rn(C, __fsub_rn(h, S)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  return df_norm(s, __fadd_rn(t, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 df_from_double(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+struct HxDfArgs {
+  Geo g;
+  NeighbourTables nt;
+  const float2* __restrict__ blk;
+  const uint8_t* __restrict__ species;
+  const float2* __restrict__ onsite;   // [ns][norb] double-float
+  const double* __restrict__ U;
+  const float2* x;
+  float2* y;
+  long long nrows;
+  double sigma;
+  int slot_stride;
+};
+
+template <int NORB>
+__global__ void __launch_bounds__(128) hx_df_kernel(HxDfArgs a) {
+  const Geo& g = a.g;
+  const int b = blockIdx.x & 7;
+  const int cell = (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
+  if (cell >= g.ncells) return;
+  const int N = g.natoms;
+  const int atom = b * g.ncells + cell;
+  const int ix = cell % g.nx, iy = (cell / g.nx) % g.ny, iz = cell / (g.nx * g.ny);
+  const float2* __restrict__ x = a.x + (size_t)blockIdx.z * a.nrows;
+  float2* __restrict__ y = a.y + (size_t)blockIdx.z * a.nrows;
+  const int sp = a.species[atom];
+  float S[NORB], C[NORB];
+  {
+    const float2 u = df_from_double(a.U[atom] - a.sigma);
+#pragma unroll
+    for (int o = 0; o < NORB; ++o) {
+      S[o] = 0.f;
+      C[o] = 0.f;
+      df_mac(S[o], C[o], df_add(a.onsite[sp * NORB + o], u), x[(size_t)o * N + atom]);
+    }
+  }
+  const bool is_a = b < 4;
+  const int s = is_a ? b : b - 4;
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) {
+    int ox, oy, oz, site2;
+    if (is_a) {
+      ox = a.nt.a_to_b_off[s][k][0]; oy = a.nt.a_to_b_off[s][k][1]; oz = a.nt.a_to_b_off[s][k][2];
+      site2 = a.nt.a_to_b_site[s][k];
+    } else {
+      ox = a.nt.b_to_a_off[s][k][0]; oy = a.nt.b_to_a_off[s][k][1]; oz = a.nt.b_to_a_off[s][k][2];
+      site2 = a.nt.b_to_a_site[s][k];
+    }
+    int cell2, wrap[3];
+    if (!shift_cell(g, ix, iy, iz, ox, oy, oz, cell2, wrap)) continue;
+    const int atom2 = site2 * g.ncells + cell2;
+    float2 xn[NORB];
+#pragma unroll
+    for (int o = 0; o < NORB; ++o) xn[o] = x[(size_t)o * N + atom2];
+    const size_t ks = is_a ? (size_t)(k * 4 + s) : (size_t)(k * 4 + site2);
+    const size_t pidx = ks * a.slot_stride + (is_a ? cell : cell2);
+    const float2* __restrict__ hb = a.blk + ((pidx >> 5) * (NORB * NORB)) * 32 + (pidx & 31);
+    constexpr int RB = (NORB == 10) ? 5 : NORB;
+#pragma unroll
+    for (int r0 = 0; r0 < NORB; r0 += RB) {
+      float2 hr[RB * NORB];
+#pragma unroll
+      for (int e = 0; e < RB * NORB; ++e) hr[e] = __ldg(hb + (size_t)(r0 * NORB + e) * 32);
+      if (is_a) {
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+          for (int o2 = 0; o2 < NORB; ++o2) df_mac(S[r0 + i], C[r0 + i], hr[i * NORB + o2], xn[o2]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+          for (int o2 = 0; o2 < NORB; ++o2) df_mac(S[o2], C[o2], hr[i * NORB + o2], xn[r0 + i]);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < NORB; ++o) y[(size_t)o * N + atom] = df_norm(S[o], C[o]);
+}
+
+__global__ void f64_to_df_kernel(const double* __restrict__ src, float2* __restrict__ dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = df_from_double(src[i]);
+}
+__global__ void df_to_f64_kernel(const float2* __restrict__ src, double* __restrict__ dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i].x + (double)src[i].y;
+}
+
+static cudaError_t launch_df(const omen_ham* h, const void* x, void* y, int nvec, double sigma, cudaStream_t st) {
+  const omen_lattice* L = h->lat;
+  HxDfArgs a;
+  a.g = Geo{L->nx, L->ny, L->nz, L->ncells, L->natoms, {L->periodic[0], L->periodic[1], L->periodic[2]}};
+  a.nt = host_neighbour_tables();
+  a.blk = h->d_blkdf;
+  a.species = L->d_species;
+  a.onsite = h->d_onsite_df;
+  a.U = h->d_U;
+  a.x = static_cast<const float2*>(x);
+  a.y = static_cast<float2*>(y);
+  a.nrows = h->nrows;
+  a.sigma = sigma;
+  a.slot_stride = h->slot_stride;
+  dim3 grid(((a.g.ncells + 127) / 128) * 8, 1, nvec);
+  if (h->norb == 10) hx_df_kernel<10><<<grid, 128, 0, st>>>(a);
+  else hx_df_kernel<5><<<grid, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+extern "C" omen_status omen_convert_vectors(omen_ctx* ctx, const void* src, int sp, void* dst, int dp, long long n) {
+  if (!ctx || !src || !dst || n < 0) return set_err(ctx, OMEN_EINVAL, "null argument");
+  const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 16));
+  if (sp == OMEN_F64 && dp == OMEN_F64_DF)
+    f64_to_df_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const double*>(src), static_cast<float2*>(dst), n);
+  else if (sp == OMEN_F64_DF && dp == OMEN_F64)
+    df_to_f64_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float2*>(src), static_cast<double*>(dst), n);
+  else
+    return set_err(ctx, OMEN_EINVAL, "conversion supports F64 <-> F64_DF");
+  OMEN_CHECK_LAUNCH(ctx);
+  return OMEN_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // k-batched product: y_k = (H(k) - sigma) x_k for nk Bloch wave vectors in one launch.  The real
 // bond blocks are the same for every k (the phase sits only on bonds that wrap a Bloch face),
 // so each thread loads a block entry once and applies it to KB vectors; grid.z runs over
@@ -329,7 +485,7 @@ __global__ void __launch_bounds__(128) hx_kbatch_kernel(HxArgs<T> a, const doubl
 }
 
 size_t vec_elem_bytes(const omen_ham* h, int precision) {
-  const size_t r = (precision == OMEN_F64) ? 8 : 4;
+  const size_t r = (precision == OMEN_F64 || precision == OMEN_F64_DF) ? 8 : 4;
   return h->is_complex ? 2 * r : r;
 }
 
@@ -376,7 +532,10 @@ static cudaError_t launch_prec(const omen_ham* h, const T* blk, const T* b0, con
 omen_status launch_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma, int vec_precision) {
   if (nvec < 1 || nvec > 65535) return set_err(ctx, OMEN_EINVAL, "nvec must be 1..65535");
   cudaError_t e;
-  if (vec_precision == OMEN_F64) {
+  if (vec_precision == OMEN_F64_DF) {
+    if (!h->d_blkdf) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no double-float blocks");
+    e = launch_df(h, x, y, nvec, sigma, ctx->stream);
+  } else if (vec_precision == OMEN_F64) {
     if (!h->matrix_free && !h->d_blk64) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP64 blocks");
     e = launch_prec<double>(h, h->d_blk64, h->d_b0_64, x, y, nvec, sigma, ctx->stream);
   } else {
@@ -387,7 +546,10 @@ omen_status launch_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, 
   return OMEN_OK;
 }
 
-static int native_precision(const omen_ham* h) { return h->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64; }
+static int native_precision(const omen_ham* h) {
+  if (h->precision == OMEN_F64_DF) return OMEN_F64_DF;
+  return h->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64;
+}
 
 extern "C" omen_status omen_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma) {
   if (!ctx || !h || !x || !y) return set_err(ctx, OMEN_EINVAL, "null argument");
@@ -398,6 +560,30 @@ extern "C" omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* h, const void
   if (!ctx || !h || !xh || !yh) return set_err(ctx, OMEN_EINVAL, "null argument");
   if (nvec < 1) return set_err(ctx, OMEN_EINVAL, "nvec must be >= 1");
   const size_t bytes = vec_elem_bytes(h, native_precision(h)) * (size_t)h->nrows * nvec;
+  if (h->precision == OMEN_F64_DF) {
+    // FP64 host arrays; double-float conversion on the device
+    const long long n = h->nrows * nvec;
+    void *dx = nullptr, *dy = nullptr, *fx = nullptr;
+    if (cudaMallocAsync(&dx, bytes, ctx->stream) != cudaSuccess || cudaMallocAsync(&dy, bytes, ctx->stream) != cudaSuccess ||
+        cudaMallocAsync(&fx, 8 * (size_t)n, ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, OMEN_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    }
+    omen_status st = OMEN_OK;
+    cudaError_t e = cudaMemcpyAsync(fx, xh, 8 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) st = omen_convert_vectors(ctx, fx, OMEN_F64, dx, OMEN_F64_DF, n);
+    if (e == cudaSuccess && st == OMEN_OK) st = launch_hx(ctx, h, dx, dy, nvec, sigma, OMEN_F64_DF);
+    if (e == cudaSuccess && st == OMEN_OK) st = omen_convert_vectors(ctx, dy, OMEN_F64_DF, fx, OMEN_F64, n);
+    if (e == cudaSuccess && st == OMEN_OK) e = cudaMemcpyAsync(yh, fx, 8 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    cudaFreeAsync(dx, ctx->stream);
+    cudaFreeAsync(dy, ctx->stream);
+    cudaFreeAsync(fx, ctx->stream);
+    cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+    if (st != OMEN_OK) return st;
+    if (e != cudaSuccess || e2 != cudaSuccess)
+      return set_err(ctx, OMEN_ECUDA, "host H·X failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return OMEN_OK;
+  }
   void *dx = nullptr, *dy = nullptr;
   if (cudaMallocAsync(&dx, bytes, ctx->stream) != cudaSuccess || cudaMallocAsync(&dy, bytes, ctx->stream) != cudaSuccess) {
     cudaGetLastError();

@@ -1435,6 +1435,7 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   if (o->max_iter < 1 || (long long)o->max_iter * b < o->nev)
     return set_err(ctx, OMEN_EINVAL, "max_iter * block must be >= nev");
   if ((long long)o->basis + b > ham->nrows) return set_err(ctx, OMEN_EINVAL, "basis larger than the problem");
+  if (ham->precision == OMEN_F64_DF) return set_err(ctx, OMEN_EUNSUPPORTED, "the eigensolver runs in F64, F32 or F32_REFINE64");
   OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
   auto t0 = std::chrono::steady_clock::now();
   omen_eig_info local{};

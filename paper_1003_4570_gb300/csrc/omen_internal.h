@@ -44,11 +44,13 @@ struct omen_ham {
   int slot_stride = 0;                    // ncells rounded up to a multiple of 32
   double* d_blk64 = nullptr;
   float* d_blk32 = nullptr;
+  float2* d_blkdf = nullptr;              // double-float (hi, lo) blocks, same tiled layout
   // matrix-free table: B0[((sa*ns + sb)*4 + k)*norb*norb + e]
   double* d_b0_64 = nullptr;
   float* d_b0_32 = nullptr;
   // onsite energies per species and orbital [ns][norb], potential per atom
   double* d_onsite = nullptr;
+  float2* d_onsite_df = nullptr;          // the same as double-float pairs (OMEN_F64_DF)
   double* d_U = nullptr;                  // [natoms]
   double lambda_so[4] = {0, 0, 0, 0};
   double* d_lambda = nullptr;             // [ns]

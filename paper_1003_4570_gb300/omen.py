@@ -19,7 +19,7 @@ OMEN_OK, OMEN_EINVAL, OMEN_ENOMEM, OMEN_ENOCONV, OMEN_ENUMERIC, OMEN_ETIMEOUT, O
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOCONV", "ENUMERIC", "ETIMEOUT", "ECUDA", "EUNSUPPORTED"]
 OMEN_SP3S, OMEN_SP3D5S = 5, 10
 OMEN_HARD_WALL, OMEN_PERIODIC, OMEN_BLOCH = 0, 1, 2
-OMEN_F64, OMEN_F32, OMEN_F32_REFINE64 = 0, 1, 2
+OMEN_F64, OMEN_F32, OMEN_F32_REFINE64, OMEN_F64_DF = 0, 1, 2, 3
 OMEN_LOWEST, OMEN_NEAREST, OMEN_HIGHEST = 0, 1, 2
 
 
@@ -123,6 +123,7 @@ def lib():
             "omen_ham_set_potential": (i, [vp, vp, vp]),
             "omen_hx": (i, [vp, vp, vp, vp, i, d]),
             "omen_hx_host": (i, [vp, vp, vp, vp, i, d]),
+            "omen_convert_vectors": (i, [vp, vp, i, vp, i, ll]),
             "omen_eigs": (i, [vp, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
             "omen_hx_kbatch": (i, [vp, vp, i, vp, vp, vp, d]),
             "omen_eigs_kbatch": (i, [vp, vp, i, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
@@ -248,6 +249,7 @@ class Hamiltonian:
 
     @property
     def numpy_dtype(self):
+        """dtype of host vectors (omen_hx_host); double-float Hamiltonians take FP64 on the host."""
         if self.is_complex:
             return np.complex128 if self.elem_bytes == 16 else np.complex64
         return np.float64 if self.elem_bytes == 8 else np.float32

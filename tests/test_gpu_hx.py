@@ -92,3 +92,35 @@ def test_hard_wall_bond_count_and_invalid_species(ctx):
     with pytest.raises(omen.OmenError) as e:
         omen.omen_assemble_H(ctx, lat, p)
     assert e.value.status == omen.OMEN_EINVAL
+
+
+def test_double_float_hx_matches_oracle(ctx):
+    """OMEN_F64_DF: FP64-accurate product on the FP32 pipe, same 1e-12 tolerance as FP64."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(5, 4, 7, (0, 1, 0), seed=33, alloy_fraction=0.3, strain_amp=0.02)
+    p = synth.draw_tb_params(33, 10, 2)
+    U = np.random.default_rng(4).uniform(-0.2, 0.2, spec.natoms)
+    H = hamiltonian.assemble(spec, p, U_atom=U)
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F64_DF, U_atom_dev=torch.from_numpy(U).cuda())
+    x = synth.random_vectors(6, H.shape[0], 2)
+    y = omen.omen_hx_host(ctx, ham, x, sigma=0.21)
+    for v in range(2):
+        ref = H @ x[v] - 0.21 * x[v]
+        np.testing.assert_allclose(y[v], ref, atol=1e-12 * np.abs(ref).max(), rtol=0)
+    # device buffers in double-float form
+    n = H.shape[0]
+    xd = torch.from_numpy(x[0]).cuda()
+    xdf = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+    ydf = torch.empty_like(xdf)
+    yd = torch.empty(n, dtype=torch.float64, device="cuda")
+    from paper_1003_4570_gb300.omen import lib
+    ctx.check(lib().omen_convert_vectors(ctx.handle, xd.data_ptr(), omen.OMEN_F64, xdf.data_ptr(), omen.OMEN_F64_DF, n))
+    omen.omen_hx(ctx, ham, xdf, ydf, 1, 0.0)
+    ctx.check(lib().omen_convert_vectors(ctx.handle, ydf.data_ptr(), omen.OMEN_F64_DF, yd.data_ptr(), omen.OMEN_F64, n))
+    torch.cuda.synchronize()
+    ref = H @ x[0]
+    np.testing.assert_allclose(yd.cpu().numpy(), ref, atol=1e-12 * np.abs(ref).max(), rtol=0)
+    with pytest.raises(omen.OmenError) as e:
+        omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F64_DF, spin_orbit=True)
+    assert e.value.status == omen.OMEN_EUNSUPPORTED
