@@ -1164,13 +1164,31 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   std::vector<double> theta;
   std::vector<cd> Y;
   auto t_start = std::chrono::steady_clock::now();
+  bool fresh = true;   // first step of a cycle: the new vector couples to every kept vector
   while (true) {
     s = op.apply(op.col(V, jstart), W, tmp, 1, folded, o->sigma, hx);
     if (s != OMEN_OK) return s;
-    for (int pass = 0; pass < 2; ++pass) {
-      s = op.dots_dev(V, nbas, W, 1, dh, dT, ldT, jstart);
+    if (fresh) {
+      // two full classical Gram–Schmidt passes
+      for (int pass = 0; pass < 2; ++pass) {
+        s = op.dots_dev(V, nbas, W, 1, dh, dT, ldT, jstart);
+        if (s != OMEN_OK) return s;
+        s = op.combine_dev(V, nbas, dh, 1, W, -1.0, 1.0);
+        if (s != OMEN_OK) return s;
+      }
+      fresh = false;
+    } else {
+      // three-term step against v_j (alpha) and v_{j-1} (beta, already in T), then one full
+      // pass that removes what rounding left along every basis vector
+      s = op.dots_dev(op.col(V, jstart), 1, W, 1, dh, dT + jstart, ldT, jstart);
+      if (s == OMEN_OK) s = op.combine_dev(op.col(V, jstart), 1, dh, 1, W, -1.0, 1.0);
+      if (s == OMEN_OK)
+        s = op.combine_dev(op.col(V, jstart - 1), 1, dT + jstart + (size_t)(jstart - 1) * ldT, 1, W, -1.0, 1.0);
       if (s != OMEN_OK) return s;
-      s = op.combine_dev(V, nbas, dh, 1, W, -1.0, 1.0);
+      OMEN_CUDA(ctx, cudaMemcpyAsync(dT + (jstart - 1) + (size_t)jstart * ldT, dT + jstart + (size_t)(jstart - 1) * ldT,
+                                     sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+      s = op.dots_dev(V, nbas, W, 1, dh, dT, ldT, jstart);
+      if (s == OMEN_OK) s = op.combine_dev(V, nbas, dh, 1, W, -1.0, 1.0);
       if (s != OMEN_OK) return s;
     }
     s = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
@@ -1266,6 +1284,7 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
         jstart = kk;
         nbas = kk + 1;
         ++restarts;
+        fresh = true;
         continue;
       }
     }
