@@ -321,6 +321,42 @@ def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
                          "train_seconds": t_train}}
 
 
+def measure_kbatch_full(ctx, omen, nk=128, nev=8, seed=4, per_k_sample=4):
+    """The k-batching workload: instances of drawn lateral sizes x 80 cells, each with its donor
+    sheet, nk wave vectors along Gamma-X, nev lowest bands per k, lockstep per instance against one
+    solve per k (per-k time extrapolated from per_k_sample wave vectors per instance)."""
+    import torch
+    out = []
+    tot_b, tot_p, bands = 0.0, 0.0, 0
+    for idx, (nxy, nz, lam) in enumerate(synth.draw_kbatch_instances(seed)):
+        spec = synth.lattice_spec(nxy, nxy, nz, (2, 2, 0), seed=seed + idx)
+        U = synth.donor_sheet_potential(spec, seed + idx, lam)
+        lat = omen.omen_build_lattice(ctx, spec)
+        ham = omen.omen_assemble_H(ctx, lat, synth.gapped_si_params(), precision=omen.OMEN_F32, k=(0.0, 0.0, 0.0),
+                                   U_atom_dev=torch.from_numpy(U).cuda())
+        ks = np.zeros((nk, 3))
+        ks[:, 0] = np.linspace(0.0, 1.0, nk) * np.pi / (nxy * spec.a_nm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, info, st = omen.omen_eigs_kbatch(ctx, ham, ks, nev, tol=1e-6, max_iter=20000, basis=48, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for q in np.linspace(0, nk - 1, per_k_sample).astype(int):
+            omen.omen_eigs_kbatch(ctx, ham, ks[q:q + 1], nev, tol=1e-6, max_iter=20000, basis=48, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        tp = (time.perf_counter() - t0) / per_k_sample * nk
+        out.append({"lateral": nxy, "atoms": spec.natoms, "lambda_TF_nm": lam, "batched_s": tb, "per_k_s": tp,
+                    "converged": info["converged"], "max_residual": info["max_residual"]})
+        tot_b += tb
+        tot_p += tp
+        bands += nk * nev
+        del ham, lat
+    return {"instances": out, "bands": bands, "bands_per_s_batched": bands / tot_b,
+            "bands_per_s_per_k": bands / tot_p, "speedup": tot_p / tot_b,
+            "per_k_time": f"extrapolated from {per_k_sample} wave vectors per instance"}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_1003_4570_gb300 import omen
@@ -464,6 +500,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the Lanczos and k-batch side measurements")
     ap.add_argument("--cells", type=int, default=N_CELLS, help="cells per edge (50 = the 1M-atom workload; "
                     "smaller only for profiling captures)")
+    ap.add_argument("--kbatch-full", action="store_true",
+                    help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
     ap.add_argument("--lanczos-only", type=int, default=0, metavar="ITERS",
                     help="profiling aid: run only ITERS Lanczos iterations (FP64, basis 64) and print their time")
     args = ap.parse_args()
@@ -472,6 +510,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.kbatch_full:
+        import torch
+        from paper_1003_4570_gb300 import omen
+        ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+        print(json.dumps({"kbatch_full": measure_kbatch_full(ctx, omen)}))
         return
     if args.lanczos_only:
         import torch

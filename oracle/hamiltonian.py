@@ -105,6 +105,10 @@ def assemble(spec, params, U_atom=None, kvec=None, spin_orbit=False, row_atoms=N
         for s2 in range(ns):
             for k in range(4):
                 blocks[s1, s2, k] = sk_block(u[k], params.V[s1, s2], params.V[s2, s1], norb)
+    if keep_row is not None:
+        # only bonds that touch a requested row
+        m = keep_row[bonds.a] | keep_row[bonds.b]
+        bonds = lattice.Bonds(bonds.a[m], bonds.b[m], bonds.k[m], bonds.T[m], bonds.slot[m])
     sa = spec.species[bonds.a]
     sb = spec.species[bonds.b]
     f = harrison_factor(1.0 + spec.strain[bonds.slot], params.eta)

@@ -1,0 +1,101 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark times.
+
+The oracle cannot assemble 10M-row matrices quickly, so it computes sampled rows one by one
+(all orbitals of 256 seeded atoms, including every boundary class) from its own neighbour
+search over the whole structure, and the GPU products are compared on those rows:
+* Si0.7Ge0.3 50^3 cells (1,000,000 atoms): FP64 and double-float stored H·X (1e-12 of
+  max |y| over the sample), FP32 stored and matrix-free (2e-6);
+* the same alloy with spin-orbit, complex64 (20M rows, 2e-6);
+* the 4x4x80-cell delta-doped Si slab with its donor-sheet potential, k-batched complex64
+  products at 3 wave vectors (2e-6).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import hamiltonian, lattice  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1003_4570_gb300 import omen
+    return omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+
+
+@pytest.fixture(scope="module")
+def alloy():
+    spec, p = synth.config_sige_alloy(50, seed=2)
+    bonds = lattice.find_bonds(spec.nx, spec.ny, spec.nz, spec.periodic)
+    g = np.random.default_rng(77)
+    ncell = spec.ncells
+    # sample: random atoms plus atoms on the corners / faces of the block
+    corners = [b * ncell + c for b in range(8) for c in (0, ncell - 1, spec.nx - 1, ncell - spec.nx)]
+    atoms = np.unique(np.concatenate([g.choice(spec.natoms, 224, replace=False), corners]))
+    return spec, p, bonds, atoms
+
+
+def sampled_rows(spec, p, bonds, atoms, x, **kw):
+    return hamiltonian.hx_rows(spec, p, x, atoms, bonds=bonds, **kw)
+
+
+@pytest.mark.parametrize("prec,mf", [(0, False), (3, False), (1, False), (1, True)])
+def test_alloy_1m_atoms_sampled_rows(ctx, alloy, prec, mf):
+    from paper_1003_4570_gb300 import omen
+    spec, p, bonds, atoms = alloy
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, matrix_free=mf)
+    n = ham.nrows
+    x = synth.random_vectors(8, n, 1)[0]
+    if prec == omen.OMEN_F64_DF:
+        y = omen.omen_hx_host(ctx, ham, x[None, :], sigma=0.3)[0]
+    else:
+        xd = torch.from_numpy(x.astype(ham.numpy_dtype)).cuda()
+        yd = torch.empty_like(xd)
+        omen.omen_hx(ctx, ham, xd, yd, 1, 0.3)
+        torch.cuda.synchronize()
+        y = yd.cpu().numpy().astype(float)
+        x = x.astype(ham.numpy_dtype).astype(float)
+    rows, ref = sampled_rows(spec, p, bonds, atoms, x)
+    ref = ref - 0.3 * x[rows]
+    tol = 1e-12 if prec in (0, 3) else 2e-6
+    np.testing.assert_allclose(y[rows], ref, atol=tol * np.abs(ref).max(), rtol=0)
+
+
+def test_alloy_spin_orbit_1m_atoms_sampled_rows(ctx, alloy):
+    from paper_1003_4570_gb300 import omen
+    spec, p, bonds, atoms = alloy
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F32, spin_orbit=True)
+    x = synth.random_vectors(9, ham.nrows, 1, dtype=complex)[0].astype(np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    omen.omen_hx(ctx, ham, xd, yd)
+    torch.cuda.synchronize()
+    rows, ref = sampled_rows(spec, p, bonds, atoms, x.astype(complex), spin_orbit=True)
+    np.testing.assert_allclose(yd.cpu().numpy()[rows], ref, atol=2e-6 * np.abs(ref).max(), rtol=0)
+
+
+def test_delta_layer_kbatch_sampled_rows(ctx):
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(4, 4, 80, (2, 2, 0), seed=7)
+    p = synth.gapped_si_params()
+    U = synth.donor_sheet_potential(spec, 7, synth.draw_kbatch_instances(7)[0][2])
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F32, k=(0.0, 0.0, 0.0),
+                               U_atom_dev=torch.from_numpy(U).cuda())
+    ks = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [1.4459, 0.0, 0.0]])
+    x = synth.random_vectors(10, ham.nrows, len(ks), dtype=complex).astype(np.complex64)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    omen.omen_hx_kbatch(ctx, ham, ks, xd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    bonds = lattice.find_bonds(spec.nx, spec.ny, spec.nz, spec.periodic)
+    atoms = np.random.default_rng(5).choice(spec.natoms, 200, replace=False)
+    for q, kv in enumerate(ks):
+        rows, ref = hamiltonian.hx_rows(spec, p, x[q].astype(complex), atoms, bonds=bonds, U_atom=U, kvec=kv)
+        np.testing.assert_allclose(y[q][rows], ref, atol=2e-6 * np.abs(ref).max(), rtol=0)
