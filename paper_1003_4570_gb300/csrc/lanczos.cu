@@ -261,6 +261,138 @@ __global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long
   }
 }
 
+// Projections onto NB right-hand columns at once (2 <= NB <= 4): CTA (g, c) handles basis
+// vectors IG*g .. IG*g + IG-1 (IG = 16 / NB) over row chunk c; every basis load serves all NB
+// columns.  Partials P[chunk][i][j].
+template <typename T, bool C, int NB>
+__global__ void __launch_bounds__(256) dotsn_kernel(const void* Av, long long lda, int na, const void* Bv, long long ldb,
+                                                    int nb, long long n, int rows_per_cta, double2* __restrict__ P) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  using Acc = std::conditional_t<sizeof(T) == 8, double, float>;
+  constexpr int IG = 16 / NB;
+  const V* A = static_cast<const V*>(Av);
+  const V* B = static_cast<const V*>(Bv);
+  const int i0 = blockIdx.x * IG;
+  const int ni = min(IG, na - i0);
+  const long long r0 = (long long)blockIdx.y * rows_per_cta;
+  const long long r1 = min(n, r0 + rows_per_cta);
+  Acc sr[IG][NB], si[IG][NB];
+#pragma unroll
+  for (int i = 0; i < IG; ++i)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) { sr[i][j] = 0; si[i][j] = 0; }
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    V bv[NB], av[IG];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      if (j < nb) bv[j] = B[(size_t)j * ldb + r];
+#pragma unroll
+    for (int i = 0; i < IG; ++i)
+      if (i < ni) av[i] = A[(size_t)(i0 + i) * lda + r];
+#pragma unroll
+    for (int i = 0; i < IG; ++i)
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        if (i < ni && j < nb) {
+          if constexpr (C) {
+            sr[i][j] += (Acc)av[i].x * (Acc)bv[j].x + (Acc)av[i].y * (Acc)bv[j].y;
+            si[i][j] += (Acc)av[i].x * (Acc)bv[j].y - (Acc)av[i].y * (Acc)bv[j].x;
+          } else {
+            sr[i][j] += (Acc)av[i] * (Acc)bv[j];
+          }
+        }
+  }
+  __shared__ double red[8][16][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < IG; ++i)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      double vr = (double)sr[i][j], vi = (double)si[i][j];
+      for (int o = 16; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o);
+        if constexpr (C) vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      }
+      if (lane == 0) { red[warp][i * NB + j][0] = vr; red[warp][i * NB + j][1] = vi; }
+    }
+  __syncthreads();
+  if (threadIdx.x < IG * NB) {
+    const int i = threadIdx.x / NB, j = threadIdx.x % NB;
+    if (i < ni && j < nb) {
+      double vr = 0.0, vi = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { vr += red[w][threadIdx.x][0]; vi += red[w][threadIdx.x][1]; }
+      P[((size_t)blockIdx.y * na + i0 + i) * nb + j] = make_double2(vr, C ? vi : 0.0);
+    }
+  }
+}
+
+// Y_j = beta Y_j + alpha sum_i A_i M[i + j*na] for NB (<= 4) columns at once.
+template <typename T, bool C, int NB>
+__global__ void __launch_bounds__(256) combinen_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M,
+                                                       int nb, void* Yv, long long ldy, long long n, double alpha, double beta) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* Ms = reinterpret_cast<double2*>(smem_raw);
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Ms[t] = M[t];
+  __syncthreads();
+  const V* A = static_cast<const V*>(Av);
+  V* Y = static_cast<V*>(Yv);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    double yr[NB], yi[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) { yr[j] = 0.0; yi[j] = 0.0; }
+    int i = 0;
+    for (; i + 4 <= na; i += 4) {
+      V av[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) av[k] = A[(size_t)(i + k) * lda + r];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double xr = E::re(av[k]), xi = E::im(av[k]);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+          if (j < nb) {
+            const double2 m = Ms[i + k + j * na];
+            yr[j] = fma(xr, m.x, yr[j]);
+            if constexpr (C) {
+              yr[j] = fma(-xi, m.y, yr[j]);
+              yi[j] = fma(xr, m.y, yi[j]);
+              yi[j] = fma(xi, m.x, yi[j]);
+            }
+          }
+      }
+    }
+    for (; i < na; ++i) {
+      const V a = A[(size_t)i * lda + r];
+      const double xr = E::re(a), xi = E::im(a);
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        if (j < nb) {
+          const double2 m = Ms[i + j * na];
+          yr[j] = fma(xr, m.x, yr[j]);
+          if constexpr (C) {
+            yr[j] = fma(-xi, m.y, yr[j]);
+            yi[j] = fma(xr, m.y, yi[j]);
+            yi[j] = fma(xi, m.x, yi[j]);
+          }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      if (j < nb) {
+        V& out = Y[(size_t)j * ldy + r];
+        double orr = alpha * yr[j], oi = alpha * yi[j];
+        if (beta != 0.0) {
+          orr += beta * E::re(out);
+          oi += beta * E::im(out);
+        }
+        out = E::make(orr, oi);
+      }
+  }
+}
+
 // Device-side reduction of the partials into out (na x nb, column-major) and, optionally,
 // into columns col0.. of the projected matrix T (ldT x ldT, column-major).
 __global__ void reduce_dev_kernel(const double2* __restrict__ P, int nchunks, int na, int nb, double2* __restrict__ out,
@@ -568,11 +700,24 @@ struct KrylovOps {
   omen_status dots_dev(const void* A, int na, const void* B, int nb, double2* out_dev, double2* accT, int ldT, int col0) {
     if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "dots_dev: too many columns");
     if (nb > 1 && nb <= 4) {
-      // a few right-hand columns: the single-column kernel per column (fast path for small blocks)
-      for (int j = 0; j < nb; ++j) {
-        omen_status sj = dots_dev(A, na, col(const_cast<void*>(B), j), 1, out_dev + (size_t)j * na, accT, ldT, col0 + j);
-        if (sj != OMEN_OK) return sj;
-      }
+      // a few right-hand columns: one launch, each basis load serving every column
+      int rows = 8192;
+      while ((n + rows - 1) / rows > 65535) rows *= 2;
+      const long long nchunks = (n + rows - 1) / rows;
+      omen_status s1 = ensure_partial((size_t)nchunks * na * nb);
+      if (s1 != OMEN_OK) return s1;
+      const int ig = (nb <= 2) ? 8 : 4;
+      dim3 grid((na + ig - 1) / ig, (unsigned)nchunks);
+#define DOTSN(T, Cc)                                                                                     \
+  do {                                                                                                   \
+    if (nb <= 2) dotsn_kernel<T, Cc, 2><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, nb, n, rows, d_partial); \
+    else dotsn_kernel<T, Cc, 4><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, nb, n, rows, d_partial);        \
+  } while (0)
+      if (prec == OMEN_F64) { if (cplx) DOTSN(double, true); else DOTSN(double, false); }
+      else { if (cplx) DOTSN(float, true); else DOTSN(float, false); }
+#undef DOTSN
+      reduce_dev_kernel<<<na * nb, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, nb, out_dev, accT, ldT, col0);
+      OMEN_CHECK_LAUNCH(ctx);
       return OMEN_OK;
     }
     if (nb == 1) {
@@ -615,10 +760,22 @@ struct KrylovOps {
   omen_status combine_dev(const void* A, int na, const double2* M_dev, int nb, void* Y, double alpha, double beta) {
     if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "combine_dev: too many columns");
     if (nb > 1 && nb <= 4) {
-      for (int j = 0; j < nb; ++j) {
-        omen_status sj = combine_dev(A, na, M_dev + (size_t)j * na, 1, col(Y, j), alpha, beta);
-        if (sj != OMEN_OK) return sj;
-      }
+      const size_t shmn = (size_t)na * nb * sizeof(double2);
+      const unsigned gridn = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+#define COMBN(T, Cc)                                                                                        \
+  do {                                                                                                      \
+    if (nb <= 2) {                                                                                          \
+      smem_limit(combinen_kernel<T, Cc, 2>, shmn);                                                          \
+      combinen_kernel<T, Cc, 2><<<gridn, 256, shmn, ctx->stream>>>(A, n, na, M_dev, nb, Y, n, n, alpha, beta); \
+    } else {                                                                                                \
+      smem_limit(combinen_kernel<T, Cc, 4>, shmn);                                                          \
+      combinen_kernel<T, Cc, 4><<<gridn, 256, shmn, ctx->stream>>>(A, n, na, M_dev, nb, Y, n, n, alpha, beta); \
+    }                                                                                                       \
+  } while (0)
+      if (prec == OMEN_F64) { if (cplx) COMBN(double, true); else COMBN(double, false); }
+      else { if (cplx) COMBN(float, true); else COMBN(float, false); }
+#undef COMBN
+      OMEN_CHECK_LAUNCH(ctx);
       return OMEN_OK;
     }
     if (nb == 1) {
