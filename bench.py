@@ -44,6 +44,19 @@ def measured_peaks():
         return {}
 
 
+def max_over_ranks(value, dist, device):
+    """The slowest rank's time (the job's time) — every rank gets the same value."""
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, bytes_per_step, steps, seconds):
+    """Whole-job throughput of weakly scaled replicas: all ranks' bytes over the slowest time."""
+    return world * bytes_per_step * steps / seconds / 1e9
+
+
 def alg_bytes_per_hx(nbonds, natoms, nrows, elem, vec_elem, matrix_free):
     h = 0 if matrix_free else nbonds * 100 * elem
     extra = natoms * (1 + 8) + (nbonds * 8 if matrix_free else 0)
@@ -408,11 +421,9 @@ def run_gpu(args, rank, world, local_rank):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     if dist:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(ms, dist, "cuda")
     alg = alg_bytes_per_hx(nbonds, natoms, ham.nrows, el, el, args.matrix_free)
-    value = world * 2 * alg * args.steps / (ms / 1e3) / 1e9
+    value = job_throughput(world, 2 * alg, args.steps, ms / 1e3)
     launch_ms = ms / (2 * args.steps)
 
     # end to end through the host-buffer entry point (pinned host x, y; copies timed)
@@ -430,10 +441,8 @@ def run_gpu(args, rank, world, local_rank):
         ctx.check(L.omen_hx_host(ctx.handle, ham.handle, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(yh.data_ptr()), 1, sigma))
     e2e_s = time.perf_counter() - t0
     if dist:
-        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_val = world * alg * e2e_steps / e2e_s / 1e9
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e_val = job_throughput(world, alg, e2e_steps, e2e_s)
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs") or 6800.0

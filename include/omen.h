@@ -44,7 +44,8 @@ typedef enum {
   OMEN_ENOMEM = 2,       /* device or host allocation failed */
   OMEN_ENOCONV = 3,      /* iteration limit reached; partial results and info are filled */
   OMEN_ENUMERIC = 4,     /* NaN/Inf or breakdown that could not be recovered */
-  OMEN_ETIMEOUT = 5,     /* a bounded device wait expired */
+  OMEN_ETIMEOUT = 5,     /* reserved: no kernel of this build waits on a flag (the CG solver's
+                            grid barriers are those of a cooperative launch) */
   OMEN_ECUDA = 6,        /* CUDA runtime error (message has the CUDA error string) */
   OMEN_EUNSUPPORTED = 7  /* valid request that this build does not implement */
 } omen_status;
@@ -77,9 +78,6 @@ typedef struct omen_ham omen_ham;
 omen_status omen_create(omen_ctx** out, int device, void* cuda_stream);
 void omen_destroy(omen_ctx* ctx);
 const char* omen_last_error(const omen_ctx* ctx);
-/* Set the iteration budget of bounded device waits (0 = library default).  A wait that
- * exhausts it makes the call return OMEN_ETIMEOUT with the device still usable. */
-omen_status omen_set_wait_limit(omen_ctx* ctx, long long spins);
 
 /* ---- structure (paper Section II-A: atoms of the domain and their neighbours) ---------- */
 

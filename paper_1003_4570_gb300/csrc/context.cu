@@ -15,7 +15,6 @@ extern "C" omen_status omen_create(omen_ctx** out, int device, void* stream) {
   auto* c = new omen_ctx();
   c->device = device;
   c->stream = static_cast<cudaStream_t>(stream);
-  c->wait_limit = 0;
   c->work_bytes = 1 << 20;
   if (cudaMalloc(&c->d_work, c->work_bytes) != cudaSuccess || cudaMalloc(&c->d_status, 64 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -34,9 +33,3 @@ extern "C" void omen_destroy(omen_ctx* c) {
 }
 
 extern "C" const char* omen_last_error(const omen_ctx* c) { return c ? c->err.c_str() : "null context"; }
-
-extern "C" omen_status omen_set_wait_limit(omen_ctx* c, long long spins) {
-  if (!c || spins < 0) return set_err(c, OMEN_EINVAL, "invalid wait limit");
-  c->wait_limit = spins;
-  return OMEN_OK;
-}

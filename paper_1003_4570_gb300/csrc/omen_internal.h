@@ -13,7 +13,6 @@ struct omen_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   std::string err;
-  long long wait_limit = 0;
   // small device work area: reduction partials and a status word
   double* d_work = nullptr;
   size_t work_bytes = 0;

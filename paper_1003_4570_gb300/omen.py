@@ -113,7 +113,6 @@ def lib():
             "omen_create": (i, [C.POINTER(vp), i, vp]),
             "omen_destroy": (None, [vp]),
             "omen_last_error": (C.c_char_p, [vp]),
-            "omen_set_wait_limit": (i, [vp, ll]),
             "omen_build_lattice": (i, [vp, C.POINTER(LatticeDesc), C.POINTER(vp)]),
             "omen_free_lattice": (None, [vp]),
             "omen_lattice_counts": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),

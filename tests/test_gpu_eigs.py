@@ -84,3 +84,21 @@ def test_iteration_limit_returns_enoconv(ctx):
     ev, info, st = omen.omen_eigs(ctx, ham, 4, tol=1e-12, block=1, basis=16, max_iter=5, raise_on_noconv=False)
     assert st == omen.OMEN_ENOCONV
     assert info["iterations"] == 5 and np.all(np.isfinite(ev))
+
+
+def test_non_finite_input_returns_enumeric(ctx):
+    """A NaN in the potential poisons H·X; the solver must report OMEN_ENUMERIC, not hang."""
+    from paper_1003_4570_gb300 import omen
+    spec, p = synth.config_si_periodic(2, seed=1)
+    U = np.zeros(spec.natoms)
+    U[5] = np.nan
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, U_atom_dev=torch.from_numpy(U).cuda())
+    for block in (1, 2):
+        with pytest.raises(omen.OmenError) as e:
+            omen.omen_eigs(ctx, ham, 4, tol=1e-9, block=block, basis=24, max_iter=200)
+        assert e.value.status == omen.OMEN_ENUMERIC
+    # the context stays usable afterwards
+    ham2 = omen.omen_assemble_H(ctx, lat, p)
+    ev, info, st = omen.omen_eigs(ctx, ham2, 2, tol=1e-9, block=8, basis=48, max_iter=500)
+    assert st == omen.OMEN_OK
