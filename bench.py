@@ -222,6 +222,51 @@ def measure_eigs_1m(ctx, omen, lat, p, nev=16):
     return out
 
 
+def measure_small_si(ctx, omen, n=8, nev=8):
+    """Bulk Si 8^3 cells, periodic, sp3s* (20,480 rows, FP64): seconds to the 8 lowest
+    eigenpairs at 1e-9 eV — single-vector Lanczos with and without graph replay of the steps,
+    and block Lanczos (b = 8).  At this size every kernel is a few microseconds long, so the
+    launch path, not HBM, sets the pace."""
+    import torch
+    spec, p = synth.config_si_periodic(n, seed=1)
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p)
+    out = {"rows": ham.nrows}
+    for name, block, graphs in (("single_graphs", 1, True), ("single_direct", 1, False), ("block8", 8, True)):
+        omen.omen_set_graph_capture(ctx, graphs)
+        best = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev, info, st = omen.omen_eigs(ctx, ham, nev, omen.OMEN_LOWEST, tol=1e-9, block=block, basis=64,
+                                          max_iter=4000, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        out[name] = {"seconds": best, "iterations": info["iterations"], "converged": info["converged"],
+                     "max_error_bound": info["max_error_bound"],
+                     "ms_per_iteration": 1e3 * best / max(1, info["iterations"])}
+    omen.omen_set_graph_capture(ctx, True)
+    return out
+
+
+def measure_cube_500(ctx, omen, n=80, iters=500):
+    """The paper's 3-D benchmark unit (Section II-B, Fig. 3): 500 Lanczos iterations on a Si
+    cube of 80^3 conventional cells (4,096,000 atoms, sp3d5s*, hard wall), FP64 and FP32."""
+    import torch
+    spec = synth.lattice_spec(n, n, n, (0, 0, 0), seed=11)
+    p = synth.draw_tb_params(11, 10, 1)
+    lat = omen.omen_build_lattice(ctx, spec)
+    out = {"atoms": spec.natoms}
+    for name, prec in (("f64", omen.OMEN_F64), ("f32", omen.OMEN_F32)):
+        ham = omen.omen_assemble_H(ctx, lat, p, precision=prec)
+        out[name] = measure_lanczos(ctx, omen, ham, iters=iters)
+        out["rows"] = ham.nrows
+        del ham
+        torch.cuda.empty_cache()
+    return out
+
+
 def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
     """Bands/s of the lockstep k-batched solve against one solve per k (same solver, nk = 1)."""
     import torch
@@ -236,11 +281,13 @@ def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
     ks[:, 0] = np.linspace(0.0, 1.0, nk) * np.pi / (nxy * spec.a_nm)
     out = {"workload": f"delta-doped Si {nxy}x{nxy}x{nz} cells ({spec.natoms} atoms), donor sheet lambda_TF "
                        f"{lam:.2f} nm, sp3d5s* complex64, {nk} k along Gamma-X, {nev} bands per k"}
+    out["tile_batched"] = omen.omen_tune_hx_kbatch(ctx, ham, nk, reps=5)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ev, info, st = omen.omen_eigs_kbatch(ctx, ham, ks, nev, tol=1e-6, max_iter=20000, basis=64, raise_on_noconv=False)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
+    out["tile_per_k"] = omen.omen_tune_hx_kbatch(ctx, ham, 1, reps=5)
     t0 = time.perf_counter()
     for q in range(nk):
         ev1, _, _ = omen.omen_eigs_kbatch(ctx, ham, ks[q:q + 1], nev, tol=1e-6, max_iter=20000, basis=64,
@@ -252,6 +299,7 @@ def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
     # folded spectrum near the conduction-band edge, fixed step budget (does not converge here)
     steps = 200
     sigma = synth.GAPPED_SI_EC - 0.2
+    omen.omen_tune_hx_kbatch(ctx, ham, nk, reps=5)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     omen.omen_eigs_kbatch(ctx, ham, ks, nev, which=omen.OMEN_NEAREST, sigma=sigma, tol=1e-12, max_iter=steps,
@@ -259,6 +307,7 @@ def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
     torch.cuda.synchronize()
     fb = time.perf_counter() - t0
     nper = 4
+    omen.omen_tune_hx_kbatch(ctx, ham, 1, reps=5)
     t0 = time.perf_counter()
     for q in range(nper):
         omen.omen_eigs_kbatch(ctx, ham, ks[q:q + 1], nev, which=omen.OMEN_NEAREST, sigma=sigma, tol=1e-12,
@@ -349,18 +398,22 @@ def measure_kbatch_full(ctx, omen, nk=128, nev=8, seed=4, per_k_sample=4):
                                    U_atom_dev=torch.from_numpy(U).cuda())
         ks = np.zeros((nk, 3))
         ks[:, 0] = np.linspace(0.0, 1.0, nk) * np.pi / (nxy * spec.a_nm)
+        tile_b = omen.omen_tune_hx_kbatch(ctx, ham, nk, reps=5)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev, info, st = omen.omen_eigs_kbatch(ctx, ham, ks, nev, tol=1e-6, max_iter=20000, basis=48, raise_on_noconv=False)
         torch.cuda.synchronize()
         tb = time.perf_counter() - t0
+        tile_p = omen.omen_tune_hx_kbatch(ctx, ham, 1, reps=5)
         t0 = time.perf_counter()
         for q in np.linspace(0, nk - 1, per_k_sample).astype(int):
             omen.omen_eigs_kbatch(ctx, ham, ks[q:q + 1], nev, tol=1e-6, max_iter=20000, basis=48, raise_on_noconv=False)
         torch.cuda.synchronize()
         tp = (time.perf_counter() - t0) / per_k_sample * nk
         out.append({"lateral": nxy, "atoms": spec.natoms, "lambda_TF_nm": lam, "batched_s": tb, "per_k_s": tp,
-                    "converged": info["converged"], "max_residual": info["max_residual"]})
+                    "converged": info["converged"], "max_residual": info["max_residual"],
+                    "tile_batched": [tile_b["threads"], tile_b["rows_per_batch"]],
+                    "tile_per_k": [tile_p["threads"], tile_p["rows_per_batch"]]})
         tot_b += tb
         tot_p += tp
         bands += nk * nev
@@ -398,6 +451,9 @@ def run_gpu(args, rank, world, local_rank):
     t = torch.empty_like(x)
     y = torch.empty_like(x)
     sigma = 0.3
+    # launch shape of the product: timed on this Hamiltonian by the library's tuner (identical
+    # results for every shape); the double-float kernel has one shape
+    tile = None if prec == omen.OMEN_F64_DF else omen.omen_tune_hx(ctx, ham, prec, nvec=1, reps=5)
 
     def step():
         omen.omen_hx(ctx, ham, x, t, 1, sigma)
@@ -452,7 +508,8 @@ def run_gpu(args, rank, world, local_rank):
         achieved_tf = fl / (launch_ms / 1e3) / 1e12
         # DRAM bytes per launch of this kernel at this workload, from the ncu launch list in
         # profiles/hx_kernel_sige_alloy.md (null for other workloads)
-        traffic = 2.552e9 if (args.cells == N_CELLS and not args.matrix_free) else None
+        default_shape = tile is not None and tile["threads"] == 128 and tile["rows_per_batch"] in (0, 1)
+        traffic = 2.552e9 if (args.cells == N_CELLS and not args.matrix_free and default_shape) else None
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "hx_kernel<double,10,real,stored>", "hbm_achieved_gbs": achieved_gbs,
@@ -470,6 +527,7 @@ def run_gpu(args, rank, world, local_rank):
                                      "strain, sp3d5s*; step = folded operator (H-sigma)^2 x (two H·X)",
                          "atoms": natoms, "bonds": nbonds, "rows": ham.nrows,
                          "storage": "matrix-free" if args.matrix_free else "stored bond blocks",
+                         "launch_shape": tile,
                          "l2": "no flush: H blocks exceed L2", "parallelism": f"replicas x{world}"},
               "roofline": roof, "gpu_launches": 2 * args.steps,
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": ham.nrows * el,
@@ -481,6 +539,9 @@ def run_gpu(args, rank, world, local_rank):
         if args.cells == N_CELLS and prec == omen.OMEN_F64 and not args.matrix_free:
             del ham
             result["eigs_16_lowest_1M_atoms"] = measure_eigs_1m(ctx, omen, lat, p)
+        result["eigs_8_lowest_si_8cubed"] = measure_small_si(ctx, omen)
+        if args.cells == N_CELLS:
+            result["lanczos_500_iterations_80cubed_si"] = measure_cube_500(ctx, omen)
         result["kbatch"] = measure_kbatch(ctx, omen)
         result["scf_learned_vs_zero"] = measure_scf(ctx, omen)
     if rank == 0 and not args.no_cpu:

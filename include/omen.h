@@ -79,6 +79,12 @@ omen_status omen_create(omen_ctx** out, int device, void* cuda_stream);
 void omen_destroy(omen_ctx* ctx);
 const char* omen_last_error(const omen_ctx* ctx);
 
+/* Replay Lanczos steps as CUDA graphs (default on).  The single-vector solver captures the
+ * kernel sequence of the steps between two host convergence checks once and replays it on
+ * later cycles; results are identical either way (same kernels, same order).  The paper has
+ * no counterpart: launch overhead was not a cost on its CPUs.  EINVAL for a null context. */
+omen_status omen_set_graph_capture(omen_ctx* ctx, int enable);
+
 /* ---- structure (paper Section II-A: atoms of the domain and their neighbours) ---------- */
 
 typedef struct {
@@ -146,6 +152,39 @@ omen_status omen_convert_vectors(omen_ctx* ctx, const void* src_dev, int src_pre
 /* The same product with host buffers (copies in and out on the ctx stream; synchronous). */
 omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* ham, const void* x_host, void* y_host,
                          int nvec, double sigma);
+
+/* ---- launch-shape tuning of the products (no counterpart in the paper) ------------------ */
+
+typedef struct {
+  int threads;               /* CTA width chosen (threads per block) */
+  int rows_per_batch;        /* block rows per register batch (omen_tune_hx) or wave vectors
+                                per thread (omen_tune_hx_kbatch); 0 = the built-in rule */
+  int candidates;            /* launch shapes timed */
+  double ms_best;            /* mean launch time of the chosen shape (ms) */
+  double ms_default;         /* mean launch time of the built-in shape (ms) */
+} omen_tune_result;
+
+/* Time every compiled launch shape of omen_hx on this Hamiltonian (nvec vectors of precision
+ * OMEN_F64 or OMEN_F32, `reps` timed launches each after two warm-ups, CUDA events on the ctx
+ * stream) and keep the fastest for later products and solves with that vector precision.
+ * Allocates and frees two scratch blocks of nvec vectors; synchronises the stream.  Results
+ * of the product do not depend on the shape.  out may be NULL.  EINVAL for a precision
+ * without blocks in this Hamiltonian. */
+omen_status omen_tune_hx(omen_ctx* ctx, omen_ham* ham, int vec_precision, int nvec, int reps,
+                         omen_tune_result* out);
+
+/* The same for the k-batched product with nk wave vectors (Bloch Hamiltonian, stored blocks,
+ * no spin-orbit); the vector precision is the Hamiltonian's. */
+omen_status omen_tune_hx_kbatch(omen_ctx* ctx, omen_ham* ham, int nk, int reps, omen_tune_result* out);
+
+/* Set a launch shape directly: threads a multiple of 32 in 32..128 (0 = default 128) and
+ * rows_per_batch from the compiled set (FP32 stored blocks 1, 2, 5, and 10 without spin-orbit
+ * for sp3d5s*; FP64 stored 1, 2; 0 = the built-in rule; rows_per_batch must divide the
+ * orbital count).  k batch: wave vectors per thread 1, 2 (FP64 and FP32) or 4 (FP32), 0 =
+ * default 2.  EINVAL for a shape that is not compiled. */
+omen_status omen_hx_set_tile(omen_ctx* ctx, omen_ham* ham, int vec_precision, int threads, int rows_per_batch);
+omen_status omen_hx_kbatch_set_tile(omen_ctx* ctx, omen_ham* ham, int vec_precision, int threads,
+                                    int k_per_thread);
 
 /* ---- eigenpairs (paper Section III-A item 1: (block) Lanczos) -------------------------- */
 

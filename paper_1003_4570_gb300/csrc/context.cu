@@ -29,7 +29,14 @@ extern "C" void omen_destroy(omen_ctx* c) {
   if (!c) return;
   cudaFree(c->d_work);
   cudaFree(c->d_status);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
+}
+
+extern "C" omen_status omen_set_graph_capture(omen_ctx* c, int enable) {
+  if (!c) return OMEN_EINVAL;
+  c->use_graphs = enable != 0;
+  return OMEN_OK;
 }
 
 extern "C" const char* omen_last_error(const omen_ctx* c) { return c ? c->err.c_str() : "null context"; }

@@ -64,7 +64,9 @@ template <typename T, typename C> __device__ __forceinline__ void fma_c(C& acc, 
   acc.y = fma(h, x.y, acc.y);
 }
 
-template <typename T, int NORB, bool CPLX, bool SO, bool MATFREE>
+// RBT: block rows loaded per register batch (0 = the built-in rule below); the CTA width
+// (blockDim.x, a multiple of 32 up to 128) and RBT are the tile shape the tuner chooses.
+template <typename T, int NORB, bool CPLX, bool SO, bool MATFREE, int RBT>
 __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
   using V = typename VecT<T, CPLX>::t;
   constexpr int NS = SO ? 2 : 1;
@@ -194,8 +196,10 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
         }
     }
     // Rows of the block are loaded RB at a time into registers before their FMAs, so each
-    // thread keeps RB*NORB independent loads in flight (memory-level parallelism).
-    constexpr int RB = (sizeof(T) == 8 || MATFREE) ? 1 : (NS == 1 ? NORB : (NORB == 10 ? 5 : NORB));
+    // thread keeps RB*NORB independent loads in flight (memory-level parallelism).  Every
+    // accumulator sums its terms in the same order for any RB: the result does not depend on it.
+    constexpr int RB = RBT > 0 ? RBT : ((sizeof(T) == 8 || MATFREE) ? 1 : (NS == 1 ? NORB : (NORB == 10 ? 5 : NORB)));
+    static_assert(NORB % RB == 0, "RB must divide the orbital count");
 #pragma unroll
     for (int r0 = 0; r0 < NORB; r0 += RB) {
       T hr[RB * NORB];
@@ -489,19 +493,57 @@ size_t vec_elem_bytes(const omen_ham* h, int precision) {
   return h->is_complex ? 2 * r : r;
 }
 
-template <typename T, int NORB, bool CPLX, bool SO, bool MF>
-static cudaError_t launch_t(const HxArgs<T>& a, int nvec, cudaStream_t st) {
-  dim3 grid(((a.g.ncells + 127) / 128) * 8, 1, nvec);
-  hx_kernel<T, NORB, CPLX, SO, MF><<<grid, 128, 0, st>>>(a);
+template <typename T, int NORB, bool CPLX, bool SO, bool MF, int RBT>
+static cudaError_t launch_t(const HxArgs<T>& a, int nvec, int threads, cudaStream_t st) {
+  dim3 grid(((a.g.ncells + threads - 1) / threads) * 8, 1, nvec);
+  hx_kernel<T, NORB, CPLX, SO, MF, RBT><<<grid, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
+// Register-batch sizes compiled for each variant (0 = the built-in rule): FP32 stored blocks
+// take 1, 2, 5 or NORB rows (NORB only without spin-orbit); FP64 stored 1 or 2; matrix-free
+// only the rule.
+template <typename T, int NORB, bool SO, bool MF>
+static constexpr bool rb_compiled(int rb) {
+  if (rb == 0) return true;
+  if (MF || NORB % rb != 0) return false;
+  if (sizeof(T) == 8) return rb == 1 || rb == 2;
+  return rb == 1 || rb == 2 || rb == 5 || (rb == NORB && !SO);
+}
+
+template <typename T, int NORB, bool CPLX, bool SO, bool MF>
+static cudaError_t launch_rb(const HxArgs<T>& a, int nvec, HxTile t, cudaStream_t st) {
+  const int thr = t.threads ? t.threads : 128;
+  if constexpr (rb_compiled<T, NORB, SO, MF>(1)) if (t.rb == 1) return launch_t<T, NORB, CPLX, SO, MF, 1>(a, nvec, thr, st);
+  if constexpr (rb_compiled<T, NORB, SO, MF>(2)) if (t.rb == 2) return launch_t<T, NORB, CPLX, SO, MF, 2>(a, nvec, thr, st);
+  if constexpr (rb_compiled<T, NORB, SO, MF>(5)) if (t.rb == 5) return launch_t<T, NORB, CPLX, SO, MF, 5>(a, nvec, thr, st);
+  if constexpr (rb_compiled<T, NORB, SO, MF>(10)) if (t.rb == 10) return launch_t<T, NORB, CPLX, SO, MF, 10>(a, nvec, thr, st);
+  return launch_t<T, NORB, CPLX, SO, MF, 0>(a, nvec, thr, st);
+}
+
 template <typename T, int NORB>
-static cudaError_t launch_norb(const HxArgs<T>& a, const omen_ham* h, int nvec, cudaStream_t st) {
+static cudaError_t launch_norb(const HxArgs<T>& a, const omen_ham* h, int nvec, HxTile t, cudaStream_t st) {
   const bool mf = h->matrix_free;
-  if (!h->is_complex) return mf ? launch_t<T, NORB, false, false, true>(a, nvec, st) : launch_t<T, NORB, false, false, false>(a, nvec, st);
-  if (!h->spin_orbit) return mf ? launch_t<T, NORB, true, false, true>(a, nvec, st) : launch_t<T, NORB, true, false, false>(a, nvec, st);
-  return mf ? launch_t<T, NORB, true, true, true>(a, nvec, st) : launch_t<T, NORB, true, true, false>(a, nvec, st);
+  if (!h->is_complex) return mf ? launch_rb<T, NORB, false, false, true>(a, nvec, t, st) : launch_rb<T, NORB, false, false, false>(a, nvec, t, st);
+  if (!h->spin_orbit) return mf ? launch_rb<T, NORB, true, false, true>(a, nvec, t, st) : launch_rb<T, NORB, true, false, false>(a, nvec, t, st);
+  return mf ? launch_rb<T, NORB, true, true, true>(a, nvec, t, st) : launch_rb<T, NORB, true, true, false>(a, nvec, t, st);
+}
+
+// Whether (threads, rb) is a compiled tile shape for this Hamiltonian and vector precision.
+bool hx_tile_valid(const omen_ham* h, int vec_precision, int threads, int rb) {
+  if (threads != 0 && (threads < 32 || threads > 128 || threads % 32 != 0)) return false;
+  const bool f64 = vec_precision == OMEN_F64;
+  const bool so = h->spin_orbit, mf = h->matrix_free;
+  if (h->norb == 10) {
+    if (f64) return so ? (mf ? rb_compiled<double, 10, true, true>(rb) : rb_compiled<double, 10, true, false>(rb))
+                       : (mf ? rb_compiled<double, 10, false, true>(rb) : rb_compiled<double, 10, false, false>(rb));
+    return so ? (mf ? rb_compiled<float, 10, true, true>(rb) : rb_compiled<float, 10, true, false>(rb))
+              : (mf ? rb_compiled<float, 10, false, true>(rb) : rb_compiled<float, 10, false, false>(rb));
+  }
+  if (f64) return so ? (mf ? rb_compiled<double, 5, true, true>(rb) : rb_compiled<double, 5, true, false>(rb))
+                     : (mf ? rb_compiled<double, 5, false, true>(rb) : rb_compiled<double, 5, false, false>(rb));
+  return so ? (mf ? rb_compiled<float, 5, true, true>(rb) : rb_compiled<float, 5, true, false>(rb))
+            : (mf ? rb_compiled<float, 5, false, true>(rb) : rb_compiled<float, 5, false, false>(rb));
 }
 
 template <typename T>
@@ -526,7 +568,8 @@ static cudaError_t launch_prec(const omen_ham* h, const T* blk, const T* b0, con
   for (int d = 0; d < 3; ++d) a.phase[d] = h->phase[d];
   a.ns = h->nspecies;
   a.slot_stride = h->slot_stride;
-  return h->norb == 10 ? launch_norb<T, 10>(a, h, nvec, st) : launch_norb<T, 5>(a, h, nvec, st);
+  const HxTile t = h->tile[sizeof(T) == 8 ? 0 : 1];
+  return h->norb == 10 ? launch_norb<T, 10>(a, h, nvec, t, st) : launch_norb<T, 5>(a, h, nvec, t, st);
 }
 
 omen_status launch_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma, int vec_precision) {
@@ -605,7 +648,24 @@ extern "C" omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* h, const void
   return OMEN_OK;
 }
 
-static constexpr int kKB = 2;   // wave vectors per thread (register budget: 2 x 10 complex amplitudes per bond)
+// Wave vectors per thread KB: 2 by default (the FP64 register budget: 2 x 10 complex
+// amplitudes per bond); 1, 2, 4 compiled for FP32 and 1, 2 for FP64.
+static constexpr int kKB = 2;
+static bool kb_compiled(bool f64, int kb) { return kb == 0 || kb == 1 || kb == 2 || (!f64 && kb == 4); }
+
+bool hx_kbatch_tile_valid(int vec_precision, int threads, int kb) {
+  if (threads != 0 && (threads < 32 || threads > 128 || threads % 32 != 0)) return false;
+  return kb_compiled(vec_precision == OMEN_F64, kb);
+}
+
+template <typename T, int KB>
+static cudaError_t launch_kb(const HxArgs<T>& a, const omen_ham* h, const double2* phases, int nk, int threads,
+                             cudaStream_t st) {
+  dim3 grid(((a.g.ncells + threads - 1) / threads) * 8, 1, (nk + KB - 1) / KB);
+  if (h->norb == 10) hx_kbatch_kernel<T, 10, KB><<<grid, threads, 0, st>>>(a, phases, nk);
+  else hx_kbatch_kernel<T, 5, KB><<<grid, threads, 0, st>>>(a, phases, nk);
+  return cudaGetLastError();
+}
 
 template <typename T>
 static cudaError_t launch_kbatch_prec(const omen_ham* h, const T* blk, const double2* phases, int nk, const void* x,
@@ -629,16 +689,17 @@ static cudaError_t launch_kbatch_prec(const omen_ham* h, const T* blk, const dou
   for (int d = 0; d < 3; ++d) a.phase[d] = h->phase[d];
   a.ns = h->nspecies;
   a.slot_stride = h->slot_stride;
-  dim3 grid(((a.g.ncells + 127) / 128) * 8, 1, (nk + kKB - 1) / kKB);
-  if (h->norb == 10) hx_kbatch_kernel<T, 10, kKB><<<grid, 128, 0, st>>>(a, phases, nk);
-  else hx_kbatch_kernel<T, 5, kKB><<<grid, 128, 0, st>>>(a, phases, nk);
-  return cudaGetLastError();
+  const HxTile t = h->ktile[sizeof(T) == 8 ? 0 : 1];
+  const int thr = t.threads ? t.threads : 128;
+  if (t.rb == 1) return launch_kb<T, 1>(a, h, phases, nk, thr, st);
+  if constexpr (sizeof(T) == 4) if (t.rb == 4) return launch_kb<T, 4>(a, h, phases, nk, thr, st);
+  return launch_kb<T, kKB>(a, h, phases, nk, thr, st);
 }
 
 omen_status launch_hx_kbatch(omen_ctx* ctx, const omen_ham* h, int nk, const double2* phases_dev, const void* x, void* y,
                              double sigma, int vec_precision) {
   if (h->matrix_free || h->spin_orbit) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch needs stored blocks without spin-orbit");
-  if ((long long)(nk + kKB - 1) / kKB > 65535) return set_err(ctx, OMEN_EINVAL, "too many wave vectors");
+  if ((long long)nk > 65535) return set_err(ctx, OMEN_EINVAL, "too many wave vectors");
   cudaError_t e;
   if (vec_precision == OMEN_F64) {
     if (!h->d_blk64) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP64 blocks");

@@ -13,6 +13,7 @@
 // values) are accumulated and kept in FP64.  OMEN_F32_REFINE64 finishes with FP64
 // Rayleigh–Ritz steps on span{X, H X - X Lambda}.
 #include <algorithm>
+#include <array>
 #include <omp.h>
 
 #include <chrono>
@@ -277,11 +278,11 @@ __global__ void __launch_bounds__(256) dotsn_kernel(const void* Av, long long ld
   const int ni = min(IG, na - i0);
   const long long r0 = (long long)blockIdx.y * rows_per_cta;
   const long long r1 = min(n, r0 + rows_per_cta);
-  Acc sr[IG][NB], si[IG][NB];
+  Acc sr[IG][NB], si[IG][NB], cr[IG][NB], ci[IG][NB];   // c*: Kahan compensation (FP32 only)
 #pragma unroll
   for (int i = 0; i < IG; ++i)
 #pragma unroll
-    for (int j = 0; j < NB; ++j) { sr[i][j] = 0; si[i][j] = 0; }
+    for (int j = 0; j < NB; ++j) { sr[i][j] = 0; si[i][j] = 0; cr[i][j] = 0; ci[i][j] = 0; }
   for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     V bv[NB], av[IG];
 #pragma unroll
@@ -295,11 +296,23 @@ __global__ void __launch_bounds__(256) dotsn_kernel(const void* Av, long long ld
 #pragma unroll
       for (int j = 0; j < NB; ++j)
         if (i < ni && j < nb) {
+          Acc pr, pi = 0;
           if constexpr (C) {
-            sr[i][j] += (Acc)av[i].x * (Acc)bv[j].x + (Acc)av[i].y * (Acc)bv[j].y;
-            si[i][j] += (Acc)av[i].x * (Acc)bv[j].y - (Acc)av[i].y * (Acc)bv[j].x;
+            pr = (Acc)av[i].x * (Acc)bv[j].x + (Acc)av[i].y * (Acc)bv[j].y;
+            pi = (Acc)av[i].x * (Acc)bv[j].y - (Acc)av[i].y * (Acc)bv[j].x;
           } else {
-            sr[i][j] += (Acc)av[i] * (Acc)bv[j];
+            pr = (Acc)av[i] * (Acc)bv[j];
+          }
+          if constexpr (sizeof(T) == 8) {
+            sr[i][j] += pr;
+            si[i][j] += pi;
+          } else {
+            const Acc yr = pr - cr[i][j], tr = sr[i][j] + yr;
+            cr[i][j] = (tr - sr[i][j]) - yr;
+            sr[i][j] = tr;
+            const Acc yi = pi - ci[i][j], ti = si[i][j] + yi;
+            ci[i][j] = (ti - si[i][j]) - yi;
+            si[i][j] = ti;
           }
         }
   }
@@ -309,7 +322,7 @@ __global__ void __launch_bounds__(256) dotsn_kernel(const void* Av, long long ld
   for (int i = 0; i < IG; ++i)
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      double vr = (double)sr[i][j], vi = (double)si[i][j];
+      double vr = (double)sr[i][j] - (double)cr[i][j], vi = (double)si[i][j] - (double)ci[i][j];
       for (int o = 16; o > 0; o >>= 1) {
         vr += __shfl_xor_sync(0xffffffffu, vr, o);
         if constexpr (C) vi += __shfl_xor_sync(0xffffffffu, vi, o);
@@ -327,22 +340,32 @@ __global__ void __launch_bounds__(256) dotsn_kernel(const void* Av, long long ld
   }
 }
 
-// Y_j = beta Y_j + alpha sum_i A_i M[i + j*na] for NB (<= 4) columns at once.
+// Y_j = beta Y_j + alpha sum_i A_i M[i + j*na] for NB (<= 4) columns at once, every basis
+// load serving all NB columns.  Arithmetic in the vectors' precision, as in combine1_kernel
+// (coefficients alpha*M rounded once), so FP32 vectors stay off the FP64 pipe.
 template <typename T, bool C, int NB>
 __global__ void __launch_bounds__(256) combinen_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M,
                                                        int nb, void* Yv, long long ldy, long long n, double alpha, double beta) {
   using E = Elem<T, C>;
   using V = typename E::V;
+  using A2 = std::conditional_t<sizeof(T) == 8, double2, float2>;
+  using R = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* Ms = reinterpret_cast<double2*>(smem_raw);
-  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Ms[t] = M[t];
+  A2* Ms = reinterpret_cast<A2*>(smem_raw);
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
+    A2 m;
+    m.x = (R)(alpha * M[t].x);
+    m.y = (R)(alpha * M[t].y);
+    Ms[t] = m;
+  }
   __syncthreads();
   const V* A = static_cast<const V*>(Av);
   V* Y = static_cast<V*>(Yv);
+  const R rbeta = (R)beta;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-    double yr[NB], yi[NB];
+    R yr[NB], yi[NB];
 #pragma unroll
-    for (int j = 0; j < NB; ++j) { yr[j] = 0.0; yi[j] = 0.0; }
+    for (int j = 0; j < NB; ++j) { yr[j] = 0; yi[j] = 0; }
     int i = 0;
     for (; i + 4 <= na; i += 4) {
       V av[4];
@@ -350,11 +373,11 @@ __global__ void __launch_bounds__(256) combinen_kernel(const void* Av, long long
       for (int k = 0; k < 4; ++k) av[k] = A[(size_t)(i + k) * lda + r];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const double xr = E::re(av[k]), xi = E::im(av[k]);
+        const R xr = E::re(av[k]), xi = E::im(av[k]);
 #pragma unroll
         for (int j = 0; j < NB; ++j)
           if (j < nb) {
-            const double2 m = Ms[i + k + j * na];
+            const A2 m = Ms[i + k + j * na];
             yr[j] = fma(xr, m.x, yr[j]);
             if constexpr (C) {
               yr[j] = fma(-xi, m.y, yr[j]);
@@ -366,11 +389,11 @@ __global__ void __launch_bounds__(256) combinen_kernel(const void* Av, long long
     }
     for (; i < na; ++i) {
       const V a = A[(size_t)i * lda + r];
-      const double xr = E::re(a), xi = E::im(a);
+      const R xr = E::re(a), xi = E::im(a);
 #pragma unroll
       for (int j = 0; j < NB; ++j)
         if (j < nb) {
-          const double2 m = Ms[i + j * na];
+          const A2 m = Ms[i + j * na];
           yr[j] = fma(xr, m.x, yr[j]);
           if constexpr (C) {
             yr[j] = fma(-xi, m.y, yr[j]);
@@ -383,10 +406,10 @@ __global__ void __launch_bounds__(256) combinen_kernel(const void* Av, long long
     for (int j = 0; j < NB; ++j)
       if (j < nb) {
         V& out = Y[(size_t)j * ldy + r];
-        double orr = alpha * yr[j], oi = alpha * yi[j];
+        R orr = yr[j], oi = yi[j];
         if (beta != 0.0) {
-          orr += beta * E::re(out);
-          oi += beta * E::im(out);
+          orr = fma(rbeta, (R)E::re(out), orr);
+          oi = fma(rbeta, (R)E::im(out), oi);
         }
         out = E::make(orr, oi);
       }
@@ -1274,6 +1297,50 @@ static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X,
 // projection coefficients accumulate into a device copy of T and the norm of the new
 // direction is applied from device memory, so a step issues kernels only and the host
 // synchronises once per convergence check (every few steps / at each restart).
+// Executable graphs of step sequences, keyed by what fixes their kernel arguments (first step's
+// basis index, basis size, fresh flag, number of steps).  Captured on the context's private
+// stream, replayed on the caller's stream; destroyed (after the stream drains) with the solve.
+struct SegmentGraphs {
+  omen_ctx* ctx;
+  std::map<std::array<int, 4>, cudaGraphExec_t> cache;
+  explicit SegmentGraphs(omen_ctx* c) : ctx(c) {}
+  ~SegmentGraphs() {
+    if (cache.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : cache) cudaGraphExecDestroy(kv.second);
+  }
+  template <typename F>
+  omen_status run(const std::array<int, 4>& key, F&& enqueue) {
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+      if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        ctx->cap_stream = nullptr;
+        return set_err(ctx, OMEN_ECUDA, "could not create the capture stream");
+      }
+      cudaStream_t user = ctx->stream;
+      ctx->stream = ctx->cap_stream;
+      cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+      omen_status s = (e == cudaSuccess) ? enqueue() : OMEN_ECUDA;
+      cudaGraph_t g = nullptr;
+      if (e == cudaSuccess) e = cudaStreamEndCapture(ctx->cap_stream, &g);
+      ctx->stream = user;
+      if (s != OMEN_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return s != OMEN_OK ? s : set_err(ctx, OMEN_ECUDA, "Lanczos step capture: %s", cudaGetErrorString(e));
+      }
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "Lanczos graph instantiation: %s", cudaGetErrorString(e));
+      it = cache.emplace(key, ex).first;
+    }
+    const cudaError_t e = cudaGraphLaunch(it->second, ctx->stream);
+    if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "Lanczos graph launch: %s", cudaGetErrorString(e));
+    return OMEN_OK;
+  }
+};
+
 static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, void* X, int k_out,
                                         omen_eig_info* info, bool& converged) {
   omen_ctx* ctx = op.ctx;
@@ -1322,41 +1389,75 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   std::vector<cd> Y;
   auto t_start = std::chrono::steady_clock::now();
   bool fresh = true;   // first step of a cycle: the new vector couples to every kept vector
-  while (true) {
-    s = op.apply(op.col(V, jstart), W, tmp, 1, folded, o->sigma, hx);
-    if (s != OMEN_OK) return s;
-    if (fresh) {
+  // One step on the device: W = A v_js, orthogonalise W against v_0..v_{nb-1} (T column js),
+  // v_nb = W / ||W|| (T[nb, js] = ||W||).  No host synchronisation.
+  auto enqueue_step = [&](int js, int nb, bool fr) -> omen_status {
+    long long unused = 0;
+    omen_status s2 = op.apply(op.col(V, js), W, tmp, 1, folded, o->sigma, unused);
+    if (s2 != OMEN_OK) return s2;
+    if (fr) {
       // two full classical Gram–Schmidt passes
-      for (int pass = 0; pass < 2; ++pass) {
-        s = op.dots_dev(V, nbas, W, 1, dh, dT, ldT, jstart);
-        if (s != OMEN_OK) return s;
-        s = op.combine_dev(V, nbas, dh, 1, W, -1.0, 1.0);
-        if (s != OMEN_OK) return s;
+      for (int pass = 0; pass < 2 && s2 == OMEN_OK; ++pass) {
+        s2 = op.dots_dev(V, nb, W, 1, dh, dT, ldT, js);
+        if (s2 == OMEN_OK) s2 = op.combine_dev(V, nb, dh, 1, W, -1.0, 1.0);
       }
-      fresh = false;
     } else {
       // three-term step against v_j (alpha) and v_{j-1} (beta, already in T), then one full
       // pass that removes what rounding left along every basis vector
-      s = op.dots_dev(op.col(V, jstart), 1, W, 1, dh, dT + jstart, ldT, jstart);
-      if (s == OMEN_OK) s = op.combine_dev(op.col(V, jstart), 1, dh, 1, W, -1.0, 1.0);
-      if (s == OMEN_OK)
-        s = op.combine_dev(op.col(V, jstart - 1), 1, dT + jstart + (size_t)(jstart - 1) * ldT, 1, W, -1.0, 1.0);
-      if (s != OMEN_OK) return s;
-      OMEN_CUDA(ctx, cudaMemcpyAsync(dT + (jstart - 1) + (size_t)jstart * ldT, dT + jstart + (size_t)(jstart - 1) * ldT,
+      s2 = op.dots_dev(op.col(V, js), 1, W, 1, dh, dT + js, ldT, js);
+      if (s2 == OMEN_OK) s2 = op.combine_dev(op.col(V, js), 1, dh, 1, W, -1.0, 1.0);
+      if (s2 == OMEN_OK) s2 = op.combine_dev(op.col(V, js - 1), 1, dT + js + (size_t)(js - 1) * ldT, 1, W, -1.0, 1.0);
+      if (s2 != OMEN_OK) return s2;
+      OMEN_CUDA(ctx, cudaMemcpyAsync(dT + (js - 1) + (size_t)js * ldT, dT + js + (size_t)(js - 1) * ldT,
                                      sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
-      s = op.dots_dev(V, nbas, W, 1, dh, dT, ldT, jstart);
-      if (s == OMEN_OK) s = op.combine_dev(V, nbas, dh, 1, W, -1.0, 1.0);
-      if (s != OMEN_OK) return s;
+      s2 = op.dots_dev(V, nb, W, 1, dh, dT, ldT, js);
+      if (s2 == OMEN_OK) s2 = op.combine_dev(V, nb, dh, 1, W, -1.0, 1.0);
     }
-    s = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
+    if (s2 == OMEN_OK) s2 = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
+    if (s2 == OMEN_OK) s2 = op.normalize_dev(W, op.col(V, nb), dn, dT, ldT, nb, js);
+    return s2;
+  };
+  // a host check follows the step that leaves nb basis vectors when this holds
+  auto check_after = [&](int nb, int it, int since) {
+    const bool full_ = nb + 1 > m;
+    return (full_ || it >= max_iter_of(o) || (since >= check_every && nb >= o->nev + 1)) && nb >= o->nev;
+  };
+  SegmentGraphs graphs(ctx);
+  const bool use_graphs = ctx->use_graphs && !op.negate;
+  if (use_graphs) {
+    // the partial-sum buffer must not move under a captured graph: size it for the widest pass
+    int rows = 8192;
+    while ((op.n + rows - 1) / rows > 65535) rows *= 2;
+    s = op.ensure_partial((size_t)((op.n + rows - 1) / rows) * (m + 1));
     if (s != OMEN_OK) return s;
-    s = op.normalize_dev(W, op.col(V, nbas), dn, dT, ldT, nbas, jstart);
+  }
+  while (true) {
+    // the steps up to and including the next host check run as one segment
+    int nseg = 0;
+    for (int nb = nbas, it = iter, sc = since_check;; ++nb) {
+      ++nseg;
+      if (check_after(nb, ++it, ++sc)) break;
+    }
+    auto run_segment = [&]() -> omen_status {
+      int js = jstart, nb = nbas;
+      bool fr = fresh;
+      for (int i = 0; i < nseg; ++i, fr = false, js = nb, ++nb) {
+        omen_status s2 = enqueue_step(js, nb, fr);
+        if (s2 != OMEN_OK) return s2;
+      }
+      return OMEN_OK;
+    };
+    if (use_graphs && nseg >= 2) s = graphs.run({jstart, nbas, fresh ? 1 : 0, nseg}, run_segment);
+    else s = run_segment();
     if (s != OMEN_OK) return s;
-    ++iter;
-    ++since_check;
+    hx += (long long)nseg * (folded ? 2 : 1);
+    iter += nseg;
+    since_check += nseg;
+    nbas += nseg - 1;
+    jstart = nbas - 1;
+    fresh = false;
     const bool full = nbas + 1 > m;
-    const bool check = full || iter >= max_iter_of(o) || (since_check >= check_every && nbas >= o->nev + 1);
-    if (check && nbas >= o->nev) {
+    {
       since_check = 0;
       OMEN_CUDA(ctx, cudaMemcpyAsync(Th.data(), dT, sizeof(double2) * ldT * ldT, cudaMemcpyDeviceToHost, ctx->stream));
       int flag = 0;
@@ -1783,10 +1884,27 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
   std::vector<char> conv(P, 0);
   int jstart = 0, nbas = 1, iter = 0, restarts = 0, since = 0;
   const int check_every = std::max(8, m / 2);
+  bool fresh = true;   // first step of a cycle: the new vector couples to every kept vector
   while (true) {
     s = apply(slot(jstart), Wb.p);
-    for (int pass = 0; pass < 2 && s == OMEN_OK; ++pass) {
-      s = op.dots_dev_batch(P, V, lda, nbas, Wb.p, dh, ldT, dT, ldT, tps, jstart);
+    if (fresh) {
+      // two full classical Gram–Schmidt passes
+      for (int pass = 0; pass < 2 && s == OMEN_OK; ++pass) {
+        s = op.dots_dev_batch(P, V, lda, nbas, Wb.p, dh, ldT, dT, ldT, tps, jstart);
+        if (s == OMEN_OK) s = op.combine_dev_batch(P, V, lda, nbas, dh, ldT, Wb.p, -1.0, 1.0);
+      }
+      fresh = false;
+    } else if (s == OMEN_OK) {
+      // three-term step (alpha against v_j, beta against v_{j-1} from T), then one full pass
+      s = op.dots_dev_batch(P, slot(jstart), lda, 1, Wb.p, dh, ldT, dT + jstart, ldT, tps, jstart);
+      if (s == OMEN_OK) s = op.combine_dev_batch(P, slot(jstart), lda, 1, dh, ldT, Wb.p, -1.0, 1.0);
+      if (s == OMEN_OK)
+        s = op.combine_dev_batch(P, slot(jstart - 1), lda, 1, dT + jstart + (size_t)(jstart - 1) * ldT, tps, Wb.p, -1.0, 1.0);
+      if (s == OMEN_OK)
+        OMEN_CUDA(ctx, cudaMemcpy2DAsync(dT + (jstart - 1) + (size_t)jstart * ldT, tps * sizeof(double2),
+                                         dT + jstart + (size_t)(jstart - 1) * ldT, tps * sizeof(double2), sizeof(double2), P,
+                                         cudaMemcpyDeviceToDevice, ctx->stream));
+      if (s == OMEN_OK) s = op.dots_dev_batch(P, V, lda, nbas, Wb.p, dh, ldT, dT, ldT, tps, jstart);
       if (s == OMEN_OK) s = op.combine_dev_batch(P, V, lda, nbas, dh, ldT, Wb.p, -1.0, 1.0);
     }
     if (s == OMEN_OK) s = op.dots_dev_batch(P, Wb.p, n, 1, Wb.p, dn, 1, nullptr, 0, 0, 0);
@@ -1882,6 +2000,7 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
       jstart = kk;
       nbas = kk + 1;
       ++restarts;
+      fresh = true;
       continue;
     }
     jstart = nbas;

@@ -17,6 +17,9 @@ struct omen_ctx {
   double* d_work = nullptr;
   size_t work_bytes = 0;
   int* d_status = nullptr;
+  // Lanczos step sequences between host checks are captured once as CUDA graphs and replayed
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;   // private stream the captures are recorded on
 };
 
 struct omen_lattice {
@@ -26,6 +29,12 @@ struct omen_lattice {
   uint8_t* d_species = nullptr;  // [natoms]
   double* d_strain = nullptr;    // [16*ncells]
   long long nbonds = 0;
+};
+
+// Launch shape of an H·X kernel: CTA width and rows per register batch (k batch: wave vectors
+// per thread); zeros select the built-in defaults.
+struct HxTile {
+  int threads = 0, rb = 0;
 };
 
 // Per-species-pair bond blocks for the four ideal directions, at d0 (device, row-major).
@@ -53,6 +62,8 @@ struct omen_ham {
   double* d_U = nullptr;                  // [natoms]
   double lambda_so[4] = {0, 0, 0, 0};
   double* d_lambda = nullptr;             // [ns]
+  HxTile tile[2];                         // H·X launch shape for FP64 [0] and FP32 [1] vectors
+  HxTile ktile[2];                        // the same for the k-batched product
 };
 
 // status / error helpers ---------------------------------------------------------------------

@@ -68,6 +68,14 @@ class CGOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("threads", C.c_int), ("rows_per_batch", C.c_int), ("candidates", C.c_int),
+                ("ms_best", C.c_double), ("ms_default", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double), ("seconds", C.c_double)]
 
@@ -113,6 +121,11 @@ def lib():
             "omen_create": (i, [C.POINTER(vp), i, vp]),
             "omen_destroy": (None, [vp]),
             "omen_last_error": (C.c_char_p, [vp]),
+            "omen_set_graph_capture": (i, [vp, i]),
+            "omen_tune_hx": (i, [vp, vp, i, i, i, C.POINTER(TuneResult)]),
+            "omen_tune_hx_kbatch": (i, [vp, vp, i, i, C.POINTER(TuneResult)]),
+            "omen_hx_set_tile": (i, [vp, vp, i, i, i]),
+            "omen_hx_kbatch_set_tile": (i, [vp, vp, i, i, i]),
             "omen_build_lattice": (i, [vp, C.POINTER(LatticeDesc), C.POINTER(vp)]),
             "omen_free_lattice": (None, [vp]),
             "omen_lattice_counts": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
@@ -196,6 +209,10 @@ def omen_create(device=0, stream=None) -> Context:
     if s != OMEN_OK:
         raise OmenError(s, "omen_create failed (no CUDA device?)")
     return Context(h)
+
+
+def omen_set_graph_capture(ctx: Context, enable: bool) -> None:
+    ctx.check(lib().omen_set_graph_capture(ctx.handle, int(bool(enable))))
 
 
 class Lattice:
@@ -366,6 +383,29 @@ def omen_scf(ctx: Context, lat: Lattice, params, grid, phi_dev, donor_rho_dev, n
     if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
         ctx.check(s)
     return info.as_dict(), s
+
+
+def omen_tune_hx(ctx: Context, ham: Hamiltonian, vec_precision=None, nvec=1, reps=10) -> dict:
+    """Time the compiled launch shapes of the product on this Hamiltonian; keep the fastest."""
+    if vec_precision is None:
+        vec_precision = OMEN_F32 if ham.elem_bytes == (8 if ham.is_complex else 4) else OMEN_F64
+    r = TuneResult()
+    ctx.check(lib().omen_tune_hx(ctx.handle, ham.handle, int(vec_precision), int(nvec), int(reps), C.byref(r)))
+    return r.as_dict()
+
+
+def omen_tune_hx_kbatch(ctx: Context, ham: Hamiltonian, nk, reps=10) -> dict:
+    r = TuneResult()
+    ctx.check(lib().omen_tune_hx_kbatch(ctx.handle, ham.handle, int(nk), int(reps), C.byref(r)))
+    return r.as_dict()
+
+
+def omen_hx_set_tile(ctx: Context, ham: Hamiltonian, vec_precision, threads, rows_per_batch) -> None:
+    ctx.check(lib().omen_hx_set_tile(ctx.handle, ham.handle, int(vec_precision), int(threads), int(rows_per_batch)))
+
+
+def omen_hx_kbatch_set_tile(ctx: Context, ham: Hamiltonian, vec_precision, threads, k_per_thread) -> None:
+    ctx.check(lib().omen_hx_kbatch_set_tile(ctx.handle, ham.handle, int(vec_precision), int(threads), int(k_per_thread)))
 
 
 def omen_hx_kbatch(ctx: Context, ham: Hamiltonian, kpts, x_dev, y_dev, sigma=0.0):

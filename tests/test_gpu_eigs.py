@@ -102,3 +102,31 @@ def test_non_finite_input_returns_enumeric(ctx):
     ham2 = omen.omen_assemble_H(ctx, lat, p)
     ev, info, st = omen.omen_eigs(ctx, ham2, 2, tol=1e-9, block=8, basis=48, max_iter=500)
     assert st == omen.OMEN_OK
+
+
+@pytest.mark.parametrize("which", ["lowest", "nearest"])
+def test_graph_replay_matches_direct_launches(ctx, which):
+    """Replayed step graphs run the same kernels in the same order: identical results."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(2, 2, 3, (0, 0, 0), seed=45, alloy_fraction=0.3, strain_amp=0.02)
+    p = synth.draw_tb_params(45, 10, 2)
+    H = hamiltonian.assemble(spec, p)
+    w = np.linalg.eigvalsh(H.toarray())
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p)
+    kw = dict(tol=1e-9, block=1, basis=32, max_iter=20000)
+    if which == "nearest":
+        sigma = round(0.5 * (w[0] + w[-1]), 3)
+        kw.update(which=omen.OMEN_NEAREST, sigma=sigma)
+        ref = eigs.nearest(w, sigma, 6)
+    else:
+        ref = w[:6]
+    out = []
+    for enable in (False, True, True):
+        omen.omen_set_graph_capture(ctx, enable)
+        out.append(omen.omen_eigs(ctx, ham, 6, **kw))
+    omen.omen_set_graph_capture(ctx, True)
+    (ev0, i0, _), (ev1, i1, _), (ev2, _, _) = out
+    assert i0["restarts"] >= 2 and i0["iterations"] == i1["iterations"]
+    assert np.array_equal(ev0, ev1) and np.array_equal(ev1, ev2)
+    np.testing.assert_allclose(ev1, ref, atol=1e-9, rtol=0)

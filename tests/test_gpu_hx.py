@@ -124,3 +124,97 @@ def test_double_float_hx_matches_oracle(ctx):
     with pytest.raises(omen.OmenError) as e:
         omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F64_DF, spin_orbit=True)
     assert e.value.status == omen.OMEN_EUNSUPPORTED
+
+
+TILE_CASES = [
+    # (dims, periodic, basis, so, k, precision, matrix_free)
+    ((5, 4, 7), (0, 0, 0), 10, False, None, 1, False),
+    ((5, 4, 7), (0, 1, 0), 10, False, None, 0, False),
+    ((3, 5, 9), (0, 1, 0), 10, True, None, 1, False),
+    ((4, 3, 11), (1, 1, 0), 5, False, None, 1, False),
+    ((4, 3, 11), (2, 2, 0), 10, False, (0.31, -0.52, 0.0), 1, True),
+]
+
+
+@pytest.mark.parametrize("case", TILE_CASES, ids=[f"t{i}" for i in range(len(TILE_CASES))])
+def test_every_launch_shape_gives_the_same_product(ctx, case):
+    """Each compiled (CTA width, rows per register batch) gives the default shape's result bit
+    for bit (same summation order per accumulator), and that result matches the oracle."""
+    from paper_1003_4570_gb300 import omen
+    dims, per, basis, so, k, prec, mf = case
+    spec = synth.lattice_spec(*dims, per, seed=35, alloy_fraction=0.3, strain_amp=0.02)
+    p = synth.draw_tb_params(35, basis, 2)
+    H = hamiltonian.assemble(spec, p, kvec=k, spin_orbit=so)
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, spin_orbit=so, precision=prec, matrix_free=mf, k=k)
+    x = synth.random_vectors(7, H.shape[0], 2, dtype=complex if ham.is_complex else float)
+    xd = torch.from_numpy(x.astype(ham.numpy_dtype)).cuda()
+
+    def product():
+        yd = torch.empty_like(xd)
+        omen.omen_hx(ctx, ham, xd, yd, nvec=2, sigma=0.2)
+        torch.cuda.synchronize()
+        return yd.cpu().numpy()
+
+    base = product()
+    for v in range(2):
+        xv = x[v].astype(ham.numpy_dtype).astype(complex if ham.is_complex else float)
+        ref = H @ xv - 0.2 * xv
+        tol = 1e-12 if prec == 0 else 2e-6
+        np.testing.assert_allclose(base[v], ref, atol=tol * np.abs(ref).max(), rtol=0)
+    shapes = 0
+    for thr in (32, 64, 96, 128, 256):
+        for rb in (0, 1, 2, 5, 10):
+            try:
+                omen.omen_hx_set_tile(ctx, ham, prec, thr, rb)
+            except omen.OmenError as e:
+                assert e.status == omen.OMEN_EINVAL
+                continue
+            shapes += 1
+            assert np.array_equal(product(), base), (thr, rb)
+    assert shapes >= 4
+    for bad in ((48, 0), (256, 0), (128, 3), (128, 7)):
+        with pytest.raises(omen.OmenError) as e:
+            omen.omen_hx_set_tile(ctx, ham, prec, *bad)
+        assert e.value.status == omen.OMEN_EINVAL
+    r = omen.omen_tune_hx(ctx, ham, prec, nvec=2, reps=3)
+    assert r["candidates"] >= shapes // 2 and r["ms_best"] <= r["ms_default"] + 1e-9
+    assert np.array_equal(product(), base)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_kbatch_launch_shape_gives_the_same_product(ctx, prec):
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(3, 2, 9, (2, 2, 0), seed=36, alloy_fraction=0.3, strain_amp=0.02)
+    p = synth.draw_tb_params(36, 10, 2)
+    lat = omen.omen_build_lattice(ctx, spec)
+    kpts = np.array([[0.1 * q, -0.05 * q, 0.0] for q in range(7)])
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, k=(0.0, 0.0, 0.0))
+    n = ham.nrows
+    x = synth.random_vectors(8, n, len(kpts), dtype=complex)
+    xd = torch.from_numpy(x.astype(ham.numpy_dtype)).cuda()
+
+    def product():
+        yd = torch.empty_like(xd)
+        omen.omen_hx_kbatch(ctx, ham, kpts, xd, yd, sigma=0.1)
+        torch.cuda.synchronize()
+        return yd.cpu().numpy()
+
+    base = product()
+    for q in (0, 6):
+        H = hamiltonian.assemble(spec, p, kvec=kpts[q])
+        xv = x[q].astype(ham.numpy_dtype).astype(complex)
+        ref = H @ xv - 0.1 * xv
+        tol = 1e-12 if prec == 0 else 2e-6
+        np.testing.assert_allclose(base[q], ref, atol=tol * np.abs(ref).max(), rtol=0)
+    for thr in (32, 64, 128):
+        for kb in (1, 2, 4):
+            if prec == 0 and kb == 4:
+                with pytest.raises(omen.OmenError):
+                    omen.omen_hx_kbatch_set_tile(ctx, ham, prec, thr, kb)
+                continue
+            omen.omen_hx_kbatch_set_tile(ctx, ham, prec, thr, kb)
+            assert np.array_equal(product(), base), (thr, kb)
+    r = omen.omen_tune_hx_kbatch(ctx, ham, len(kpts), reps=3)
+    assert r["ms_best"] <= r["ms_default"] + 1e-9
+    assert np.array_equal(product(), base)
