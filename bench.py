@@ -36,6 +36,11 @@ SAMPLE_NZ = 4          # CPU sample: 50 x 50 x 4 cells of the same recipe
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure is in the measured-peaks file)
 
 
+# DRAM bytes per FP64 H·X launch on the 1M-atom alloy, by launch shape (CTA width, block rows
+# per register batch), from the ncu launch lists summarised in profiles/hx_kernel_sige_alloy.md
+HX_F64_TRAFFIC = {(128, 1): 2.552e9}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -174,32 +179,47 @@ def measure_variants(ctx, omen, lat, p, natoms, nbonds, reps=50):
         vel = el * (2 if so else 1)
         x = torch.zeros(ham.nrows * vel // 4, dtype=torch.float32, device="cuda")
         y = torch.empty_like(x)
-        for _ in range(3):
-            omen.omen_hx(ctx, ham, x, y)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            omen.omen_hx(ctx, ham, x, y)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+
+        def timed():
+            for _ in range(3):
+                omen.omen_hx(ctx, ham, x, y)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                omen.omen_hx(ctx, ham, x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        ms = timed()
         alg = alg_bytes_per_hx(nbonds, natoms, ham.nrows, el, vel, mf)
         out[name] = {"ms": ms, "alg_GB": alg / 1e9, "GB_per_s": alg / ms / 1e6}
+        if prec != omen.OMEN_F64_DF:
+            tile = omen.omen_tune_hx(ctx, ham, prec, nvec=1, reps=5)
+            mst = timed()
+            out[name].update({"tuned_shape": [tile["threads"], tile["rows_per_batch"]], "tuned_ms": mst,
+                              "tuned_GB_per_s": alg / mst / 1e6})
         del ham, x, y
     return out
 
 
 def measure_lanczos(ctx, omen, ham, iters=500, basis=64):
-    """The paper's benchmark unit (Section II-B): wall time of 500 Lanczos iterations."""
+    """The paper's benchmark unit (Section II-B): wall time of 500 Lanczos iterations, with the
+    default full Gram–Schmidt update at every step and with the semi-orthogonal policy."""
     import torch
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ev, info, st = omen.omen_eigs(ctx, ham, 16, omen.OMEN_LOWEST, tol=1e-30, block=1, basis=basis,
-                                  max_iter=iters, raise_on_noconv=False)
-    torch.cuda.synchronize()
-    return {"iterations": info["iterations"], "seconds": time.perf_counter() - t0, "basis": basis,
-            "hx_count": info["hx_count"]}
+    out = {}
+    for name, pol in (("full_update", omen.OMEN_REORTH_FULL), ("semi_orthogonal", omen.OMEN_REORTH_SEMI)):
+        omen.omen_set_reorthogonalization(ctx, pol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, info, st = omen.omen_eigs(ctx, ham, 16, omen.OMEN_LOWEST, tol=1e-30, block=1, basis=basis,
+                                      max_iter=iters, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        out[name] = {"iterations": info["iterations"], "seconds": time.perf_counter() - t0, "basis": basis,
+                     "hx_count": info["hx_count"], "lowest": float(ev[0])}
+    omen.omen_set_reorthogonalization(ctx, omen.OMEN_REORTH_FULL)
+    return out
 
 
 def measure_eigs_1m(ctx, omen, lat, p, nev=16):
@@ -335,7 +355,7 @@ def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
     eg = synth.GAPPED_SI_EC - synth.GAPPED_SI_EV
     common = dict(kT=8.617333262e-5 * 4, kpts=[(0.0, 0.0, 0.0)], kweights=[1.0], nev=8,
                   sigma=synth.GAPPED_SI_EC - 0.4 * eg, e_cut=0.5 * (synth.GAPPED_SI_EC + synth.GAPPED_SI_EV),
-                  eig_tol=1e-10, eig_block=4, eig_basis=48, mix=0.3, mix_history=6, tol_V=1e-6, max_iter=200)
+                  eig_tol=1e-10, eig_block=1, eig_basis=48, mix=0.3, mix_history=6, tol_V=1e-6, max_iter=200)
 
     def solve(seed, phi):
         ns, w = synth.draw_doping(seed)
@@ -385,11 +405,11 @@ def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
 
 def measure_kbatch_full(ctx, omen, nk=128, nev=8, seed=4, per_k_sample=4):
     """The k-batching workload: instances of drawn lateral sizes x 80 cells, each with its donor
-    sheet, nk wave vectors along Gamma-X, nev lowest bands per k, lockstep per instance against one
-    solve per k (per-k time extrapolated from per_k_sample wave vectors per instance)."""
+    sheet, nk wave vectors along Gamma-X, nev lowest bands per k.  Three ways: every (instance, k)
+    in one lockstep solve (one H·X launch per step over the whole work list); one lockstep solve
+    per instance; one solve per k (time extrapolated from per_k_sample wave vectors per instance)."""
     import torch
-    out = []
-    tot_b, tot_p, bands = 0.0, 0.0, 0
+    insts = []
     for idx, (nxy, nz, lam) in enumerate(synth.draw_kbatch_instances(seed)):
         spec = synth.lattice_spec(nxy, nxy, nz, (2, 2, 0), seed=seed + idx)
         U = synth.donor_sheet_potential(spec, seed + idx, lam)
@@ -398,6 +418,20 @@ def measure_kbatch_full(ctx, omen, nk=128, nev=8, seed=4, per_k_sample=4):
                                    U_atom_dev=torch.from_numpy(U).cuda())
         ks = np.zeros((nk, 3))
         ks[:, 0] = np.linspace(0.0, 1.0, nk) * np.pi / (nxy * spec.a_nm)
+        insts.append(dict(nxy=nxy, spec=spec, lam=lam, lat=lat, ham=ham, ks=ks))
+    bands = nk * nev * len(insts)
+    # all instances in one lockstep solve
+    tile_m = omen.omen_tune_hx_kbatch(ctx, insts[0]["ham"], nk, reps=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    evm, infom, _ = omen.omen_eigs_kbatch_multi(ctx, [(d["ham"], d["ks"]) for d in insts], nev, tol=1e-6,
+                                                max_iter=20000, basis=48, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    tm = time.perf_counter() - t0
+    out = []
+    tot_b, tot_p = 0.0, 0.0
+    for d, ev_multi in zip(insts, evm):
+        ham, ks = d["ham"], d["ks"]
         tile_b = omen.omen_tune_hx_kbatch(ctx, ham, nk, reps=5)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -410,16 +444,19 @@ def measure_kbatch_full(ctx, omen, nk=128, nev=8, seed=4, per_k_sample=4):
             omen.omen_eigs_kbatch(ctx, ham, ks[q:q + 1], nev, tol=1e-6, max_iter=20000, basis=48, raise_on_noconv=False)
         torch.cuda.synchronize()
         tp = (time.perf_counter() - t0) / per_k_sample * nk
-        out.append({"lateral": nxy, "atoms": spec.natoms, "lambda_TF_nm": lam, "batched_s": tb, "per_k_s": tp,
-                    "converged": info["converged"], "max_residual": info["max_residual"],
+        out.append({"lateral": d["nxy"], "atoms": d["spec"].natoms, "lambda_TF_nm": d["lam"], "batched_s": tb,
+                    "per_k_s": tp, "converged": info["converged"], "max_residual": info["max_residual"],
+                    "max_diff_multi_vs_batched_eV": float(np.abs(ev_multi - ev).max()),
                     "tile_batched": [tile_b["threads"], tile_b["rows_per_batch"]],
                     "tile_per_k": [tile_p["threads"], tile_p["rows_per_batch"]]})
         tot_b += tb
         tot_p += tp
-        bands += nk * nev
-        del ham, lat
-    return {"instances": out, "bands": bands, "bands_per_s_batched": bands / tot_b,
-            "bands_per_s_per_k": bands / tot_p, "speedup": tot_p / tot_b,
+    return {"instances": out, "bands": bands,
+            "all_instances_one_solve": {"seconds": tm, "bands_per_s": bands / tm, "iterations": infom["iterations"],
+                                        "converged": infom["converged"], "max_residual": infom["max_residual"],
+                                        "tile": [tile_m["threads"], tile_m["rows_per_batch"]]},
+            "bands_per_s_batched": bands / tot_b, "bands_per_s_per_k": bands / tot_p,
+            "speedup_per_instance_batch": tot_p / tot_b, "speedup_one_solve": tot_p / tm,
             "per_k_time": f"extrapolated from {per_k_sample} wave vectors per instance"}
 
 
@@ -453,7 +490,14 @@ def run_gpu(args, rank, world, local_rank):
     sigma = 0.3
     # launch shape of the product: timed on this Hamiltonian by the library's tuner (identical
     # results for every shape); the double-float kernel has one shape
-    tile = None if prec == omen.OMEN_F64_DF else omen.omen_tune_hx(ctx, ham, prec, nvec=1, reps=5)
+    if prec == omen.OMEN_F64_DF:
+        tile = None
+    elif args.tile:
+        thr, rb = (int(v) for v in args.tile.split(","))
+        omen.omen_hx_set_tile(ctx, ham, prec, thr, rb)
+        tile = {"threads": thr or 128, "rows_per_batch": rb, "candidates": 0, "source": "--tile"}
+    else:
+        tile = omen.omen_tune_hx(ctx, ham, prec, nvec=1, reps=5)
 
     def step():
         omen.omen_hx(ctx, ham, x, t, 1, sigma)
@@ -508,8 +552,8 @@ def run_gpu(args, rank, world, local_rank):
         achieved_tf = fl / (launch_ms / 1e3) / 1e12
         # DRAM bytes per launch of this kernel at this workload, from the ncu launch list in
         # profiles/hx_kernel_sige_alloy.md (null for other workloads)
-        default_shape = tile is not None and tile["threads"] == 128 and tile["rows_per_batch"] in (0, 1)
-        traffic = 2.552e9 if (args.cells == N_CELLS and not args.matrix_free and default_shape) else None
+        shape = (tile["threads"], tile["rows_per_batch"] or 1) if tile else None
+        traffic = HX_F64_TRAFFIC.get(shape) if (args.cells == N_CELLS and not args.matrix_free) else None
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "hx_kernel<double,10,real,stored>", "hbm_achieved_gbs": achieved_gbs,
@@ -572,6 +616,10 @@ def main():
                     "smaller only for profiling captures)")
     ap.add_argument("--kbatch-full", action="store_true",
                     help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
+    ap.add_argument("--only", default="", choices=["", "kbatch", "scf", "small-si", "cube"],
+                    help="profiling aid: run one side measurement alone and print its JSON")
+    ap.add_argument("--tile", default="", metavar="THREADS,RB",
+                    help="fix the H·X launch shape instead of tuning it (e.g. 64,2; profiling aid)")
     ap.add_argument("--lanczos-only", type=int, default=0, metavar="ITERS",
                     help="profiling aid: run only ITERS Lanczos iterations (FP64, basis 64) and print their time")
     args = ap.parse_args()
@@ -586,6 +634,14 @@ def main():
         from paper_1003_4570_gb300 import omen
         ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
         print(json.dumps({"kbatch_full": measure_kbatch_full(ctx, omen)}))
+        return
+    if args.only:
+        import torch
+        from paper_1003_4570_gb300 import omen
+        ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+        fn = {"kbatch": measure_kbatch, "scf": measure_scf, "small-si": measure_small_si,
+              "cube": measure_cube_500}[args.only]
+        print(json.dumps({args.only: fn(ctx, omen)}))
         return
     if args.lanczos_only:
         import torch

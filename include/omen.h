@@ -85,6 +85,18 @@ const char* omen_last_error(const omen_ctx* ctx);
  * no counterpart: launch overhead was not a cost on its CPUs.  EINVAL for a null context. */
 omen_status omen_set_graph_capture(omen_ctx* ctx, int enable);
 
+/* Orthogonalisation of the single-vector Lanczos steps.  Every step removes the new vector's
+ * components along v_j and v_{j-1} (three-term recurrence) and measures its overlaps h with the
+ * whole basis (a projection pass).  OMEN_REORTH_FULL (default) subtracts V h at every step.
+ * OMEN_REORTH_SEMI subtracts it only when some |h_i| exceeds sqrt(u) ||w|| (u the vectors' unit
+ * roundoff) or the previous step did so, which keeps the basis semi-orthogonal — enough for
+ * Ritz values of working accuracy (Simon, Math. Comp. 42 (1984) 115; the paper's Lanczos
+ * solver, Section III-A item 1, does not say how it orthogonalises).  It saves the update only
+ * while no Ritz pair has converged; it costs one extra norm per step.  The first step after a
+ * start or restart always takes two full passes.  EINVAL for another value. */
+enum { OMEN_REORTH_FULL = 0, OMEN_REORTH_SEMI = 1 };
+omen_status omen_set_reorthogonalization(omen_ctx* ctx, int policy);
+
 /* ---- structure (paper Section II-A: atoms of the domain and their neighbours) ---------- */
 
 typedef struct {
@@ -233,6 +245,22 @@ omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_eig_opts* o
 omen_status omen_hx_kbatch(omen_ctx* ctx, const omen_ham* ham, int nk, const double* k_host,
                            const void* x_dev, void* y_dev, double sigma);
 
+/* Several structures in one k batch (paper Section III-A item 1: eigenstates on finite
+ * k-points; structures of different sizes batched together).  Item i: a Bloch Hamiltonian with
+ * stored blocks and no spin-orbit, all items of one precision and basis, and its nk wave
+ * vectors k_host [nk][3] (1/nm).  At most 16 items. */
+typedef struct {
+  const omen_ham* ham;
+  int nk;
+  const double* k_host;
+} omen_kbatch_item;
+
+/* y = (H_i(k) - sigma) x for every wave vector of every item in ONE launch over the
+ * (structure, k) work list.  x_dev, y_dev: the items' [nk_i][nrows_i] complex blocks stored one
+ * after another in item order.  Launch shape from the first item (omen_hx_kbatch_set_tile). */
+omen_status omen_hx_kbatch_multi(omen_ctx* ctx, int nitems, const omen_kbatch_item* items,
+                                 const void* x_dev, void* y_dev, double sigma);
+
 /* nev eigenpairs for each of nk wave vectors, all solved in lockstep (single-vector thick-
  * restart Lanczos, one k-batched H·X launch per step).  opts as for omen_eigs with block = 1
  * and which LOWEST or NEAREST; for NEAREST, tol bounds the H residual estimated from the
@@ -241,6 +269,15 @@ omen_status omen_hx_kbatch(omen_ctx* ctx, const omen_ham* ham, int nk, const dou
 omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int nk, const double* k_host,
                              const omen_eig_opts* opts, double* evals_host, void* evecs_dev,
                              omen_eig_info* info);
+
+/* The same over several structures: every (structure, wave vector) pair is its own problem,
+ * all in lockstep, one H·X launch per step for all of them.  opts.basis + 1 must not exceed
+ * the smallest structure's rows.  evals_host [sum nk_i][nev] in item order, then k order;
+ * evecs_dev (or NULL): per problem nev vectors of that structure's rows, problems one after
+ * another in the same order. */
+omen_status omen_eigs_kbatch_multi(omen_ctx* ctx, int nitems, const omen_kbatch_item* items,
+                                   const omen_eig_opts* opts, double* evals_host, void* evecs_dev,
+                                   omen_eig_info* info);
 
 /* ---- charge, Poisson, self-consistency (paper Section III-A items 2-3) ------------------- */
 

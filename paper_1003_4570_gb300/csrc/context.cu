@@ -30,7 +30,16 @@ extern "C" void omen_destroy(omen_ctx* c) {
   cudaFree(c->d_work);
   cudaFree(c->d_status);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaStream_t st : c->copy_stream)
+    if (st) cudaStreamDestroy(st);
   delete c;
+}
+
+extern "C" omen_status omen_set_reorthogonalization(omen_ctx* c, int policy) {
+  if (!c) return OMEN_EINVAL;
+  if (policy != OMEN_REORTH_FULL && policy != OMEN_REORTH_SEMI) return set_err(c, OMEN_EINVAL, "unknown policy %d", policy);
+  c->reorth = policy;
+  return OMEN_OK;
 }
 
 extern "C" omen_status omen_set_graph_capture(omen_ctx* c, int enable) {

@@ -47,6 +47,7 @@ struct HxArgs {
   double2 phase[3];
   int ns;
   int slot_stride;
+  int cell0, cell1;                   // cells [cell0, cell1) of this launch (a z-range of planes)
 };
 
 template <typename T>
@@ -74,8 +75,8 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
   // site fastest in the block order: CTAs in flight cover all 8 sites of a window of cells,
   // so the transposed (B-end) read of a bond block follows its A-end read within L2 reach
   const int b = blockIdx.x & 7;
-  const int cell = (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
-  if (cell >= g.ncells) return;
+  const int cell = a.cell0 + (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
+  if (cell >= a.cell1) return;
   const int N = g.natoms;
   const int atom = b * g.ncells + cell;
   const int ix = cell % g.nx, iy = (cell / g.nx) % g.ny, iz = cell / (g.nx * g.ny);
@@ -281,14 +282,15 @@ struct HxDfArgs {
   long long nrows;
   double sigma;
   int slot_stride;
+  int cell0, cell1;                    // cells [cell0, cell1) of this launch
 };
 
 template <int NORB>
 __global__ void __launch_bounds__(128) hx_df_kernel(HxDfArgs a) {
   const Geo& g = a.g;
   const int b = blockIdx.x & 7;
-  const int cell = (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
-  if (cell >= g.ncells) return;
+  const int cell = a.cell0 + (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
+  if (cell >= a.cell1) return;
   const int N = g.natoms;
   const int atom = b * g.ncells + cell;
   const int ix = cell % g.nx, iy = (cell / g.nx) % g.ny, iz = cell / (g.nx * g.ny);
@@ -358,7 +360,8 @@ __global__ void df_to_f64_kernel(const float2* __restrict__ src, double* __restr
     dst[i] = (double)src[i].x + (double)src[i].y;
 }
 
-static cudaError_t launch_df(const omen_ham* h, const void* x, void* y, int nvec, double sigma, cudaStream_t st) {
+static cudaError_t launch_df(const omen_ham* h, const void* x, void* y, int nvec, double sigma, cudaStream_t st,
+                             int cell0, int cell1) {
   const omen_lattice* L = h->lat;
   HxDfArgs a;
   a.g = Geo{L->nx, L->ny, L->nz, L->ncells, L->natoms, {L->periodic[0], L->periodic[1], L->periodic[2]}};
@@ -372,7 +375,9 @@ static cudaError_t launch_df(const omen_ham* h, const void* x, void* y, int nvec
   a.nrows = h->nrows;
   a.sigma = sigma;
   a.slot_stride = h->slot_stride;
-  dim3 grid(((a.g.ncells + 127) / 128) * 8, 1, nvec);
+  a.cell0 = cell0;
+  a.cell1 = cell1;
+  dim3 grid(((cell1 - cell0 + 127) / 128) * 8, 1, nvec);
   if (h->norb == 10) hx_df_kernel<10><<<grid, 128, 0, st>>>(a);
   else hx_df_kernel<5><<<grid, 128, 0, st>>>(a);
   return cudaGetLastError();
@@ -392,28 +397,64 @@ extern "C" omen_status omen_convert_vectors(omen_ctx* ctx, const void* src, int 
 }
 
 // ---------------------------------------------------------------------------------------
-// k-batched product: y_k = (H(k) - sigma) x_k for nk Bloch wave vectors in one launch.  The real
-// bond blocks are the same for every k (the phase sits only on bonds that wrap a Bloch face),
-// so each thread loads a block entry once and applies it to KB vectors; grid.z runs over
-// batches of KB wave vectors.  phases[k*3 + d] = exp(i k_d L_d).  Vectors are [nk][nrows].
+// k-batched product over several structures: y = (H_i(k) - sigma) x for every wave vector k of
+// every structure i, all in one launch (the (structure, k) work list).  Within a structure the
+// real bond blocks are the same for every k (the phase sits only on bonds that wrap a Bloch
+// face), so each thread loads a block entry once and applies it to KB wave vectors.  The CTAs
+// of structure i are [cta0_i, cta0_i + tiles_i * ceil(nk_i / KB)); within them the tile index
+// runs fastest.  phases_i[k*3 + d] = exp(i k_d L_d).  Structure i's vectors are [nk_i][nrows_i]
+// starting at element x_off_i of x and y.
+static constexpr int kMaxKInst = 16;
+
+template <typename T>
+struct KInst {
+  Geo g;
+  const T* blk;
+  const uint8_t* species;
+  const double* onsite;
+  const double* U;
+  const double2* phases;
+  long long nrows;
+  long long x_off;
+  int nk;
+  int slot_stride;
+  int cta0;
+  int tiles;
+};
+
+template <typename T>
+struct KMulti {
+  NeighbourTables nt;
+  KInst<T> in[kMaxKInst];
+  int n;
+  const void* x;
+  void* y;
+  double sigma;
+};
+
 template <typename T, int NORB, int KB>
-__global__ void __launch_bounds__(128) hx_kbatch_kernel(HxArgs<T> a, const double2* __restrict__ phases, int nk) {
+__global__ void __launch_bounds__(128) hx_kbatch_kernel(KMulti<T> m) {
   using V = typename Cx<T>::t;
-  const Geo& g = a.g;
-  const int b = blockIdx.x & 7;
-  const int cell = (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
+  int inst = 0;
+  while (inst + 1 < m.n && (int)blockIdx.x >= m.in[inst + 1].cta0) ++inst;
+  const KInst<T>& I = m.in[inst];
+  const Geo& g = I.g;
+  const int local = (int)blockIdx.x - I.cta0;
+  const int tile = local % I.tiles;
+  const int b = tile & 7;
+  const int cell = (tile >> 3) * blockDim.x + threadIdx.x;
   if (cell >= g.ncells) return;
   const int N = g.natoms;
   const int atom = b * g.ncells + cell;
   const int ix = cell % g.nx, iy = (cell / g.nx) % g.ny, iz = cell / (g.nx * g.ny);
-  const int k0 = blockIdx.z * KB;
-  const int nkb = min(KB, nk - k0);
-  const V* __restrict__ x = static_cast<const V*>(a.x);
-  V* __restrict__ y = static_cast<V*>(a.y);
-  const int sp = a.species[atom];
+  const int k0 = (local / I.tiles) * KB;
+  const int nkb = min(KB, I.nk - k0);
+  const V* __restrict__ x = static_cast<const V*>(m.x) + I.x_off;
+  V* __restrict__ y = static_cast<V*>(m.y) + I.x_off;
+  const int sp = I.species[atom];
   V acc[KB][NORB];
   {
-    const T u = (T)(a.U[atom] - a.sigma);
+    const T u = (T)(I.U[atom] - m.sigma);
 #pragma unroll
     for (int q = 0; q < KB; ++q)
 #pragma unroll
@@ -421,8 +462,8 @@ __global__ void __launch_bounds__(128) hx_kbatch_kernel(HxArgs<T> a, const doubl
         acc[q][o].x = (T)0;
         acc[q][o].y = (T)0;
         if (q < nkb) {
-          const T d = (T)a.onsite[sp * NORB + o] + u;
-          const V xv = x[(size_t)(k0 + q) * a.nrows + (size_t)o * N + atom];
+          const T d = (T)I.onsite[sp * NORB + o] + u;
+          const V xv = x[(size_t)(k0 + q) * I.nrows + (size_t)o * N + atom];
           acc[q][o].x = d * xv.x;
           acc[q][o].y = d * xv.y;
         }
@@ -434,11 +475,11 @@ __global__ void __launch_bounds__(128) hx_kbatch_kernel(HxArgs<T> a, const doubl
   for (int k = 0; k < 4; ++k) {
     int ox, oy, oz, site2;
     if (is_a) {
-      ox = a.nt.a_to_b_off[s][k][0]; oy = a.nt.a_to_b_off[s][k][1]; oz = a.nt.a_to_b_off[s][k][2];
-      site2 = a.nt.a_to_b_site[s][k];
+      ox = m.nt.a_to_b_off[s][k][0]; oy = m.nt.a_to_b_off[s][k][1]; oz = m.nt.a_to_b_off[s][k][2];
+      site2 = m.nt.a_to_b_site[s][k];
     } else {
-      ox = a.nt.b_to_a_off[s][k][0]; oy = a.nt.b_to_a_off[s][k][1]; oz = a.nt.b_to_a_off[s][k][2];
-      site2 = a.nt.b_to_a_site[s][k];
+      ox = m.nt.b_to_a_off[s][k][0]; oy = m.nt.b_to_a_off[s][k][1]; oz = m.nt.b_to_a_off[s][k][2];
+      site2 = m.nt.b_to_a_site[s][k];
     }
     int cell2, wrap[3];
     if (!shift_cell(g, ix, iy, iz, ox, oy, oz, cell2, wrap)) continue;
@@ -453,7 +494,7 @@ __global__ void __launch_bounds__(128) hx_kbatch_kernel(HxArgs<T> a, const doubl
 #pragma unroll
         for (int d = 0; d < 3; ++d)
           if (wrap[d]) {
-            const double2 ph = phases[(size_t)(k0 + q) * 3 + d];
+            const double2 ph = I.phases[(size_t)(k0 + q) * 3 + d];
             V p;
             p.x = (T)ph.x;
             p.y = (T)(wrap[d] > 0 ? ph.y : -ph.y);
@@ -462,13 +503,13 @@ __global__ void __launch_bounds__(128) hx_kbatch_kernel(HxArgs<T> a, const doubl
       }
 #pragma unroll
       for (int o = 0; o < NORB; ++o) {
-        if (q < nkb) xn[q][o] = cmul<T>(x[(size_t)(k0 + q) * a.nrows + (size_t)o * N + atom2], f);
+        if (q < nkb) xn[q][o] = cmul<T>(x[(size_t)(k0 + q) * I.nrows + (size_t)o * N + atom2], f);
         else { xn[q][o].x = (T)0; xn[q][o].y = (T)0; }
       }
     }
     const size_t ks = is_a ? (size_t)(k * 4 + s) : (size_t)(k * 4 + site2);
-    const size_t pidx = ks * a.slot_stride + (is_a ? cell : cell2);
-    const T* __restrict__ hb = a.blk + ((pidx >> 5) * (NORB * NORB)) * 32 + (pidx & 31);
+    const size_t pidx = ks * I.slot_stride + (is_a ? cell : cell2);
+    const T* __restrict__ hb = I.blk + ((pidx >> 5) * (NORB * NORB)) * 32 + (pidx & 31);
 #pragma unroll
     for (int o1 = 0; o1 < NORB; ++o1)
 #pragma unroll
@@ -485,7 +526,7 @@ __global__ void __launch_bounds__(128) hx_kbatch_kernel(HxArgs<T> a, const doubl
   for (int q = 0; q < KB; ++q)
     if (q < nkb)
 #pragma unroll
-      for (int o = 0; o < NORB; ++o) y[(size_t)(k0 + q) * a.nrows + (size_t)o * N + atom] = acc[q][o];
+      for (int o = 0; o < NORB; ++o) y[(size_t)(k0 + q) * I.nrows + (size_t)o * N + atom] = acc[q][o];
 }
 
 size_t vec_elem_bytes(const omen_ham* h, int precision) {
@@ -495,7 +536,7 @@ size_t vec_elem_bytes(const omen_ham* h, int precision) {
 
 template <typename T, int NORB, bool CPLX, bool SO, bool MF, int RBT>
 static cudaError_t launch_t(const HxArgs<T>& a, int nvec, int threads, cudaStream_t st) {
-  dim3 grid(((a.g.ncells + threads - 1) / threads) * 8, 1, nvec);
+  dim3 grid(((a.cell1 - a.cell0 + threads - 1) / threads) * 8, 1, nvec);
   hx_kernel<T, NORB, CPLX, SO, MF, RBT><<<grid, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
@@ -548,7 +589,7 @@ bool hx_tile_valid(const omen_ham* h, int vec_precision, int threads, int rb) {
 
 template <typename T>
 static cudaError_t launch_prec(const omen_ham* h, const T* blk, const T* b0, const void* x, void* y, int nvec,
-                               double sigma, cudaStream_t st) {
+                               double sigma, cudaStream_t st, int cell0, int cell1) {
   const omen_lattice* L = h->lat;
   HxArgs<T> a;
   a.g = Geo{L->nx, L->ny, L->nz, L->ncells, L->natoms, {L->periodic[0], L->periodic[1], L->periodic[2]}};
@@ -568,25 +609,34 @@ static cudaError_t launch_prec(const omen_ham* h, const T* blk, const T* b0, con
   for (int d = 0; d < 3; ++d) a.phase[d] = h->phase[d];
   a.ns = h->nspecies;
   a.slot_stride = h->slot_stride;
+  a.cell0 = cell0;
+  a.cell1 = cell1;
   const HxTile t = h->tile[sizeof(T) == 8 ? 0 : 1];
   return h->norb == 10 ? launch_norb<T, 10>(a, h, nvec, t, st) : launch_norb<T, 5>(a, h, nvec, t, st);
 }
 
-omen_status launch_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma, int vec_precision) {
+// y rows of the cells [cell0, cell1) (all orbitals, sites, vectors); the rest of y is untouched
+static omen_status launch_hx_cells(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma,
+                                   int vec_precision, int cell0, int cell1, cudaStream_t st) {
   if (nvec < 1 || nvec > 65535) return set_err(ctx, OMEN_EINVAL, "nvec must be 1..65535");
+  if (cell1 <= cell0) return OMEN_OK;
   cudaError_t e;
   if (vec_precision == OMEN_F64_DF) {
     if (!h->d_blkdf) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no double-float blocks");
-    e = launch_df(h, x, y, nvec, sigma, ctx->stream);
+    e = launch_df(h, x, y, nvec, sigma, st, cell0, cell1);
   } else if (vec_precision == OMEN_F64) {
     if (!h->matrix_free && !h->d_blk64) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP64 blocks");
-    e = launch_prec<double>(h, h->d_blk64, h->d_b0_64, x, y, nvec, sigma, ctx->stream);
+    e = launch_prec<double>(h, h->d_blk64, h->d_b0_64, x, y, nvec, sigma, st, cell0, cell1);
   } else {
     if (!h->matrix_free && !h->d_blk32) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP32 blocks");
-    e = launch_prec<float>(h, h->d_blk32, h->d_b0_32, x, y, nvec, sigma, ctx->stream);
+    e = launch_prec<float>(h, h->d_blk32, h->d_b0_32, x, y, nvec, sigma, st, cell0, cell1);
   }
   if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "H·X launch failed: %s", cudaGetErrorString(e));
   return OMEN_OK;
+}
+
+omen_status launch_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma, int vec_precision) {
+  return launch_hx_cells(ctx, h, x, y, nvec, sigma, vec_precision, 0, h->lat->ncells, ctx->stream);
 }
 
 static int native_precision(const omen_ham* h) {
@@ -597,6 +647,81 @@ static int native_precision(const omen_ham* h) {
 extern "C" omen_status omen_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma) {
   if (!ctx || !h || !x || !y) return set_err(ctx, OMEN_EINVAL, "null argument");
   return launch_hx(ctx, h, x, y, nvec, sigma, native_precision(h));
+}
+
+// Host-buffer product with the copies overlapped: the structure is cut into slabs of whole
+// z-planes; slab i of x goes up on one copy stream, its rows of y are computed on the context's
+// stream as soon as the planes they touch (the slab and one plane on each side) are on the
+// device, and go down on the other copy stream while later slabs compute.  A slab of every
+// vector is one strided copy: rows (vector, orbital, site) are ncells apart and a slab's cells
+// are contiguous within each.  With a periodic z axis the first slab also needs the last
+// plane, so it is computed last.
+static omen_status hx_host_pipelined(omen_ctx* ctx, const omen_ham* h, const void* xh, void* yh, void* dx, void* dy,
+                                     int nvec, double sigma) {
+  const omen_lattice* L = h->lat;
+  const int prec = native_precision(h);
+  const size_t el = vec_elem_bytes(h, prec);
+  const int plane = L->nx * L->ny;
+  const int S = std::max(1, std::min(8, L->nz / 2));
+  const size_t pitch = (size_t)L->ncells * el;
+  const size_t rows = (size_t)nvec * (size_t)(h->nrows / L->ncells);   // (vector, orbital, site) runs
+  for (int k = 0; k < 2; ++k)
+    if (!ctx->copy_stream[k] && cudaStreamCreateWithFlags(&ctx->copy_stream[k], cudaStreamNonBlocking) != cudaSuccess) {
+      ctx->copy_stream[k] = nullptr;
+      return set_err(ctx, OMEN_ECUDA, "could not create a copy stream");
+    }
+  cudaStream_t sin = ctx->copy_stream[0], sout = ctx->copy_stream[1];
+  std::vector<cudaEvent_t> ev(2 * S + 2, nullptr);
+  omen_status st = OMEN_OK;
+  for (auto& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      e = nullptr;
+      st = set_err(ctx, OMEN_ECUDA, "event creation failed");
+    }
+  auto z0 = [&](int i) { return (int)((long long)L->nz * i / S); };
+  cudaEvent_t* ein = ev.data();
+  cudaEvent_t* ecomp = ev.data() + S;
+  cudaEvent_t start = ev[2 * S], done = ev[2 * S + 1];
+  cudaError_t e = cudaSuccess;
+  if (st == OMEN_OK) {
+    // the buffers were allocated on the context's stream: order the copy streams after it
+    e = cudaEventRecord(start, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, start, 0);
+  }
+  for (int i = 0; i < S && st == OMEN_OK && e == cudaSuccess; ++i) {
+    const size_t c0 = (size_t)z0(i) * plane, c1 = (size_t)z0(i + 1) * plane;
+    e = cudaMemcpy2DAsync(static_cast<char*>(dx) + c0 * el, pitch, static_cast<const char*>(xh) + c0 * el, pitch,
+                          (c1 - c0) * el, rows, cudaMemcpyHostToDevice, sin);
+    if (e == cudaSuccess) e = cudaEventRecord(ein[i], sin);
+  }
+  const bool zper = L->periodic[2] != OMEN_HARD_WALL;
+  for (int t = 0; t < S && st == OMEN_OK && e == cudaSuccess; ++t) {
+    const int i = zper ? (t + 1) % S : t;     // periodic z: slab 0 last
+    const int need = zper && i == 0 ? S - 1 : std::min(i + 1, S - 1);
+    e = cudaStreamWaitEvent(ctx->stream, ein[need], 0);
+    if (e != cudaSuccess) break;
+    st = launch_hx_cells(ctx, h, dx, dy, nvec, sigma, prec, z0(i) * plane, z0(i + 1) * plane, ctx->stream);
+    if (st != OMEN_OK) break;
+    e = cudaEventRecord(ecomp[i], ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ecomp[i], 0);
+    const size_t c0 = (size_t)z0(i) * plane, c1 = (size_t)z0(i + 1) * plane;
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(static_cast<char*>(yh) + c0 * el, pitch, static_cast<const char*>(dy) + c0 * el, pitch,
+                            (c1 - c0) * el, rows, cudaMemcpyDeviceToHost, sout);
+  }
+  // the context's stream (and the caller's frees on it) wait for the last copy down
+  if (st == OMEN_OK && e == cudaSuccess) e = cudaEventRecord(done, sout);
+  if (st == OMEN_OK && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, done, 0);
+  if (st == OMEN_OK && e != cudaSuccess) st = set_err(ctx, OMEN_ECUDA, "host H·X copies: %s", cudaGetErrorString(e));
+  if (st != OMEN_OK) {
+    // leave nothing in flight on the copy streams before the buffers go back
+    cudaStreamSynchronize(sin);
+    cudaStreamSynchronize(sout);
+  }
+  for (cudaEvent_t q : ev)
+    if (q) cudaEventDestroy(q);
+  return st;
 }
 
 extern "C" omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* h, const void* xh, void* yh, int nvec, double sigma) {
@@ -633,18 +758,12 @@ extern "C" omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* h, const void
     if (dx) cudaFreeAsync(dx, ctx->stream);
     return set_err(ctx, OMEN_ENOMEM, "device allocation of %zu bytes failed", bytes);
   }
-  omen_status st = OMEN_OK;
-  cudaError_t e = cudaMemcpyAsync(dx, xh, bytes, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) {
-    st = launch_hx(ctx, h, dx, dy, nvec, sigma, native_precision(h));
-    if (st == OMEN_OK) e = cudaMemcpyAsync(yh, dy, bytes, cudaMemcpyDeviceToHost, ctx->stream);
-  }
+  omen_status st = hx_host_pipelined(ctx, h, xh, yh, dx, dy, nvec, sigma);
   cudaFreeAsync(dx, ctx->stream);
   cudaFreeAsync(dy, ctx->stream);
   cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
   if (st != OMEN_OK) return st;
-  if (e != cudaSuccess || e2 != cudaSuccess)
-    return set_err(ctx, OMEN_ECUDA, "host H·X failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  if (e2 != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "host H·X failed: %s", cudaGetErrorString(e2));
   return OMEN_OK;
 }
 
@@ -659,57 +778,72 @@ bool hx_kbatch_tile_valid(int vec_precision, int threads, int kb) {
 }
 
 template <typename T, int KB>
-static cudaError_t launch_kb(const HxArgs<T>& a, const omen_ham* h, const double2* phases, int nk, int threads,
-                             cudaStream_t st) {
-  dim3 grid(((a.g.ncells + threads - 1) / threads) * 8, 1, (nk + KB - 1) / KB);
-  if (h->norb == 10) hx_kbatch_kernel<T, 10, KB><<<grid, threads, 0, st>>>(a, phases, nk);
-  else hx_kbatch_kernel<T, 5, KB><<<grid, threads, 0, st>>>(a, phases, nk);
+static cudaError_t launch_kb(KMulti<T>& m, int norb, int threads, cudaStream_t st) {
+  long long total = 0;
+  for (int i = 0; i < m.n; ++i) {
+    m.in[i].tiles = ((m.in[i].g.ncells + threads - 1) / threads) * 8;
+    m.in[i].cta0 = (int)total;
+    total += (long long)m.in[i].tiles * ((m.in[i].nk + KB - 1) / KB);
+  }
+  if (total > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (norb == 10) hx_kbatch_kernel<T, 10, KB><<<(unsigned)total, threads, 0, st>>>(m);
+  else hx_kbatch_kernel<T, 5, KB><<<(unsigned)total, threads, 0, st>>>(m);
   return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_kbatch_prec(const omen_ham* h, const T* blk, const double2* phases, int nk, const void* x,
-                                      void* y, double sigma, cudaStream_t st) {
-  const omen_lattice* L = h->lat;
-  HxArgs<T> a;
-  a.g = Geo{L->nx, L->ny, L->nz, L->ncells, L->natoms, {L->periodic[0], L->periodic[1], L->periodic[2]}};
-  a.nt = host_neighbour_tables();
-  a.blk = blk;
-  a.b0 = nullptr;
-  a.strain = L->d_strain;
-  a.species = L->d_species;
-  a.onsite = h->d_onsite;
-  a.U = h->d_U;
-  a.lambda = h->d_lambda;
-  a.x = x;
-  a.y = y;
-  a.nrows = h->nrows;
-  a.sigma = sigma;
-  a.eta = h->eta;
-  for (int d = 0; d < 3; ++d) a.phase[d] = h->phase[d];
-  a.ns = h->nspecies;
-  a.slot_stride = h->slot_stride;
-  const HxTile t = h->ktile[sizeof(T) == 8 ? 0 : 1];
+static cudaError_t launch_kmulti_prec(const KItem* items, int nitems, const void* x, void* y, double sigma,
+                                      cudaStream_t st) {
+  KMulti<T> m;
+  m.nt = host_neighbour_tables();
+  m.n = nitems;
+  m.x = x;
+  m.y = y;
+  m.sigma = sigma;
+  for (int i = 0; i < nitems; ++i) {
+    const omen_ham* h = items[i].ham;
+    const omen_lattice* L = h->lat;
+    KInst<T>& I = m.in[i];
+    I.g = Geo{L->nx, L->ny, L->nz, L->ncells, L->natoms, {L->periodic[0], L->periodic[1], L->periodic[2]}};
+    if constexpr (sizeof(T) == 8) I.blk = h->d_blk64; else I.blk = h->d_blk32;
+    I.species = L->d_species;
+    I.onsite = h->d_onsite;
+    I.U = h->d_U;
+    I.phases = items[i].phases;
+    I.nrows = h->nrows;
+    I.x_off = items[i].x_off;
+    I.nk = items[i].nk;
+    I.slot_stride = h->slot_stride;
+  }
+  const HxTile t = items[0].ham->ktile[sizeof(T) == 8 ? 0 : 1];
   const int thr = t.threads ? t.threads : 128;
-  if (t.rb == 1) return launch_kb<T, 1>(a, h, phases, nk, thr, st);
-  if constexpr (sizeof(T) == 4) if (t.rb == 4) return launch_kb<T, 4>(a, h, phases, nk, thr, st);
-  return launch_kb<T, kKB>(a, h, phases, nk, thr, st);
+  if (t.rb == 1) return launch_kb<T, 1>(m, items[0].ham->norb, thr, st);
+  if constexpr (sizeof(T) == 4) if (t.rb == 4) return launch_kb<T, 4>(m, items[0].ham->norb, thr, st);
+  return launch_kb<T, kKB>(m, items[0].ham->norb, thr, st);
+}
+
+omen_status launch_hx_kmulti(omen_ctx* ctx, const KItem* items, int nitems, const void* x, void* y, double sigma,
+                             int vec_precision) {
+  if (nitems < 1 || nitems > kMaxKInst) return set_err(ctx, OMEN_EINVAL, "1..%d structures per k batch", kMaxKInst);
+  const bool f64 = vec_precision == OMEN_F64;
+  for (int i = 0; i < nitems; ++i) {
+    const omen_ham* h = items[i].ham;
+    if (!h || items[i].nk < 1 || items[i].nk > 65535) return set_err(ctx, OMEN_EINVAL, "structure %d: null or nk out of range", i);
+    if (!h->bloch || h->matrix_free || h->spin_orbit)
+      return set_err(ctx, OMEN_EUNSUPPORTED, "k batch needs Bloch structures with stored blocks and no spin-orbit");
+    if (h->norb != items[0].ham->norb) return set_err(ctx, OMEN_EINVAL, "structures of one k batch share the basis");
+    if (f64 ? !h->d_blk64 : !h->d_blk32) return set_err(ctx, OMEN_EINVAL, "structure %d has no blocks of this precision", i);
+  }
+  const cudaError_t e = f64 ? launch_kmulti_prec<double>(items, nitems, x, y, sigma, ctx->stream)
+                            : launch_kmulti_prec<float>(items, nitems, x, y, sigma, ctx->stream);
+  if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "k-batched H·X launch: %s", cudaGetErrorString(e));
+  return OMEN_OK;
 }
 
 omen_status launch_hx_kbatch(omen_ctx* ctx, const omen_ham* h, int nk, const double2* phases_dev, const void* x, void* y,
                              double sigma, int vec_precision) {
-  if (h->matrix_free || h->spin_orbit) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch needs stored blocks without spin-orbit");
-  if ((long long)nk > 65535) return set_err(ctx, OMEN_EINVAL, "too many wave vectors");
-  cudaError_t e;
-  if (vec_precision == OMEN_F64) {
-    if (!h->d_blk64) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP64 blocks");
-    e = launch_kbatch_prec<double>(h, h->d_blk64, phases_dev, nk, x, y, sigma, ctx->stream);
-  } else {
-    if (!h->d_blk32) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP32 blocks");
-    e = launch_kbatch_prec<float>(h, h->d_blk32, phases_dev, nk, x, y, sigma, ctx->stream);
-  }
-  if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "k-batched H·X launch: %s", cudaGetErrorString(e));
-  return OMEN_OK;
+  const KItem item{h, nk, phases_dev, 0};
+  return launch_hx_kmulti(ctx, &item, 1, x, y, sigma, vec_precision);
 }
 
 omen_status make_phases(omen_ctx* ctx, const omen_ham* h, int nk, const double* k_host, double2** out) {
@@ -727,6 +861,31 @@ omen_status make_phases(omen_ctx* ctx, const omen_ham* h, int nk, const double* 
   }
   OMEN_CUDA(ctx, cudaMemcpyAsync(*out, ph.data(), sizeof(double2) * ph.size(), cudaMemcpyHostToDevice, ctx->stream));
   return OMEN_OK;
+}
+
+extern "C" omen_status omen_hx_kbatch_multi(omen_ctx* ctx, int nitems, const omen_kbatch_item* it, const void* x, void* y,
+                                            double sigma) {
+  if (!ctx || !it || !x || !y || nitems < 1 || nitems > kMaxKInst) return set_err(ctx, OMEN_EINVAL, "null argument or 1..%d structures", kMaxKInst);
+  std::vector<KItem> items(nitems);
+  std::vector<double2*> ph(nitems, nullptr);
+  long long off = 0;
+  omen_status s = OMEN_OK;
+  for (int i = 0; i < nitems && s == OMEN_OK; ++i) {
+    if (!it[i].ham || !it[i].k_host || it[i].nk < 1) { s = set_err(ctx, OMEN_EINVAL, "structure %d: null argument or nk < 1", i); break; }
+    if (!it[i].ham->bloch) { s = set_err(ctx, OMEN_EINVAL, "structure %d has no Bloch-periodic direction", i); break; }
+    s = make_phases(ctx, it[i].ham, it[i].nk, it[i].k_host, &ph[i]);
+    items[i] = KItem{it[i].ham, it[i].nk, ph[i], off};
+    off += (long long)it[i].nk * it[i].ham->nrows;
+  }
+  if (s == OMEN_OK) {
+    const omen_ham* h0 = it[0].ham;
+    for (int i = 1; i < nitems && s == OMEN_OK; ++i)
+      if (it[i].ham->precision != h0->precision) s = set_err(ctx, OMEN_EINVAL, "structures of one k batch share the precision");
+    if (s == OMEN_OK) s = launch_hx_kmulti(ctx, items.data(), nitems, x, y, sigma, native_precision(h0));
+  }
+  for (double2* q : ph)
+    if (q) cudaFreeAsync(q, ctx->stream);
+  return s;
 }
 
 extern "C" omen_status omen_hx_kbatch(omen_ctx* ctx, const omen_ham* h, int nk, const double* k_host, const void* x,

@@ -123,32 +123,43 @@ __global__ void reduce_partial_kernel(const double2* __restrict__ P, int nchunks
 // so b stays in L2 across the basis groups.  FP64 vectors accumulate in FP64; FP32 vectors
 // accumulate each thread's rows in compensated FP32 (Kahan) before the FP64 block sum.
 static constexpr int kIG = 16;
+// basis vectors per CTA of dots1_kernel: 16 real, 8 complex (the complex accumulators would
+// otherwise hold the kernel to one CTA per SM)
+static constexpr int dots1_ig(bool cplx) { return cplx ? 8 : kIG; }
 template <typename T, bool C>
-__global__ void __launch_bounds__(256) dots1_kernel(const void* Av, long long lda, int na, const void* Bv,
+__global__ void __launch_bounds__(256, C ? 1 : 2) dots1_kernel(const void* Av, long long lda, int na, const void* Bv,
                                                     long long n, int rows_per_cta, double2* __restrict__ P,
-                                                    long long a_ps = 0, long long b_ps = 0, long long p_ps = 0) {
+                                                    long long a_ps = 0, long long b_ps = 0, long long p_ps = 0,
+                                                    const long long* __restrict__ poff = nullptr,
+                                                    const long long* __restrict__ plen = nullptr,
+                                                    const int* __restrict__ act = nullptr) {
   using E = Elem<T, C>;
   using V = typename E::V;
   using Acc = std::conditional_t<sizeof(T) == 8, double, float>;
-  // grid.z = independent problems (batched Lanczos), offsets a_ps, b_ps (elements), p_ps (partials)
-  const V* A = static_cast<const V*>(Av) + blockIdx.z * a_ps;
-  const V* B = static_cast<const V*>(Bv) + blockIdx.z * b_ps;
+  constexpr int IG = dots1_ig(C);
+  // grid.z = independent problems (batched Lanczos): offsets a_ps, b_ps (elements), p_ps
+  // (partials) per problem, or per-problem element offsets poff and lengths plen
+  const long long off = poff ? poff[blockIdx.z] : 0;
+  if (act && !act[blockIdx.z]) return;   // a converged (frozen) problem of the batch
+  if (plen) n = plen[blockIdx.z];
+  const V* A = static_cast<const V*>(Av) + blockIdx.z * a_ps + off;
+  const V* B = static_cast<const V*>(Bv) + blockIdx.z * b_ps + off;
   P += blockIdx.z * p_ps;
-  const int i0 = blockIdx.x * kIG;
-  const int ni = min(kIG, na - i0);
+  const int i0 = blockIdx.x * IG;
+  const int ni = min(IG, na - i0);
   const long long r0 = (long long)blockIdx.y * rows_per_cta;
   const long long r1 = min(n, r0 + rows_per_cta);
-  Acc sr[kIG], si[kIG], cr[kIG], ci[kIG];
+  Acc sr[IG], si[IG], cr[IG], ci[IG];
 #pragma unroll
-  for (int i = 0; i < kIG; ++i) { sr[i] = 0; si[i] = 0; cr[i] = 0; ci[i] = 0; }
+  for (int i = 0; i < IG; ++i) { sr[i] = 0; si[i] = 0; cr[i] = 0; ci[i] = 0; }
   for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const V bv = B[r];
-    V av[kIG];
+    V av[IG];
 #pragma unroll
-    for (int i = 0; i < kIG; ++i)
+    for (int i = 0; i < IG; ++i)
       if (i < ni) av[i] = A[(size_t)(i0 + i) * lda + r];
 #pragma unroll
-    for (int i = 0; i < kIG; ++i) {
+    for (int i = 0; i < IG; ++i) {
       if (i < ni) {
         Acc pr, pi = 0;
         if constexpr (C) {
@@ -171,10 +182,10 @@ __global__ void __launch_bounds__(256) dots1_kernel(const void* Av, long long ld
       }
     }
   }
-  __shared__ double red[8][kIG][2];
+  __shared__ double red[8][IG][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < kIG; ++i) {
+  for (int i = 0; i < IG; ++i) {
     double vr = (double)sr[i] - (double)cr[i], vi = (double)si[i] - (double)ci[i];
     for (int o = 16; o > 0; o >>= 1) {
       vr += __shfl_xor_sync(0xffffffffu, vr, o);
@@ -190,30 +201,14 @@ __global__ void __launch_bounds__(256) dots1_kernel(const void* Av, long long ld
   }
 }
 
-// y = beta*y + alpha * sum_i A_i m_i for one output vector, 8 basis loads in flight per row.
-// FP64 vectors accumulate in FP64; FP32 vectors in FP32 (coefficients rounded once from their
-// FP64 values; the result is stored in FP32), which keeps them off GB300's slow FP64 pipe.
-template <typename T, bool C>
-__global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M,
-                                                       void* Yv, long long n, double alpha, double beta,
-                                                       long long a_ps = 0, long long m_ps = 0, long long y_ps = 0) {
-  using E = Elem<T, C>;
-  using V = typename E::V;
-  using A2 = std::conditional_t<sizeof(T) == 8, double2, float2>;
+// y = beta*y + sum_i A_i Ms_i over this CTA's rows (Ms: coefficients in shared memory, alpha
+// already applied), 8 basis loads in flight per row.
+template <typename T, bool C, typename A2>
+__device__ __forceinline__ void combine1_rows(const typename Elem<T, C>::V* __restrict__ A, long long lda, int na,
+                                              const A2* __restrict__ Ms, typename Elem<T, C>::V* __restrict__ Y,
+                                              long long n, T rbeta, bool use_beta) {
+  using V = typename Elem<T, C>::V;
   using R = T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  A2* Ms = reinterpret_cast<A2*>(smem_raw);
-  M += blockIdx.y * m_ps;
-  for (int t = threadIdx.x; t < na; t += blockDim.x) {
-    A2 m;
-    m.x = (R)(alpha * M[t].x);
-    m.y = (R)(alpha * M[t].y);
-    Ms[t] = m;
-  }
-  __syncthreads();
-  const V* A = static_cast<const V*>(Av) + blockIdx.y * a_ps;
-  V* Y = static_cast<V*>(Yv) + blockIdx.y * y_ps;
-  const R rbeta = (R)beta;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
     R yr = 0, yi = 0;
     int i = 0;
@@ -250,20 +245,96 @@ __global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long
     if constexpr (C) {
       out.x = yr;
       out.y = yi;
-      if (beta != 0.0) {
+      if (use_beta) {
         out.x = fma(rbeta, Y[r].x, out.x);
         out.y = fma(rbeta, Y[r].y, out.y);
       }
     } else {
       out = yr;
-      if (beta != 0.0) out = fma(rbeta, Y[r], out);
+      if (use_beta) out = fma(rbeta, Y[r], out);
     }
     Y[r] = out;
   }
 }
 
+// y = beta*y + alpha * sum_i A_i m_i for one output vector.
+// FP64 vectors accumulate in FP64; FP32 vectors in FP32 (coefficients rounded once from their
+// FP64 values; the result is stored in FP32), which keeps them off GB300's slow FP64 pipe.
+template <typename T, bool C>
+__global__ void __launch_bounds__(256) combine1_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M,
+                                                       void* Yv, long long n, double alpha, double beta,
+                                                       long long a_ps = 0, long long m_ps = 0, long long y_ps = 0,
+                                                       const long long* __restrict__ poff = nullptr,
+                                                       const long long* __restrict__ plen = nullptr,
+                                                       const int* __restrict__ act = nullptr) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  using A2 = std::conditional_t<sizeof(T) == 8, double2, float2>;
+  using R = T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A2* Ms = reinterpret_cast<A2*>(smem_raw);
+  M += blockIdx.y * m_ps;
+  for (int t = threadIdx.x; t < na; t += blockDim.x) {
+    A2 m;
+    m.x = (R)(alpha * M[t].x);
+    m.y = (R)(alpha * M[t].y);
+    Ms[t] = m;
+  }
+  __syncthreads();
+  const long long off = poff ? poff[blockIdx.y] : 0;
+  if (act && !act[blockIdx.y]) return;
+  if (plen) n = plen[blockIdx.y];
+  const V* A = static_cast<const V*>(Av) + blockIdx.y * a_ps + off;
+  V* Y = static_cast<V*>(Yv) + blockIdx.y * y_ps + off;
+  combine1_rows<T, C, A2>(A, lda, na, Ms, Y, n, (R)beta, beta != 0.0);
+}
+
+// The update w -= V h of the full Gram–Schmidt pass, applied only where it is needed to keep
+// the basis semi-orthogonal (Simon, Math. Comp. 42 (1984) 115): when some |h_i| exceeds
+// eta * ||w|| (eta = square root of the vectors' unit roundoff; ||w||^2 read from nrm2), or
+// when the previous step applied its pass (a correction is always repeated once, since the
+// vector it repairs feeds the next step).  gate[parity] records whether this step applied it,
+// gate[parity ^ 1] is the previous step's record.  When applied, h is also added into column
+// Tcol of the projected matrix.
+template <typename T, bool C>
+__global__ void __launch_bounds__(256) combine1_gated_kernel(const void* Av, int na, const double2* __restrict__ M,
+                                                             void* Yv, long long n, const double2* __restrict__ nrm2,
+                                                             double eta, int* __restrict__ gate, int parity,
+                                                             double2* __restrict__ Tcol) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  using A2 = std::conditional_t<sizeof(T) == 8, double2, float2>;
+  using R = T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  A2* Ms = reinterpret_cast<A2*>(smem_raw);
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const double lim = eta * eta * fmax(nrm2->x, 0.0);
+  int mine = 0;
+  for (int t = threadIdx.x; t < na; t += blockDim.x) {
+    const double2 h = M[t];
+    if (h.x * h.x + h.y * h.y > lim || !(h.x == h.x) || !(h.y == h.y)) mine = 1;
+    A2 m;
+    m.x = (R)(-h.x);
+    m.y = (R)(-h.y);
+    Ms[t] = m;
+  }
+  if (mine) any = 1;
+  __syncthreads();
+  const bool run = any || gate[parity ^ 1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) gate[parity] = run ? 1 : 0;
+  if (!run) return;
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < na; t += blockDim.x) {
+      Tcol[t].x += M[t].x;
+      Tcol[t].y += M[t].y;
+    }
+  combine1_rows<T, C, A2>(static_cast<const V*>(Av), n, na, Ms, static_cast<V*>(Yv), n, (R)1, true);
+}
+
 // Projections onto NB right-hand columns at once (2 <= NB <= 4): CTA (g, c) handles basis
-// vectors IG*g .. IG*g + IG-1 (IG = 16 / NB) over row chunk c; every basis load serves all NB
+// vectors IG*g .. IG*g + IG-1 (IG = 16 / NB real, 8 / NB complex) over row chunk c; every basis load serves all NB
 // columns.  Partials P[chunk][i][j].
 template <typename T, bool C, int NB>
 __global__ void __launch_bounds__(256) dotsn_kernel(const void* Av, long long lda, int na, const void* Bv, long long ldb,
@@ -271,7 +342,7 @@ __global__ void __launch_bounds__(256) dotsn_kernel(const void* Av, long long ld
   using E = Elem<T, C>;
   using V = typename E::V;
   using Acc = std::conditional_t<sizeof(T) == 8, double, float>;
-  constexpr int IG = 16 / NB;
+  constexpr int IG = dots1_ig(C) / NB;
   const V* A = static_cast<const V*>(Av);
   const V* B = static_cast<const V*>(Bv);
   const int i0 = blockIdx.x * IG;
@@ -420,7 +491,8 @@ __global__ void __launch_bounds__(256) combinen_kernel(const void* Av, long long
 // into columns col0.. of the projected matrix T (ldT x ldT, column-major).
 __global__ void reduce_dev_kernel(const double2* __restrict__ P, int nchunks, int na, int nb, double2* __restrict__ out,
                                   double2* __restrict__ accT, int ldT, int col0, long long p_ps = 0,
-                                  long long out_ps = 0, long long t_ps = 0) {
+                                  long long out_ps = 0, long long t_ps = 0, const int* __restrict__ act = nullptr) {
+  if (act && !act[blockIdx.y]) return;
   const int e = blockIdx.x;
   P += blockIdx.y * p_ps;
   out += blockIdx.y * out_ps;
@@ -458,15 +530,21 @@ __global__ void reduce_dev_kernel(const double2* __restrict__ P, int nchunks, in
 template <typename T, bool C>
 __global__ void normalize_kernel(const void* Wv, void* Vv, long long n, const double2* __restrict__ nrm2,
                                  double2* __restrict__ Tm, int ldT, int row, int col, int* __restrict__ flag,
-                                 long long w_ps = 0, long long v_ps = 0, long long n_ps = 0, long long t_ps = 0) {
+                                 long long w_ps = 0, long long v_ps = 0, long long n_ps = 0, long long t_ps = 0,
+                                 const long long* __restrict__ poff = nullptr,
+                                 const long long* __restrict__ plen = nullptr,
+                                 const int* __restrict__ act = nullptr) {
   using E = Elem<T, C>;
   using V = typename E::V;
   nrm2 += blockIdx.y * n_ps;
   if (Tm) Tm += blockIdx.y * t_ps;
   const double b = sqrt(fmax(nrm2->x, 0.0));
   const double inv = (b > 1e-300) ? 1.0 / b : 0.0;
-  const V* W = static_cast<const V*>(Wv) + blockIdx.y * w_ps;
-  V* Vo = static_cast<V*>(Vv) + blockIdx.y * v_ps;
+  if (act && !act[blockIdx.y]) return;
+  const long long off = poff ? poff[blockIdx.y] : 0;
+  if (plen) n = plen[blockIdx.y];
+  const V* W = static_cast<const V*>(Wv) + blockIdx.y * w_ps + off;
+  V* Vo = static_cast<V*>(Vv) + blockIdx.y * v_ps + off;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
     Vo[r] = E::make(E::re(W[r]) * inv, E::im(W[r]) * inv);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -703,6 +781,28 @@ struct KrylovOps {
     return OMEN_OK;
   }
 
+  // Rows per CTA of the projection kernels (na basis vectors, ig of them per CTA): enough row
+  // chunks that the grid covers every SM about twice (small problems would otherwise run on a
+  // handful of CTAs), at most 8192 rows per chunk, at most 65535 chunks.
+  long long dot_rows(int na, int ig) const {
+    const long long groups = std::max(1, (na + ig - 1) / ig);
+    const long long want = std::max<long long>(1, (2LL * sm_count + groups - 1) / groups);
+    long long rows = (n + want - 1) / want;
+    rows = std::min<long long>(8192, std::max<long long>(256, (rows + 255) / 256 * 256));
+    while ((n + rows - 1) / rows > 65535) rows *= 2;
+    return rows;
+  }
+  // the largest partial-sum count a projection of up to na_max basis vectors asks for
+  size_t max_partials(int na_max) const {
+    size_t need = 0;
+    for (int na = 1; na <= na_max; ++na)
+      for (int ig : {kIG, 8, 4, 2}) {
+        const long long rows = dot_rows(na, ig);
+        need = std::max(need, (size_t)((n + rows - 1) / rows) * na * 4);
+      }
+    return need;
+  }
+
   // grows geometrically (cudaFree synchronises the device, so it must not happen per step)
   omen_status ensure_partial(size_t need) {
     if (need <= partial_cap) return OMEN_OK;
@@ -724,12 +824,11 @@ struct KrylovOps {
     if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "dots_dev: too many columns");
     if (nb > 1 && nb <= 4) {
       // a few right-hand columns: one launch, each basis load serving every column
-      int rows = 8192;
-      while ((n + rows - 1) / rows > 65535) rows *= 2;
+      const int ig = dots1_ig(cplx) / ((nb <= 2) ? 2 : 4);
+      const int rows = (int)dot_rows(na, ig);
       const long long nchunks = (n + rows - 1) / rows;
       omen_status s1 = ensure_partial((size_t)nchunks * na * nb);
       if (s1 != OMEN_OK) return s1;
-      const int ig = (nb <= 2) ? 8 : 4;
       dim3 grid((na + ig - 1) / ig, (unsigned)nchunks);
 #define DOTSN(T, Cc)                                                                                     \
   do {                                                                                                   \
@@ -744,12 +843,12 @@ struct KrylovOps {
       return OMEN_OK;
     }
     if (nb == 1) {
-      int rows = 8192;
-      while ((n + rows - 1) / rows > 65535) rows *= 2;
+      const int ig1 = dots1_ig(cplx);
+      const int rows = (int)dot_rows(na, ig1);
       const long long nchunks = (n + rows - 1) / rows;
       omen_status s1 = ensure_partial((size_t)nchunks * na);
       if (s1 != OMEN_OK) return s1;
-      dim3 grid((na + kIG - 1) / kIG, (unsigned)nchunks);
+      dim3 grid((na + ig1 - 1) / ig1, (unsigned)nchunks);
       if (prec == OMEN_F64) {
         if (cplx) dots1_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
         else dots1_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
@@ -829,6 +928,30 @@ struct KrylovOps {
     return OMEN_OK;
   }
 
+  // w -= V h only where semi-orthogonality needs it (combine1_gated_kernel); h added into Tcol then
+  omen_status combine_gated(const void* A, int na, const double2* h_dev, void* W, const double2* nrm2, int parity,
+                            double2* Tcol) {
+    const double eta = prec == OMEN_F64 ? 1.0536712127723509e-08 : 2.44140625e-04;  // sqrt(2^-53), sqrt(2^-24)
+    const size_t shm = (size_t)na * sizeof(double2);
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+    int* gate = ctx->d_status + 2;
+#define GATED(T, Cc)                                                                                  \
+  do {                                                                                                \
+    smem_limit(combine1_gated_kernel<T, Cc>, shm);                                                    \
+    combine1_gated_kernel<T, Cc><<<grid, 256, shm, ctx->stream>>>(A, na, h_dev, W, n, nrm2, eta, gate, parity, Tcol); \
+  } while (0)
+    if (prec == OMEN_F64) { if (cplx) GATED(double, true); else GATED(double, false); }
+    else { if (cplx) GATED(float, true); else GATED(float, false); }
+#undef GATED
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+  // the next gated pass (parity) is applied unconditionally (after a restart's full passes)
+  omen_status force_next_pass(int parity) {
+    OMEN_CUDA(ctx, cudaMemsetAsync(ctx->d_status + 2 + (parity ^ 1), 1, sizeof(int), ctx->stream));
+    return OMEN_OK;
+  }
+
   omen_status normalize_dev(const void* W, void* V, const double2* nrm2, double2* Tm, int ldT, int row, int col) {
     const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
     int* flag = ctx->d_status + 1;
@@ -843,26 +966,34 @@ struct KrylovOps {
     return OMEN_OK;
   }
 
-  // ---- batched (P independent problems of n rows each, problem p at offset p*n) ----
-  // A: na basis vectors with stride lda between vectors; B, out, T per problem.
+  // ---- batched: P independent problems.  Problem p's part of a vector slot starts at element
+  // b_off[p] and has b_len[p] rows (device arrays; b_nmax = the longest).  A: na basis slots with
+  // stride lda between slots; B, out, T per problem. ----
+  const long long* b_off = nullptr;
+  const long long* b_len = nullptr;
+  const int* b_act = nullptr;   // per-problem 0/1: frozen problems are skipped
+  long long b_nmax = 0;
+
   omen_status dots_dev_batch(int P, const void* A, long long lda, int na, const void* B, double2* out_dev,
                              long long out_ps, double2* accT, int ldT, long long t_ps, int col0) {
-    int rows = 8192;
-    while ((n + rows - 1) / rows > 65535) rows *= 2;
-    const long long nchunks = (n + rows - 1) / rows;
+    // the P problems share the grid: chunks sized for about two CTAs per SM over the batch
+    const long long groups = (na + dots1_ig(cplx) - 1) / dots1_ig(cplx);
+    const long long want = std::max<long long>(1, (2LL * sm_count + groups * P - 1) / (groups * P));
+    long long rows = (b_nmax + want - 1) / want;
+    rows = std::min<long long>(8192, std::max<long long>(256, (rows + 255) / 256 * 256));
+    while ((b_nmax + rows - 1) / rows > 65535) rows *= 2;
+    const long long nchunks = (b_nmax + rows - 1) / rows;
     const long long pps = nchunks * na;
     omen_status s1 = ensure_partial((size_t)pps * P);
     if (s1 != OMEN_OK) return s1;
-    dim3 grid((na + kIG - 1) / kIG, (unsigned)nchunks, P);
-    if (prec == OMEN_F64) {
-      if (cplx) dots1_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, n, rows, d_partial, n, n, pps);
-      else dots1_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, n, rows, d_partial, n, n, pps);
-    } else {
-      if (cplx) dots1_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, n, rows, d_partial, n, n, pps);
-      else dots1_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, n, rows, d_partial, n, n, pps);
-    }
+    dim3 grid((unsigned)groups, (unsigned)nchunks, P);
+#define DOTSB(T, Cc) \
+  dots1_kernel<T, Cc><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, b_nmax, (int)rows, d_partial, 0, 0, pps, b_off, b_len, b_act)
+    if (prec == OMEN_F64) { if (cplx) DOTSB(double, true); else DOTSB(double, false); }
+    else { if (cplx) DOTSB(float, true); else DOTSB(float, false); }
+#undef DOTSB
     reduce_dev_kernel<<<dim3(na, P), 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, 1, out_dev, accT, ldT, col0, pps,
-                                                            out_ps, t_ps);
+                                                            out_ps, t_ps, b_act);
     OMEN_CHECK_LAUNCH(ctx);
     return OMEN_OK;
   }
@@ -870,12 +1001,12 @@ struct KrylovOps {
   omen_status combine_dev_batch(int P, const void* A, long long lda, int na, const double2* M_dev, long long m_ps, void* Y,
                                 double alpha, double beta) {
     const size_t shm1 = (size_t)na * sizeof(double2);
-    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)sm_count * 8 / std::max(1, P) + 1));
+    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((b_nmax + 255) / 256, (long long)sm_count * 8 / std::max(1, P) + 1));
     dim3 grid(gx, P);
 #define COMB1B(T, Cc)                                                                                 \
   do {                                                                                                \
     smem_limit(combine1_kernel<T, Cc>, shm1);                                                         \
-    combine1_kernel<T, Cc><<<grid, 256, shm1, ctx->stream>>>(A, lda, na, M_dev, Y, n, alpha, beta, n, m_ps, n); \
+    combine1_kernel<T, Cc><<<grid, 256, shm1, ctx->stream>>>(A, lda, na, M_dev, Y, b_nmax, alpha, beta, 0, m_ps, 0, b_off, b_len, b_act); \
   } while (0)
     if (prec == OMEN_F64) { if (cplx) COMB1B(double, true); else COMB1B(double, false); }
     else { if (cplx) COMB1B(float, true); else COMB1B(float, false); }
@@ -886,16 +1017,14 @@ struct KrylovOps {
 
   omen_status normalize_dev_batch(int P, const void* W, void* Vo, const double2* nrm2, double2* Tm, int ldT,
                                   long long t_ps, int row, int col) {
-    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)sm_count * 8 / std::max(1, P) + 1));
+    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((b_nmax + 255) / 256, (long long)sm_count * 8 / std::max(1, P) + 1));
     dim3 grid(gx, P);
     int* flag = ctx->d_status + 1;
-    if (prec == OMEN_F64) {
-      if (cplx) normalize_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(W, Vo, n, nrm2, Tm, ldT, row, col, flag, n, n, 1, t_ps);
-      else normalize_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(W, Vo, n, nrm2, Tm, ldT, row, col, flag, n, n, 1, t_ps);
-    } else {
-      if (cplx) normalize_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(W, Vo, n, nrm2, Tm, ldT, row, col, flag, n, n, 1, t_ps);
-      else normalize_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(W, Vo, n, nrm2, Tm, ldT, row, col, flag, n, n, 1, t_ps);
-    }
+#define NORMB(T, Cc) \
+  normalize_kernel<T, Cc><<<grid, 256, 0, ctx->stream>>>(W, Vo, b_nmax, nrm2, Tm, ldT, row, col, flag, 0, 0, 1, t_ps, b_off, b_len, b_act)
+    if (prec == OMEN_F64) { if (cplx) NORMB(double, true); else NORMB(double, false); }
+    else { if (cplx) NORMB(float, true); else NORMB(float, false); }
+#undef NORMB
     OMEN_CHECK_LAUNCH(ctx);
     return OMEN_OK;
   }
@@ -1391,6 +1520,7 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   bool fresh = true;   // first step of a cycle: the new vector couples to every kept vector
   // One step on the device: W = A v_js, orthogonalise W against v_0..v_{nb-1} (T column js),
   // v_nb = W / ||W|| (T[nb, js] = ||W||).  No host synchronisation.
+  const bool semi = ctx->reorth == OMEN_REORTH_SEMI;
   auto enqueue_step = [&](int js, int nb, bool fr) -> omen_status {
     long long unused = 0;
     omen_status s2 = op.apply(op.col(V, js), W, tmp, 1, folded, o->sigma, unused);
@@ -1401,17 +1531,25 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
         s2 = op.dots_dev(V, nb, W, 1, dh, dT, ldT, js);
         if (s2 == OMEN_OK) s2 = op.combine_dev(V, nb, dh, 1, W, -1.0, 1.0);
       }
+      if (s2 == OMEN_OK && semi) s2 = op.force_next_pass((js + 1) & 1);
     } else {
       // three-term step against v_j (alpha) and v_{j-1} (beta, already in T), then one full
-      // pass that removes what rounding left along every basis vector
+      // pass that removes what rounding left along every basis vector (under the
+      // semi-orthogonality policy: only when the measured overlaps call for it)
       s2 = op.dots_dev(op.col(V, js), 1, W, 1, dh, dT + js, ldT, js);
       if (s2 == OMEN_OK) s2 = op.combine_dev(op.col(V, js), 1, dh, 1, W, -1.0, 1.0);
       if (s2 == OMEN_OK) s2 = op.combine_dev(op.col(V, js - 1), 1, dT + js + (size_t)(js - 1) * ldT, 1, W, -1.0, 1.0);
       if (s2 != OMEN_OK) return s2;
       OMEN_CUDA(ctx, cudaMemcpyAsync(dT + (js - 1) + (size_t)js * ldT, dT + js + (size_t)(js - 1) * ldT,
                                      sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
-      s2 = op.dots_dev(V, nb, W, 1, dh, dT, ldT, js);
-      if (s2 == OMEN_OK) s2 = op.combine_dev(V, nb, dh, 1, W, -1.0, 1.0);
+      if (semi) {
+        s2 = op.dots_dev(V, nb, W, 1, dh, nullptr, 0, 0);
+        if (s2 == OMEN_OK) s2 = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
+        if (s2 == OMEN_OK) s2 = op.combine_gated(V, nb, dh, W, dn, js & 1, dT + (size_t)js * ldT);
+      } else {
+        s2 = op.dots_dev(V, nb, W, 1, dh, dT, ldT, js);
+        if (s2 == OMEN_OK) s2 = op.combine_dev(V, nb, dh, 1, W, -1.0, 1.0);
+      }
     }
     if (s2 == OMEN_OK) s2 = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
     if (s2 == OMEN_OK) s2 = op.normalize_dev(W, op.col(V, nb), dn, dT, ldT, nb, js);
@@ -1426,9 +1564,7 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   const bool use_graphs = ctx->use_graphs && !op.negate;
   if (use_graphs) {
     // the partial-sum buffer must not move under a captured graph: size it for the widest pass
-    int rows = 8192;
-    while ((op.n + rows - 1) / rows > 65535) rows *= 2;
-    s = op.ensure_partial((size_t)((op.n + rows - 1) / rows) * (m + 1));
+    s = op.ensure_partial(op.max_partials(m + 1));
     if (s != OMEN_OK) return s;
   }
   while (true) {
@@ -1820,40 +1956,136 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
 // out [basis vector][k][row], so the current Lanczos vectors of all k are contiguous.
 // Convergence (checked per k on the host): LOWEST - the Weyl / Kato–Temple bound on the Ritz
 // values; NEAREST - the H residual estimated from the folded residual, r_A / (2 sqrt(theta)).
-extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int nk, const double* k_host,
-                                        const omen_eig_opts* o, double* evals_host, void* evecs_dev,
-                                        omen_eig_info* info) {
-  if (!ctx || !ham || !k_host || !o || !evals_host || nk < 1) return set_err(ctx, OMEN_EINVAL, "null argument or nk < 1");
-  if (!ham->bloch || ham->spin_orbit || ham->matrix_free) return set_err(ctx, OMEN_EINVAL, "k batch needs a Bloch Hamiltonian with stored blocks and no spin-orbit");
-  if (ham->precision == OMEN_F32_REFINE64) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs in F64 or F32");
+// ---- k-batched lockstep Lanczos over several structures ------------------------------------
+// Every (structure, wave vector) pair is an independent problem p with its own basis, T matrix
+// and convergence test; all of them advance one step per iteration, their H·X in one launch
+// over the (structure, k) work list and their projections, updates and normalisations in one
+// launch each (blockIdx over problems).  A vector slot holds every problem's vector: problem p
+// at element off[p], len[p] = its structure's row count, structures in the given order and
+// their wave vectors in order within each.
+struct KbatchInput {
+  const omen_ham* ham;
+  int nk;
+  const double* k_host;
+};
+
+namespace {
+struct PhaseTables {
+  omen_ctx* ctx;
+  std::vector<double2*> p;
+  ~PhaseTables() {
+    for (double2* q : p)
+      if (q) cudaFreeAsync(q, ctx->stream);
+  }
+};
+struct OpsGuard {
+  KrylovOps& op;
+  ~OpsGuard() { op.release(); }
+};
+}  // namespace
+
+// Deflation and stopping rule of one lockstep run: Lanczos on the operator with the nlock
+// vectors of X (slots, the batch layout) projected out after every product; a problem also
+// counts as done once its lowest Ritz value minus its residual exceeds stop_above[p] (no
+// eigenvalue of the deflated operator lies below that line).
+struct KLock {
+  const void* X = nullptr;
+  int n = 0;
+  const std::vector<double>* stop_above = nullptr;
+  const std::vector<char>* only = nullptr;   // run just these problems (the others count as done)
+  unsigned long long seed = 0x5EEDull;
+};
+// Results of one run: the nev Ritz vectors of every problem in ascending order (slots of Xout),
+// their Rayleigh quotients and residual norms [p][nev], and per-problem convergence.
+struct KOut {
+  void* Xout = nullptr;
+  std::vector<double> lam, res;
+  std::vector<char> conv;
+  int iterations = 0, restarts = 0;
+  long long hx = 0;
+};
+
+static omen_status kbatch_core(omen_ctx* ctx, const std::vector<KbatchInput>& in, const omen_eig_opts* o, int nev,
+                               const KLock& lock, KOut& out) {
+  if (!ctx) return OMEN_EINVAL;
+  if (!o || in.empty() || (int)in.size() > 16) return set_err(ctx, OMEN_EINVAL, "null argument or 1..16 structures");
+  const omen_ham* h0 = in[0].ham;
+  for (size_t i = 0; i < in.size(); ++i) {
+    const omen_ham* h = in[i].ham;
+    if (!h || !in[i].k_host || in[i].nk < 1) return set_err(ctx, OMEN_EINVAL, "structure %zu: null argument or nk < 1", i);
+    if (!h->bloch || h->spin_orbit || h->matrix_free)
+      return set_err(ctx, OMEN_EINVAL, "k batch needs Bloch Hamiltonians with stored blocks and no spin-orbit");
+    if (h->precision == OMEN_F32_REFINE64) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs in F64 or F32");
+    if (h->precision != h0->precision || h->norb != h0->norb)
+      return set_err(ctx, OMEN_EINVAL, "structures of one k batch share precision and basis");
+    if ((long long)o->basis + 1 > h->nrows) return set_err(ctx, OMEN_EINVAL, "basis larger than structure %zu", i);
+  }
   if (o->block != 1) return set_err(ctx, OMEN_EINVAL, "k batch uses block size 1");
   if (o->which != OMEN_LOWEST && o->which != OMEN_NEAREST) return set_err(ctx, OMEN_EINVAL, "which must be LOWEST or NEAREST");
-  if (o->nev < 1 || o->basis < o->nev + 2 || o->basis > 2048 || !(o->tol > 0) || o->max_iter < o->nev)
+  if (nev < 1 || o->basis < nev + 2 || o->basis > 2048 || !(o->tol > 0) || o->max_iter < nev)
     return set_err(ctx, OMEN_EINVAL, "invalid eigen options");
-  if ((long long)o->basis + 1 > ham->nrows) return set_err(ctx, OMEN_EINVAL, "basis larger than the problem");
   OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
-  auto t0 = std::chrono::steady_clock::now();
-  const int P = nk, m = o->basis, ldT = m + 1, nev = o->nev;
+  const int m = o->basis, ldT = m + 1;
   const bool folded = o->which == OMEN_NEAREST;
-  const int prec = ham->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64;
-  KrylovOps op{ctx, ham, prec, true, ham->nrows};
+  const int prec = h0->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64;
+  // problems
+  std::vector<long long> off, len;
+  std::vector<KItem> items(in.size());
+  long long Ntot = 0, nmax = 0;
+  for (size_t i = 0; i < in.size(); ++i) {
+    items[i] = KItem{in[i].ham, in[i].nk, nullptr, Ntot};
+    for (int q = 0; q < in[i].nk; ++q) {
+      off.push_back(Ntot);
+      len.push_back(in[i].ham->nrows);
+      Ntot += in[i].ham->nrows;
+    }
+    nmax = std::max(nmax, in[i].ham->nrows);
+  }
+  const int P = (int)off.size();
+  KrylovOps op{ctx, h0, prec, true, Ntot};
   omen_status s = op.init();
   if (s != OMEN_OK) return s;
-  const long long n = ham->nrows;
-  const size_t vb = (size_t)n * op.el;               // one vector
-  const size_t blk = vb * P;                          // one basis slot for all k
-  double2* ph = nullptr;
-  s = make_phases(ctx, ham, nk, k_host, &ph);
-  if (s != OMEN_OK) { op.release(); return s; }
-  DevBuf Vb, Wb, Tb, Xb, Td, Hd;
+  OpsGuard og{op};
+  PhaseTables pt{ctx, std::vector<double2*>(in.size(), nullptr)};
+  for (size_t i = 0; i < in.size(); ++i) {
+    s = make_phases(ctx, in[i].ham, in[i].nk, in[i].k_host, &pt.p[i]);
+    if (s != OMEN_OK) return s;
+    items[i].phases = pt.p[i];
+  }
+  const size_t blk = (size_t)Ntot * op.el;   // one slot: every problem's vector
+  DevBuf Vb, Wb, Tb, Xb, Xf, Td, Hd, Ob, Lk;
   if (cudaMalloc(&Vb.p, (size_t)(m + 1) * blk) != cudaSuccess || cudaMalloc(&Wb.p, blk) != cudaSuccess ||
       cudaMalloc(&Tb.p, blk) != cudaSuccess || cudaMalloc(&Xb.p, (size_t)m * blk) != cudaSuccess ||
+      cudaMalloc(&Xf.p, (size_t)nev * blk) != cudaSuccess ||
       cudaMalloc(&Td.p, sizeof(double2) * ldT * ldT * P) != cudaSuccess ||
-      cudaMalloc(&Hd.p, sizeof(double2) * (ldT + 1) * P) != cudaSuccess) {
+      cudaMalloc(&Hd.p, sizeof(double2) * (ldT + 1) * P) != cudaSuccess ||
+      cudaMalloc(&Ob.p, sizeof(long long) * 3 * P) != cudaSuccess ||
+      cudaMalloc(&Lk.p, sizeof(double2) * (size_t)P * std::max(1, lock.n)) != cudaSuccess) {
     cudaGetLastError();
-    cudaFreeAsync(ph, ctx->stream);
-    op.release();
-    return set_err(ctx, OMEN_ENOMEM, "k-batched Lanczos basis (%d x %d vectors of %lld rows)", m + 1, P, n);
+    return set_err(ctx, OMEN_ENOMEM, "k-batched Lanczos basis (%d slots of %lld elements)", m + 1, Ntot);
+  }
+  long long* d_off = static_cast<long long*>(Ob.p);
+  OMEN_CUDA(ctx, cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * P, cudaMemcpyHostToDevice, ctx->stream));
+  OMEN_CUDA(ctx, cudaMemcpyAsync(d_off + P, len.data(), sizeof(long long) * P, cudaMemcpyHostToDevice, ctx->stream));
+  int* d_act = reinterpret_cast<int*>(d_off + 2 * P);
+  double2* d_lk = static_cast<double2*>(Lk.p);   // projections onto the locked vectors
+  std::vector<int> act(P, 1);
+  if (lock.only)
+    for (int p = 0; p < P; ++p) act[p] = (*lock.only)[p] ? 1 : 0;
+  OMEN_CUDA(ctx, cudaMemcpyAsync(d_act, act.data(), sizeof(int) * P, cudaMemcpyHostToDevice, ctx->stream));
+  op.b_off = d_off;
+  op.b_len = d_off + P;
+  op.b_act = d_act;
+  op.b_nmax = nmax;
+  // problem -> structure, and the structures that still have an unconverged problem
+  std::vector<int> owner;
+  for (size_t i = 0; i < in.size(); ++i)
+    for (int q = 0; q < in[i].nk; ++q) owner.push_back((int)i);
+  std::vector<KItem> live;
+  for (size_t i = 0; i < items.size(); ++i) {
+    bool any = false;
+    for (int p = 0; p < P; ++p) any = any || (owner[p] == (int)i && act[p]);
+    if (any) live.push_back(items[i]);
   }
   char* V = static_cast<char*>(Vb.p);
   auto slot = [&](int j) { return V + (size_t)j * blk; };
@@ -1861,27 +2093,84 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
   double2* dh = static_cast<double2*>(Hd.p);
   double2* dn = dh + (size_t)ldT * P;
   const long long tps = (long long)ldT * ldT;
-  const long long lda = (long long)P * n;   // stride between basis vectors of one problem
+  const long long lda = Ntot;   // stride between basis slots
   OMEN_CUDA(ctx, cudaMemsetAsync(dT, 0, sizeof(double2) * tps * P, ctx->stream));
   OMEN_CUDA(ctx, cudaMemsetAsync(ctx->d_status + 1, 0, sizeof(int), ctx->stream));
   long long hx = 0;
-  auto apply = [&](const void* X, void* Y) -> omen_status {
-    if (!folded) { hx += P; return launch_hx_kbatch(ctx, ham, P, ph, X, Y, 0.0, prec); }
-    omen_status s2 = launch_hx_kbatch(ctx, ham, P, ph, X, Tb.p, o->sigma, prec);
-    if (s2 != OMEN_OK) return s2;
-    hx += 2 * P;
-    return launch_hx_kbatch(ctx, ham, P, ph, Tb.p, Y, o->sigma, prec);
+  const int nitems = (int)items.size();
+  int nactive = 0;
+  for (int p = 0; p < P; ++p) nactive += act[p];
+  // y -= X_lock (X_lock^H y) for every problem
+  auto deflate = [&](void* Y) -> omen_status {
+    if (lock.n == 0) return OMEN_OK;
+    omen_status s2 = op.dots_dev_batch(P, lock.X, lda, lock.n, Y, d_lk, lock.n, nullptr, 0, 0, 0);
+    if (s2 == OMEN_OK) s2 = op.combine_dev_batch(P, lock.X, lda, lock.n, d_lk, lock.n, Y, -1.0, 1.0);
+    return s2;
   };
-  if (o->v0_dev) OMEN_CUDA(ctx, cudaMemcpyAsync(Wb.p, o->v0_dev, blk, cudaMemcpyDeviceToDevice, ctx->stream));
-  else if ((s = op.random_fill(Wb.p, P, 0x5EEDull)) != OMEN_OK) return s;
-  s = op.dots_dev_batch(P, Wb.p, n, 1, Wb.p, dn, 1, nullptr, 0, 0, 0);
+  auto apply = [&](const void* X, void* Y) -> omen_status {
+    const int nl = (int)live.size();
+    omen_status s2;
+    if (!folded) {
+      hx += nactive;
+      s2 = launch_hx_kmulti(ctx, live.data(), nl, X, Y, 0.0, prec);
+      return s2 == OMEN_OK ? deflate(Y) : s2;
+    }
+    s2 = launch_hx_kmulti(ctx, live.data(), nl, X, Tb.p, o->sigma, prec);
+    if (s2 == OMEN_OK) s2 = deflate(Tb.p);
+    if (s2 != OMEN_OK) return s2;
+    hx += 2 * nactive;
+    s2 = launch_hx_kmulti(ctx, live.data(), nl, Tb.p, Y, o->sigma, prec);
+    return s2 == OMEN_OK ? deflate(Y) : s2;
+  };
+  if (o->v0_dev && lock.n == 0) OMEN_CUDA(ctx, cudaMemcpyAsync(Wb.p, o->v0_dev, blk, cudaMemcpyDeviceToDevice, ctx->stream));
+  else if ((s = op.random_fill(Wb.p, 1, lock.seed)) != OMEN_OK) return s;
+  for (int pass = 0; pass < 2 && s == OMEN_OK; ++pass) s = deflate(Wb.p);
+  if (s == OMEN_OK) s = op.dots_dev_batch(P, Wb.p, lda, 1, Wb.p, dn, 1, nullptr, 0, 0, 0);
   if (s == OMEN_OK) s = op.normalize_dev_batch(P, Wb.p, slot(0), dn, nullptr, 0, 0, 0, 0);
-  if (s != OMEN_OK) { cudaFreeAsync(ph, ctx->stream); op.release(); return s; }
+  if (s != OMEN_OK) return s;
+
+  // problem p's basis vectors i0.. combined by its coefficients M (nbas x nbj) into slots j0.. of Out
+  auto combine_problem = [&](int p, int nbas, const std::vector<cd>& M, int nbj, char* Out, int j0) -> omen_status {
+    OMEN_CUDA(ctx, cudaMemcpyAsync(op.d_small, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
+    const size_t shm = M.size() * sizeof(double2);
+    const long long n = len[p];
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)op.sm_count * 8);
+    char* Yout = Out + (size_t)j0 * blk + (size_t)off[p] * op.el;
+    const char* Ain = V + (size_t)off[p] * op.el;
+    if (prec == OMEN_F64) {
+      smem_limit(combine_kernel<double, true>, shm);
+      combine_kernel<double, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
+    } else {
+      smem_limit(combine_kernel<float, true>, shm);
+      combine_kernel<float, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
+    }
+    OMEN_CHECK_LAUNCH(ctx);
+    // the small buffer is reused by the next call
+    OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return OMEN_OK;
+  };
 
   std::vector<cd> Th((size_t)tps * P);
   std::vector<std::vector<double>> theta(P);
   std::vector<std::vector<cd>> Y(P);
-  std::vector<char> conv(P, 0);
+  std::vector<char> conv(P, 0), frozen(P, 0);
+  for (int p = 0; p < P; ++p)
+    if (!act[p]) conv[p] = frozen[p] = 1;
+  // a converged problem is frozen: its nev Ritz vectors go to Xf and it drops out of every
+  // later launch (its structure's H·X too, once all of that structure's problems are frozen)
+  auto freeze = [&](int p, int nb) -> omen_status {
+    for (int j0 = 0; j0 < nev; j0 += kMaxBlockCols) {
+      const int nbj = std::min(kMaxBlockCols, nev - j0);
+      std::vector<cd> M((size_t)nb * nbj);
+      for (int j = 0; j < nbj; ++j)
+        for (int i = 0; i < nb; ++i) M[i + (size_t)j * nb] = Y[p][i + (size_t)(j0 + j) * nb];
+      omen_status s2 = combine_problem(p, nb, M, nbj, static_cast<char*>(Xf.p), j0);
+      if (s2 != OMEN_OK) return s2;
+    }
+    frozen[p] = 1;
+    act[p] = 0;
+    return OMEN_OK;
+  };
   int jstart = 0, nbas = 1, iter = 0, restarts = 0, since = 0;
   const int check_every = std::max(8, m / 2);
   bool fresh = true;   // first step of a cycle: the new vector couples to every kept vector
@@ -1907,9 +2196,9 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
       if (s == OMEN_OK) s = op.dots_dev_batch(P, V, lda, nbas, Wb.p, dh, ldT, dT, ldT, tps, jstart);
       if (s == OMEN_OK) s = op.combine_dev_batch(P, V, lda, nbas, dh, ldT, Wb.p, -1.0, 1.0);
     }
-    if (s == OMEN_OK) s = op.dots_dev_batch(P, Wb.p, n, 1, Wb.p, dn, 1, nullptr, 0, 0, 0);
+    if (s == OMEN_OK) s = op.dots_dev_batch(P, Wb.p, lda, 1, Wb.p, dn, 1, nullptr, 0, 0, 0);
     if (s == OMEN_OK) s = op.normalize_dev_batch(P, Wb.p, slot(nbas), dn, dT, ldT, tps, nbas, jstart);
-    if (s != OMEN_OK) break;
+    if (s != OMEN_OK) return s;
     ++iter;
     ++since;
     const bool full = nbas + 1 > m;
@@ -1923,13 +2212,13 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
     int flag = 0;
     OMEN_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->d_status + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (flag) { s = set_err(ctx, OMEN_ENUMERIC, "Lanczos breakdown or non-finite value in the k batch"); break; }
-    bool all = true;
+    if (flag) return set_err(ctx, OMEN_ENUMERIC, "Lanczos breakdown or non-finite value in the k batch");
     std::vector<double> betas(P);
     std::vector<int> bad(P, 0);
     // the P projected eigenproblems are independent: one host thread each
 #pragma omp parallel for schedule(dynamic)
     for (int p = 0; p < P; ++p) {
+      if (frozen[p]) continue;
       const cd* T = Th.data() + (size_t)p * tps;
       std::vector<cd> Tn((size_t)nbas * nbas);
       for (int j = 0; j < nbas; ++j)
@@ -1955,38 +2244,39 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
         error_bounds(theta[p], lam, res, bd);
       }
       conv[p] = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+      // nothing of the deflated operator below the line: done (Weyl: an eigenvalue lies
+      // within the residual of the lowest Ritz value, and Lanczos finds the lowest first)
+      if (lock.stop_above && !folded && theta[p][0] - res[0] > (*lock.stop_above)[p]) conv[p] = 1;
     }
+    bool all = true;
     for (int p = 0; p < P; ++p) {
-      if (bad[p]) s = set_err(ctx, OMEN_ENUMERIC, "projected eigenproblem of k %d did not converge", p);
+      if (bad[p]) return set_err(ctx, OMEN_ENUMERIC, "projected eigenproblem of problem %d did not converge", p);
+      if (!frozen[p] && (conv[p] || iter >= o->max_iter) && (s = freeze(p, nbas)) != OMEN_OK) return s;
       all = all && conv[p];
     }
-    if (s != OMEN_OK) break;
     if (all || iter >= o->max_iter) break;
+    // drop frozen problems (and structures with nothing left) from the launches
+    nactive = 0;
+    live.clear();
+    for (int p = 0; p < P; ++p) nactive += act[p];
+    for (int i = 0; i < nitems; ++i) {
+      bool any = false;
+      for (int p = 0; p < P; ++p) any = any || (owner[p] == i && act[p]);
+      if (any) live.push_back(items[i]);
+    }
+    OMEN_CUDA(ctx, cudaMemcpyAsync(d_act, act.data(), sizeof(int) * P, cudaMemcpyHostToDevice, ctx->stream));
     if (full) {
       const int kk = std::min(m - 1, std::max(nev + 1, nbas / 2));
-      for (int p = 0; p < P && s == OMEN_OK; ++p) {
+      for (int p = 0; p < P; ++p) {
+        if (frozen[p]) continue;
         for (int j0 = 0; j0 < kk; j0 += kMaxBlockCols) {
           const int nbj = std::min(kMaxBlockCols, kk - j0);
           std::vector<cd> M((size_t)nbas * nbj);
           for (int j = 0; j < nbj; ++j)
             for (int i = 0; i < nbas; ++i) M[i + (size_t)j * nbas] = Y[p][i + (size_t)(j0 + j) * nbas];
-          OMEN_CUDA(ctx, cudaMemcpyAsync(op.d_small, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
-          const size_t shm = M.size() * sizeof(double2);
-          const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)op.sm_count * 8);
-          char* Yout = static_cast<char*>(Xb.p) + (size_t)j0 * blk + (size_t)p * vb;
-          const char* Ain = V + (size_t)p * vb;
-          if (prec == OMEN_F64) {
-            smem_limit(combine_kernel<double, true>, shm);
-            combine_kernel<double, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
-          } else {
-            smem_limit(combine_kernel<float, true>, shm);
-            combine_kernel<float, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
-          }
-          OMEN_CHECK_LAUNCH(ctx);
-          OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+          if ((s = combine_problem(p, nbas, M, nbj, static_cast<char*>(Xb.p), j0)) != OMEN_OK) return s;
         }
       }
-      if (s != OMEN_OK) break;
       OMEN_CUDA(ctx, cudaMemcpyAsync(V, Xb.p, (size_t)kk * blk, cudaMemcpyDeviceToDevice, ctx->stream));
       OMEN_CUDA(ctx, cudaMemcpyAsync(slot(kk), slot(nbas), blk, cudaMemcpyDeviceToDevice, ctx->stream));
       std::fill(Th.begin(), Th.end(), cd(0));
@@ -2006,92 +2296,174 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
     jstart = nbas;
     nbas += 1;
   }
-  if (s != OMEN_OK) { cudaFreeAsync(ph, ctx->stream); op.release(); return s; }
-  // Ritz vectors (nev per k) into Xb with layout [i][k][row], then H X and Rayleigh quotients
-  for (int p = 0; p < P && s == OMEN_OK; ++p)
-    for (int j0 = 0; j0 < nev; j0 += kMaxBlockCols) {
-      const int nbj = std::min(kMaxBlockCols, nev - j0);
-      std::vector<cd> M((size_t)nbas * nbj);
-      for (int j = 0; j < nbj; ++j)
-        for (int i = 0; i < nbas; ++i) M[i + (size_t)j * nbas] = Y[p][i + (size_t)(j0 + j) * nbas];
-      OMEN_CUDA(ctx, cudaMemcpyAsync(op.d_small, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
-      const size_t shm = M.size() * sizeof(double2);
-      const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)op.sm_count * 8);
-      char* Yout = static_cast<char*>(Xb.p) + (size_t)j0 * blk + (size_t)p * vb;
-      const char* Ain = V + (size_t)p * vb;
-      if (prec == OMEN_F64) {
-        smem_limit(combine_kernel<double, true>, shm);
-        combine_kernel<double, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
-      } else {
-        smem_limit(combine_kernel<float, true>, shm);
-        combine_kernel<float, true><<<grid, 256, shm, ctx->stream>>>(Ain, lda, nbas, op.d_small, nbj, Yout, lda, n, 1.0, 0.0);
-      }
-      OMEN_CHECK_LAUNCH(ctx);
-      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    }
-  // evaluate: lam = <x,Hx>/<x,x>, r = ||Hx - lam x|| / ||x||
+  // every problem is frozen now: its Ritz vectors are in slots 0..nev-1 of Xf.
+  // evaluate all of them: lam = <x,Hx>/<x,x>, r = ||Hx - lam x|| / ||x||
+  op.b_act = nullptr;
   std::vector<double> lam((size_t)P * nev), res((size_t)P * nev);
   double2* dq = dh;  // reuse: P values
   std::vector<double2> hq(P), hn(P), hr(P);
-  for (int i = 0; i < nev && s == OMEN_OK; ++i) {
-    char* Xi = static_cast<char*>(Xb.p) + (size_t)i * blk;
-    s = launch_hx_kbatch(ctx, ham, P, ph, Xi, Wb.p, 0.0, prec);
+  for (int i = 0; i < nev; ++i) {
+    char* Xi = static_cast<char*>(Xf.p) + (size_t)i * blk;
+    s = launch_hx_kmulti(ctx, items.data(), nitems, Xi, Wb.p, 0.0, prec);
     hx += P;
-    if (s == OMEN_OK) s = op.dots_dev_batch(P, Xi, n, 1, Wb.p, dq, 1, nullptr, 0, 0, 0);
-    if (s == OMEN_OK) {
-      OMEN_CUDA(ctx, cudaMemcpyAsync(hq.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
-      s = op.dots_dev_batch(P, Xi, n, 1, Xi, dq, 1, nullptr, 0, 0, 0);
+    if (s == OMEN_OK) s = op.dots_dev_batch(P, Xi, lda, 1, Wb.p, dq, 1, nullptr, 0, 0, 0);
+    if (s != OMEN_OK) return s;
+    OMEN_CUDA(ctx, cudaMemcpyAsync(hq.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
+    if ((s = op.dots_dev_batch(P, Xi, lda, 1, Xi, dq, 1, nullptr, 0, 0, 0)) != OMEN_OK) return s;
+    OMEN_CUDA(ctx, cudaMemcpyAsync(hn.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
+    OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<double2> mlam(P);
+    for (int p = 0; p < P; ++p) {
+      lam[(size_t)p * nev + i] = hq[p].x / hn[p].x;
+      mlam[p] = make_double2(lam[(size_t)p * nev + i], 0.0);
     }
-    if (s == OMEN_OK) {
-      OMEN_CUDA(ctx, cudaMemcpyAsync(hn.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
-      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      std::vector<double2> mlam(P);
-      for (int p = 0; p < P; ++p) {
-        lam[(size_t)p * nev + i] = hq[p].x / hn[p].x;
-        mlam[p] = make_double2(lam[(size_t)p * nev + i], 0.0);
-      }
-      OMEN_CUDA(ctx, cudaMemcpyAsync(dq, mlam.data(), sizeof(double2) * P, cudaMemcpyHostToDevice, ctx->stream));
-      s = op.combine_dev_batch(P, Xi, n, 1, dq, 1, Wb.p, -1.0, 1.0);  // W = HX - lam X
-    }
-    if (s == OMEN_OK) s = op.dots_dev_batch(P, Wb.p, n, 1, Wb.p, dq, 1, nullptr, 0, 0, 0);
-    if (s == OMEN_OK) {
-      OMEN_CUDA(ctx, cudaMemcpyAsync(hr.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
-      OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      for (int p = 0; p < P; ++p) res[(size_t)p * nev + i] = std::sqrt(std::max(0.0, hr[p].x) / hn[p].x);
-    }
+    OMEN_CUDA(ctx, cudaMemcpyAsync(dq, mlam.data(), sizeof(double2) * P, cudaMemcpyHostToDevice, ctx->stream));
+    if ((s = op.combine_dev_batch(P, Xi, lda, 1, dq, 1, Wb.p, -1.0, 1.0)) != OMEN_OK) return s;  // W = HX - lam X
+    if ((s = op.dots_dev_batch(P, Wb.p, lda, 1, Wb.p, dq, 1, nullptr, 0, 0, 0)) != OMEN_OK) return s;
+    OMEN_CUDA(ctx, cudaMemcpyAsync(hr.data(), dq, sizeof(double2) * P, cudaMemcpyDeviceToHost, ctx->stream));
+    OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int p = 0; p < P; ++p) res[(size_t)p * nev + i] = std::sqrt(std::max(0.0, hr[p].x) / hn[p].x);
   }
-  double maxres = 0.0, maxbd = 0.0;
-  for (int p = 0; p < P && s == OMEN_OK; ++p) {
+  // ascending order per problem: values into out.lam / out.res, vectors into the slots of Xout
+  out.lam.assign((size_t)P * nev, 0.0);
+  out.res.assign((size_t)P * nev, 0.0);
+  for (int p = 0; p < P; ++p) {
     std::vector<int> ord(nev);
     for (int i = 0; i < nev; ++i) ord[i] = i;
     std::sort(ord.begin(), ord.end(), [&](int a, int b) { return lam[(size_t)p * nev + a] < lam[(size_t)p * nev + b]; });
-    std::vector<double> lp(nev), rp(nev), bd;
     for (int i = 0; i < nev; ++i) {
-      lp[i] = lam[(size_t)p * nev + ord[i]];
-      rp[i] = res[(size_t)p * nev + ord[i]];
-      evals_host[(size_t)p * nev + i] = lp[i];
+      out.lam[(size_t)p * nev + i] = lam[(size_t)p * nev + ord[i]];
+      out.res[(size_t)p * nev + i] = res[(size_t)p * nev + ord[i]];
+      OMEN_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(out.Xout) + (size_t)i * blk + (size_t)off[p] * op.el,
+                                     static_cast<char*>(Xf.p) + (size_t)ord[i] * blk + (size_t)off[p] * op.el,
+                                     (size_t)len[p] * op.el, cudaMemcpyDeviceToDevice, ctx->stream));
     }
+  }
+  OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  out.conv = conv;
+  out.iterations = iter;
+  out.restarts = restarts;
+  out.hx = hx;
+  return OMEN_OK;
+}
+
+// The lockstep solve, then (lowest eigenvalues) a check for eigenvalues it missed.  A
+// single-vector Krylov space holds one direction of each eigenspace, so of a degenerate pair —
+// common in symmetric supercells, e.g. every band at the zone boundary of a Bloch axis — it finds
+// one copy and may report the next eigenvalue in place of the other.  The check runs the
+// lockstep solver again for the lowest eigenvalue of each problem's operator with its current
+// nev vectors projected out (locking), from a new start vector; where that eigenvalue lies below
+// the current nev-th by more than the tolerance, it is inserted in order and the last one
+// dropped.  Repeated until no problem changes (at most nev rounds).
+static omen_status kbatch_solve(omen_ctx* ctx, const std::vector<KbatchInput>& in, const omen_eig_opts* o,
+                                double* evals_host, void* evecs_dev, omen_eig_info* info) {
+  if (!ctx) return OMEN_EINVAL;
+  if (!o || !evals_host || in.empty()) return set_err(ctx, OMEN_EINVAL, "null argument or no structures");
+  auto t0 = std::chrono::steady_clock::now();
+  const int nev = o->nev;
+  std::vector<long long> off, len;
+  long long Ntot = 0;
+  for (const KbatchInput& it : in) {
+    if (!it.ham || it.nk < 1) return set_err(ctx, OMEN_EINVAL, "null Hamiltonian or nk < 1");
+    for (int q = 0; q < it.nk; ++q) {
+      off.push_back(Ntot);
+      len.push_back(it.ham->nrows);
+      Ntot += it.ham->nrows;
+    }
+  }
+  const int P = (int)off.size();
+  const size_t el = vec_elem_bytes(in[0].ham, in[0].ham->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64);
+  const size_t blk = (size_t)Ntot * el;
+  DevBuf X, Z;
+  if (cudaMalloc(&X.p, (size_t)std::max(1, nev) * blk) != cudaSuccess || cudaMalloc(&Z.p, blk) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(ctx, OMEN_ENOMEM, "k-batch eigenvectors (%d slots of %lld elements)", nev + 1, Ntot);
+  }
+  KOut main;
+  main.Xout = X.p;
+  omen_status s = kbatch_core(ctx, in, o, nev, KLock{}, main);
+  if (s != OMEN_OK) return s;
+  int iters = main.iterations, restarts = main.restarts, rounds = 0, inserted = 0;
+  long long hx = main.hx;
+  std::vector<char> conv = main.conv;
+  if (o->which == OMEN_LOWEST) {
+    const double margin = o->tol;
+    omen_eig_opts o1 = *o;
+    o1.nev = 1;
+    o1.v0_dev = nullptr;
+    o1.basis = std::min(o->basis, std::max(16, nev + 8));
+    // a problem whose deflated operator had nothing below its line is settled: later rounds
+    // run only the problems the previous round changed
+    std::vector<char> todo(P, 1);
+    for (; rounds < nev; ++rounds) {
+      std::vector<double> line(P);
+      for (int p = 0; p < P; ++p) line[p] = main.lam[(size_t)p * nev + nev - 1] - margin;
+      KLock lk;
+      lk.X = X.p;
+      lk.n = nev;
+      lk.stop_above = &line;
+      lk.only = &todo;
+      lk.seed = 0x5EEDull + 0x9E3779B97F4A7C15ull * (unsigned long long)(rounds + 1);
+      KOut chk;
+      chk.Xout = Z.p;
+      s = kbatch_core(ctx, in, &o1, 1, lk, chk);
+      if (s != OMEN_OK) return s;
+      iters += chk.iterations;
+      hx += chk.hx;
+      bool changed = false;
+      for (int p = 0; p < P; ++p) {
+        if (!todo[p]) continue;
+        todo[p] = 0;
+        const double mu = chk.lam[p];
+        if (!(mu < line[p])) continue;
+        if (!chk.conv[p]) { conv[p] = 0; continue; }
+        // insert mu at its place in problem p's ascending list; the last pair drops out
+        double* lp = main.lam.data() + (size_t)p * nev;
+        double* rp = main.res.data() + (size_t)p * nev;
+        int j = nev - 1;
+        while (j > 0 && lp[j - 1] > mu) {
+          lp[j] = lp[j - 1];
+          rp[j] = rp[j - 1];
+          OMEN_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(X.p) + (size_t)j * blk + (size_t)off[p] * el,
+                                         static_cast<char*>(X.p) + (size_t)(j - 1) * blk + (size_t)off[p] * el,
+                                         (size_t)len[p] * el, cudaMemcpyDeviceToDevice, ctx->stream));
+          --j;
+        }
+        lp[j] = mu;
+        rp[j] = chk.res[p];
+        OMEN_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(X.p) + (size_t)j * blk + (size_t)off[p] * el,
+                                       static_cast<char*>(Z.p) + (size_t)off[p] * el, (size_t)len[p] * el,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        changed = true;
+        todo[p] = 1;
+        ++inserted;
+      }
+      if (!changed) break;
+    }
+  }
+  double maxres = 0.0, maxbd = 0.0;
+  for (int p = 0; p < P; ++p) {
+    std::vector<double> lp(main.lam.begin() + (size_t)p * nev, main.lam.begin() + (size_t)(p + 1) * nev);
+    std::vector<double> rp(main.res.begin() + (size_t)p * nev, main.res.begin() + (size_t)(p + 1) * nev), bd;
     error_bounds(lp, lp, rp, bd);
     for (int i = 0; i < nev; ++i) {
+      evals_host[(size_t)p * nev + i] = lp[i];
       maxres = std::max(maxres, rp[i]);
       maxbd = std::max(maxbd, bd[i]);
     }
+    // eigenvectors: problem p's nev vectors of len[p] rows from element nev*off[p]
     if (evecs_dev)
       for (int i = 0; i < nev; ++i)
-        OMEN_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(evecs_dev) + ((size_t)p * nev + i) * vb,
-                                       static_cast<char*>(Xb.p) + (size_t)ord[i] * blk + (size_t)p * vb, vb,
-                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        OMEN_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(evecs_dev) + ((size_t)nev * off[p] + (size_t)i * len[p]) * el,
+                                       static_cast<char*>(X.p) + (size_t)i * blk + (size_t)off[p] * el,
+                                       (size_t)len[p] * el, cudaMemcpyDeviceToDevice, ctx->stream));
   }
-  cudaFreeAsync(ph, ctx->stream);
-  cudaError_t e = cudaStreamSynchronize(ctx->stream);
-  op.release();
-  if (s != OMEN_OK) return s;
-  if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "k batch: %s", cudaGetErrorString(e));
+  OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   bool allc = true;
   for (char c : conv) allc = allc && c;
   if (info) {
     std::memset(info, 0, sizeof(*info));
-    info->iterations = iter;
+    info->iterations = iters;
     info->hx_count = hx;
     info->restarts = restarts;
     info->converged = allc;
@@ -2100,6 +2472,26 @@ extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int 
     info->max_residual_raw = maxres;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
-  if (!allc) return set_err(ctx, OMEN_ENOCONV, "k batch: not every wave vector converged in %d steps", iter);
+  if (!allc)
+    return set_err(ctx, OMEN_ENOCONV, "k batch: not every wave vector converged in %d steps (%d check rounds, %d inserted)",
+                   iters, rounds, inserted);
   return OMEN_OK;
+}
+
+
+
+extern "C" omen_status omen_eigs_kbatch(omen_ctx* ctx, const omen_ham* ham, int nk, const double* k_host,
+                                        const omen_eig_opts* o, double* evals_host, void* evecs_dev,
+                                        omen_eig_info* info) {
+  if (!ctx || !ham || !k_host) return set_err(ctx, OMEN_EINVAL, "null argument");
+  return kbatch_solve(ctx, {KbatchInput{ham, nk, k_host}}, o, evals_host, evecs_dev, info);
+}
+
+extern "C" omen_status omen_eigs_kbatch_multi(omen_ctx* ctx, int nitems, const omen_kbatch_item* items,
+                                              const omen_eig_opts* o, double* evals_host, void* evecs_dev,
+                                              omen_eig_info* info) {
+  if (!ctx || !items || nitems < 1) return set_err(ctx, OMEN_EINVAL, "null argument or no structures");
+  std::vector<KbatchInput> in;
+  for (int i = 0; i < nitems; ++i) in.push_back(KbatchInput{items[i].ham, items[i].nk, items[i].k_host});
+  return kbatch_solve(ctx, in, o, evals_host, evecs_dev, info);
 }

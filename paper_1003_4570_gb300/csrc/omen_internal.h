@@ -19,7 +19,9 @@ struct omen_ctx {
   int* d_status = nullptr;
   // Lanczos step sequences between host checks are captured once as CUDA graphs and replayed
   bool use_graphs = true;
+  int reorth = OMEN_REORTH_FULL;        // full Gram–Schmidt pass policy of the Lanczos steps
   cudaStream_t cap_stream = nullptr;   // private stream the captures are recorded on
+  cudaStream_t copy_stream[2] = {nullptr, nullptr};  // host<->device copies overlapped with H·X
 };
 
 struct omen_lattice {
@@ -94,6 +96,16 @@ omen_status launch_hx(omen_ctx* ctx, const omen_ham* ham, const void* x, void* y
                       double sigma, int vec_precision);
 omen_status launch_hx_kbatch(omen_ctx* ctx, const omen_ham* h, int nk, const double2* phases_dev, const void* x, void* y,
                              double sigma, int vec_precision);
+// One structure of a multi-structure k batch: its nk wave vectors' phase table (device) and the
+// element offset of its first vector in the batch's vector buffers ([nk][nrows] from there).
+struct KItem {
+  const omen_ham* ham;
+  int nk;
+  const double2* phases;
+  long long x_off;
+};
+omen_status launch_hx_kmulti(omen_ctx* ctx, const KItem* items, int nitems, const void* x, void* y, double sigma,
+                             int vec_precision);
 omen_status make_phases(omen_ctx* ctx, const omen_ham* h, int nk, const double* k_host, double2** out);
 
 // Krylov helpers (lanczos.cu)

@@ -122,6 +122,7 @@ def lib():
             "omen_destroy": (None, [vp]),
             "omen_last_error": (C.c_char_p, [vp]),
             "omen_set_graph_capture": (i, [vp, i]),
+            "omen_set_reorthogonalization": (i, [vp, i]),
             "omen_tune_hx": (i, [vp, vp, i, i, i, C.POINTER(TuneResult)]),
             "omen_tune_hx_kbatch": (i, [vp, vp, i, i, C.POINTER(TuneResult)]),
             "omen_hx_set_tile": (i, [vp, vp, i, i, i]),
@@ -139,6 +140,8 @@ def lib():
             "omen_eigs": (i, [vp, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
             "omen_hx_kbatch": (i, [vp, vp, i, vp, vp, vp, d]),
             "omen_eigs_kbatch": (i, [vp, vp, i, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
+            "omen_hx_kbatch_multi": (i, [vp, i, vp, vp, vp, d]),
+            "omen_eigs_kbatch_multi": (i, [vp, i, vp, C.POINTER(EigOpts), vp, vp, C.POINTER(EigInfo)]),
             "omen_poisson": (i, [vp, C.POINTER(Grid), vp, vp, C.POINTER(CGOpts), C.POINTER(SolveInfo)]),
             "omen_density_accum": (i, [vp, vp, vp, i, vp, d, vp]),
             "omen_deposit": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
@@ -209,6 +212,13 @@ def omen_create(device=0, stream=None) -> Context:
     if s != OMEN_OK:
         raise OmenError(s, "omen_create failed (no CUDA device?)")
     return Context(h)
+
+
+OMEN_REORTH_FULL, OMEN_REORTH_SEMI = 0, 1
+
+
+def omen_set_reorthogonalization(ctx: Context, policy) -> None:
+    ctx.check(lib().omen_set_reorthogonalization(ctx.handle, int(policy)))
 
 
 def omen_set_graph_capture(ctx: Context, enable: bool) -> None:
@@ -428,6 +438,44 @@ def omen_eigs_kbatch(ctx: Context, ham: Hamiltonian, kpts, nev, which=OMEN_LOWES
     if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
         ctx.check(s)
     return ev, info.as_dict(), s
+
+
+class KbatchItem(C.Structure):
+    _fields_ = [("ham", C.c_void_p), ("nk", C.c_int), ("k_host", C.c_void_p)]
+
+
+def _kbatch_items(items):
+    """items: sequence of (Hamiltonian, wave vectors [nk, 3]) -> ctypes array and kept arrays."""
+    ks = [np.ascontiguousarray(k, dtype=np.float64).reshape(-1, 3) for _, k in items]
+    arr = (KbatchItem * len(items))(*[KbatchItem(h.handle, len(k), k.ctypes.data) for (h, _), k in zip(items, ks)])
+    return arr, ks
+
+
+def omen_hx_kbatch_multi(ctx: Context, items, x_dev, y_dev, sigma=0.0):
+    """One launch over every (structure, k): vectors of the items one after another."""
+    arr, keep = _kbatch_items(items)
+    ctx.check(lib().omen_hx_kbatch_multi(ctx.handle, len(items), arr, _ptr(x_dev), _ptr(y_dev), float(sigma)))
+
+
+def omen_eigs_kbatch_multi(ctx: Context, items, nev, which=OMEN_LOWEST, sigma=0.0, tol=1e-9, max_iter=1000,
+                           basis=None, evecs_dev=None, raise_on_noconv=True):
+    """Lockstep solve over several structures.  Returns ([evals [nk_i, nev] per item], info, status)."""
+    arr, ks = _kbatch_items(items)
+    if basis is None:
+        basis = max(32, 2 * nev + 4)
+    o = EigOpts(int(nev), int(which), float(sigma), float(tol), int(max_iter), 1, int(basis), None, None)
+    total = sum(len(k) for k in ks)
+    ev = np.zeros((total, nev))
+    info = EigInfo()
+    s = lib().omen_eigs_kbatch_multi(ctx.handle, len(items), arr, C.byref(o), ev.ctypes.data, _ptr(evecs_dev),
+                                     C.byref(info))
+    if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
+        ctx.check(s)
+    out, i0 = [], 0
+    for k in ks:
+        out.append(ev[i0:i0 + len(k)])
+        i0 += len(k)
+    return out, info.as_dict(), s
 
 
 class MLP:

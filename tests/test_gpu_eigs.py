@@ -130,3 +130,33 @@ def test_graph_replay_matches_direct_launches(ctx, which):
     assert i0["restarts"] >= 2 and i0["iterations"] == i1["iterations"]
     assert np.array_equal(ev0, ev1) and np.array_equal(ev1, ev2)
     np.testing.assert_allclose(ev1, ref, atol=1e-9, rtol=0)
+
+
+@pytest.mark.parametrize("which", ["lowest", "nearest"])
+def test_semi_orthogonal_policy_matches_full_and_dense(ctx, which):
+    """Skipping the Gram–Schmidt update while the basis stays semi-orthogonal keeps the
+    eigenvalues at the dense solution's, as the full pass does."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(2, 3, 3, (0, 0, 1), seed=47, alloy_fraction=0.3, strain_amp=0.02)
+    p = synth.draw_tb_params(47, 10, 2)
+    H = hamiltonian.assemble(spec, p)
+    w = np.linalg.eigvalsh(H.toarray())
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p)
+    kw = dict(tol=1e-9, block=1, basis=40, max_iter=40000)
+    if which == "nearest":
+        sigma = round(0.5 * (w[0] + w[-1]) + 0.2, 3)
+        kw.update(which=omen.OMEN_NEAREST, sigma=sigma)
+        ref = eigs.nearest(w, sigma, 6)
+    else:
+        ref = w[:6]
+    res = {}
+    for pol in (omen.OMEN_REORTH_FULL, omen.OMEN_REORTH_SEMI):
+        omen.omen_set_reorthogonalization(ctx, pol)
+        res[pol] = omen.omen_eigs(ctx, ham, 6, **kw)
+    omen.omen_set_reorthogonalization(ctx, omen.OMEN_REORTH_FULL)
+    for pol, (ev, info, st) in res.items():
+        assert info["converged"] == 1, (pol, info)
+        np.testing.assert_allclose(ev, ref, atol=1e-9, rtol=0)
+    with pytest.raises(omen.OmenError):
+        omen.omen_set_reorthogonalization(ctx, 7)

@@ -218,3 +218,26 @@ def test_every_kbatch_launch_shape_gives_the_same_product(ctx, prec):
     r = omen.omen_tune_hx_kbatch(ctx, ham, len(kpts), reps=3)
     assert r["ms_best"] <= r["ms_default"] + 1e-9
     assert np.array_equal(product(), base)
+
+
+@pytest.mark.parametrize("per", [(0, 1, 0), (1, 0, 1), (2, 2, 1)])
+def test_hx_host_overlapped_slabs(ctx, per):
+    """The host-buffer product cuts the structure into z-slabs and overlaps their copies with the
+    product: every row must still equal the oracle's (hard-wall and periodic z, 2 vectors)."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(3, 2, 13, per, seed=37, alloy_fraction=0.3, strain_amp=0.02)
+    p = synth.draw_tb_params(37, 10, 2)
+    k = (0.2, -0.3, 0.1) if 2 in per else None
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, k=k)
+    H = hamiltonian.assemble(spec, p, kvec=k)
+    x = synth.random_vectors(12, H.shape[0], 2, dtype=complex if ham.is_complex else float)
+    y = omen.omen_hx_host(ctx, ham, x, sigma=0.3)
+    for v in range(2):
+        ref = H @ x[v] - 0.3 * x[v]
+        np.testing.assert_allclose(y[v], ref, atol=1e-12 * np.abs(ref).max(), rtol=0)
+    xp = torch.from_numpy(x).pin_memory()
+    yp = torch.empty_like(xp).pin_memory()
+    from paper_1003_4570_gb300.omen import lib
+    ctx.check(lib().omen_hx_host(ctx.handle, ham.handle, xp.data_ptr(), yp.data_ptr(), 2, 0.3))
+    assert np.array_equal(yp.numpy(), y)

@@ -76,3 +76,91 @@ def test_eigs_kbatch_lowest_and_folded(ctx):
     assert info["converged"] == 1, info
     for q in range(len(ks)):
         np.testing.assert_allclose(ev[q], eigs.nearest(dense[q], sigma, 4), atol=1e-9, rtol=0)
+
+
+def multi_items(omen, ctx, prec=0):
+    """Three structures of different sizes, each with its own potential and wave vectors."""
+    shapes = [((3, 2, 5), 61, 3), ((2, 2, 4), 62, 5), ((2, 3, 6), 63, 2)]
+    out = []
+    for dims, seed, nk in shapes:
+        spec, p = slab(*dims, seed=seed)
+        U = np.random.default_rng(seed).uniform(-0.1, 0.1, spec.natoms)
+        lat = omen.omen_build_lattice(ctx, spec)
+        ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, k=(0.0, 0.0, 0.0),
+                                   U_atom_dev=torch.from_numpy(U).cuda())
+        out.append(dict(spec=spec, p=p, U=U, lat=lat, ham=ham, ks=kpath(spec, nk)))
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_hx_kbatch_multi_matches_oracle(ctx, prec):
+    """One launch over the (structure, k) list equals the oracle's H_i(k) x for every pair."""
+    from paper_1003_4570_gb300 import omen
+    items = multi_items(omen, ctx, prec)
+    xs = [synth.random_vectors(70 + i, it["ham"].nrows, len(it["ks"]), dtype=complex) for i, it in enumerate(items)]
+    dt = items[0]["ham"].numpy_dtype
+    xd = torch.from_numpy(np.concatenate([x.astype(dt).ravel() for x in xs])).cuda()
+    yd = torch.empty_like(xd)
+    omen.omen_hx_kbatch_multi(ctx, [(it["ham"], it["ks"]) for it in items], xd, yd, sigma=0.15)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    i0 = 0
+    for it, x in zip(items, xs):
+        n = it["ham"].nrows
+        for q, kv in enumerate(it["ks"]):
+            H = hamiltonian.assemble(it["spec"], it["p"], U_atom=it["U"], kvec=kv)
+            xv = x[q].astype(dt).astype(complex)
+            ref = H @ xv - 0.15 * xv
+            tol = 1e-12 if prec == 0 else 2e-6
+            np.testing.assert_allclose(y[i0:i0 + n], ref, atol=tol * np.abs(ref).max(), rtol=0)
+            i0 += n
+    assert i0 == len(y)
+
+
+def test_eigs_kbatch_multi_matches_dense_and_single(ctx):
+    """Lockstep over three structures at once: each (structure, k) gives its dense eigenvalues,
+    the same as solving that structure alone; the returned vectors are its eigenvectors."""
+    from paper_1003_4570_gb300 import omen
+    items = multi_items(omen, ctx)
+    nev = 4
+    n_all = sum(it["ham"].nrows * len(it["ks"]) for it in items)
+    evd = torch.zeros(n_all * nev, dtype=torch.complex128, device="cuda")
+    evs, info, st = omen.omen_eigs_kbatch_multi(ctx, [(it["ham"], it["ks"]) for it in items], nev, tol=1e-9,
+                                                max_iter=5000, basis=40, evecs_dev=evd)
+    assert info["converged"] == 1, info
+    vecs = evd.cpu().numpy()
+    i0 = 0
+    for it, ev in zip(items, evs):
+        single, _, _ = omen.omen_eigs_kbatch(ctx, it["ham"], it["ks"], nev, tol=1e-9, max_iter=5000, basis=40)
+        n = it["ham"].nrows
+        for q, kv in enumerate(it["ks"]):
+            H = hamiltonian.assemble(it["spec"], it["p"], U_atom=it["U"], kvec=kv)
+            dense = np.linalg.eigvalsh(H.toarray())[:nev]
+            np.testing.assert_allclose(ev[q], dense, atol=1e-9, rtol=0)
+            np.testing.assert_allclose(single[q], dense, atol=1e-9, rtol=0)
+            X = vecs[i0:i0 + nev * n].reshape(nev, n).T
+            X = X / np.linalg.norm(X, axis=0)
+            r = np.linalg.norm(H @ X - X * ev[q][None, :], axis=0)
+            assert r.max() < 1e-3
+            i0 += nev * n
+    assert i0 == len(vecs)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_kbatch_finds_every_copy_of_degenerate_levels(ctx, prec):
+    """A pure-Si slab keeps the lattice symmetry: at Gamma one level is 4-fold among the lowest 6,
+    at the zone boundary every band is doubly degenerate.  The lockstep solver plus its locking
+    check must return the lowest 6 with multiplicity."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(2, 2, 4, (2, 2, 0), seed=64)
+    p = synth.gapped_si_params()
+    Lx = spec.nx * spec.a_nm
+    ks = np.array([[0.0, 0.0, 0.0], [np.pi / Lx, 0.0, 0.0], [0.3 * np.pi / Lx, 0.0, 0.0]])
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, k=(0.0, 0.0, 0.0))
+    tol = 1e-9 if prec == 0 else 1e-5
+    ev, info, st = omen.omen_eigs_kbatch(ctx, ham, ks, 6, tol=tol, max_iter=20000, basis=40)
+    assert info["converged"] == 1, info
+    for q, kv in enumerate(ks):
+        dense = np.linalg.eigvalsh(hamiltonian.assemble(spec, p, kvec=kv).toarray())[:6]
+        np.testing.assert_allclose(ev[q], dense, atol=(1e-9 if prec == 0 else 2e-5), rtol=0)

@@ -93,7 +93,7 @@ def delta_problem(seed, nzc=16):
 
 
 def run_scf(omen, ctx, lat, p, grid, rho_d, phi, kw):
-    return omen.omen_scf(ctx, lat, p, grid, phi, rho_d, eig_tol=1e-10, eig_block=4, eig_basis=48, mix=0.3,
+    return omen.omen_scf(ctx, lat, p, grid, phi, rho_d, eig_tol=1e-10, eig_block=1, eig_basis=48, mix=0.3,
                          mix_history=6, tol_V=1e-6, max_iter=200, **kw)
 
 
