@@ -38,7 +38,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure is in the mea
 
 # DRAM bytes per FP64 H·X launch on the 1M-atom alloy, by launch shape (CTA width, block rows
 # per register batch), from the ncu launch lists summarised in profiles/hx_kernel_sige_alloy.md
-HX_F64_TRAFFIC = {(128, 1): 2.552e9}
+HX_F64_TRAFFIC = {(128, 1): 2.547e9, (64, 2): 1.920e9, (32, 2): 1.915e9}
 
 
 def measured_peaks():
@@ -285,6 +285,36 @@ def measure_cube_500(ctx, omen, n=80, iters=500):
         del ham
         torch.cuda.empty_cache()
     return out
+
+
+def measure_hx_kbatch(ctx, omen, nxy=4, nz=80, nk=32, seed=7, reps=20):
+    """The k-batched product alone: all nk wave vectors of the 4x4x80-cell delta layer per launch
+    (complex64), default launch shape; also the profiling target of that kernel."""
+    import torch
+    spec = synth.lattice_spec(nxy, nxy, nz, (2, 2, 0), seed=seed)
+    lam = synth.draw_kbatch_instances(seed)[0][2]
+    U = synth.donor_sheet_potential(spec, seed, lam)
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, synth.gapped_si_params(), precision=omen.OMEN_F32, k=(0.0, 0.0, 0.0),
+                               U_atom_dev=torch.from_numpy(U).cuda())
+    ks = np.zeros((nk, 3))
+    ks[:, 0] = np.linspace(0.0, 1.0, nk) * np.pi / (nxy * spec.a_nm)
+    x = torch.ones(nk * ham.nrows, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        omen.omen_hx_kbatch(ctx, ham, ks, x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        omen.omen_hx_kbatch(ctx, ham, ks, x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbonds = lat.counts()[1]
+    # blocks (FP32) once per launch, complex64 vectors read and written once per k
+    alg = nbonds * 100 * 4 + nk * ham.nrows * 8 * 2 + spec.natoms * 9
+    return {"rows": ham.nrows, "k": nk, "ms": ms, "alg_GB": alg / 1e9, "GB_per_s": alg / ms / 1e6}
 
 
 def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
@@ -586,6 +616,7 @@ def run_gpu(args, rank, world, local_rank):
         result["eigs_8_lowest_si_8cubed"] = measure_small_si(ctx, omen)
         if args.cells == N_CELLS:
             result["lanczos_500_iterations_80cubed_si"] = measure_cube_500(ctx, omen)
+        result["hx_kbatch"] = measure_hx_kbatch(ctx, omen)
         result["kbatch"] = measure_kbatch(ctx, omen)
         result["scf_learned_vs_zero"] = measure_scf(ctx, omen)
     if rank == 0 and not args.no_cpu:
@@ -616,7 +647,7 @@ def main():
                     "smaller only for profiling captures)")
     ap.add_argument("--kbatch-full", action="store_true",
                     help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
-    ap.add_argument("--only", default="", choices=["", "kbatch", "scf", "small-si", "cube"],
+    ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube"],
                     help="profiling aid: run one side measurement alone and print its JSON")
     ap.add_argument("--tile", default="", metavar="THREADS,RB",
                     help="fix the H·X launch shape instead of tuning it (e.g. 64,2; profiling aid)")
@@ -639,8 +670,8 @@ def main():
         import torch
         from paper_1003_4570_gb300 import omen
         ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
-        fn = {"kbatch": measure_kbatch, "scf": measure_scf, "small-si": measure_small_si,
-              "cube": measure_cube_500}[args.only]
+        fn = {"kbatch": measure_kbatch, "hx-kbatch": measure_hx_kbatch, "scf": measure_scf,
+              "small-si": measure_small_si, "cube": measure_cube_500}[args.only]
         print(json.dumps({args.only: fn(ctx, omen)}))
         return
     if args.lanczos_only:

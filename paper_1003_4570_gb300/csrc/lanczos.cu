@@ -2281,6 +2281,7 @@ static omen_status kbatch_core(omen_ctx* ctx, const std::vector<KbatchInput>& in
       OMEN_CUDA(ctx, cudaMemcpyAsync(slot(kk), slot(nbas), blk, cudaMemcpyDeviceToDevice, ctx->stream));
       std::fill(Th.begin(), Th.end(), cd(0));
       for (int p = 0; p < P; ++p) {
+        if (frozen[p]) continue;   // its theta / Y are stale or (never run) empty
         cd* T = Th.data() + (size_t)p * tps;
         for (int i = 0; i < kk; ++i) T[i + (size_t)i * ldT] = theta[p][i];
         for (int i = 0; i < kk; ++i) T[kk + (size_t)i * ldT] = betas[p] * Y[p][jstart + (size_t)i * nbas];
