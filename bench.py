@@ -224,10 +224,12 @@ def measure_lanczos(ctx, omen, ham, iters=500, basis=64):
 
 def measure_eigs_1m(ctx, omen, lat, p, nev=16):
     """Seconds to nev converged eigenpairs at 1M atoms (lowest end of the spectrum, where the
-    thick-restart Lanczos converges): FP64, and spin-orbit complex64 + FP64 refinement."""
+    thick-restart Lanczos converges): FP64; FP64-accurate double-float Krylov vectors on the FP32
+    pipe; and spin-orbit complex64 + FP64 refinement."""
     import torch
     out = {}
-    for name, so, prec, tol in (("f64", False, omen.OMEN_F64, 1e-9), ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)):
+    for name, so, prec, tol in (("f64", False, omen.OMEN_F64, 1e-9), ("f64_double_float", False, omen.OMEN_F64_DF, 1e-9),
+                                ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)):
         ham = omen.omen_assemble_H(ctx, lat, p, spin_orbit=so, precision=prec)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -610,6 +612,9 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_extras:
         result["hx_variants"] = measure_variants(ctx, omen, lat, p, natoms, nbonds)
         result["lanczos_500_iterations"] = measure_lanczos(ctx, omen, ham)
+        ham_df = omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F64_DF)
+        result["lanczos_500_iterations_double_float"] = measure_lanczos(ctx, omen, ham_df)
+        del ham_df
         if args.cells == N_CELLS and prec == omen.OMEN_F64 and not args.matrix_free:
             del ham
             result["eigs_16_lowest_1M_atoms"] = measure_eigs_1m(ctx, omen, lat, p)
@@ -680,8 +685,10 @@ def main():
         ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
         spec, p = synth.config_sige_alloy(args.cells, seed=2)
         lat = omen.omen_build_lattice(ctx, spec)
-        ham = omen.omen_assemble_H(ctx, lat, p)
-        print(json.dumps({"lanczos": measure_lanczos(ctx, omen, ham, iters=args.lanczos_only), "cells": args.cells}))
+        prec = {"f64": omen.OMEN_F64, "f32": omen.OMEN_F32, "df": omen.OMEN_F64_DF}[args.precision]
+        ham = omen.omen_assemble_H(ctx, lat, p, precision=prec)
+        print(json.dumps({"lanczos": measure_lanczos(ctx, omen, ham, iters=args.lanczos_only), "cells": args.cells,
+                          "precision": args.precision}))
         return
     run_gpu(args, rank, world, local_rank)
 

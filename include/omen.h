@@ -97,6 +97,15 @@ omen_status omen_set_graph_capture(omen_ctx* ctx, int enable);
 enum { OMEN_REORTH_FULL = 0, OMEN_REORTH_SEMI = 1 };
 omen_status omen_set_reorthogonalization(omen_ctx* ctx, int policy);
 
+/* Missed-copy check of single-vector solves for the lowest eigenvalues (default on).  A
+ * single-vector Krylov space holds one direction of each eigenspace, so of a degenerate level
+ * (symmetric structures, zone-boundary bands) it finds one copy and may report the next
+ * eigenvalue in place of the others.  With the check, omen_eigs (block 1, OMEN_LOWEST) and
+ * omen_eigs_kbatch[_multi] (OMEN_LOWEST) solve again for the lowest eigenvalue of H with the nev
+ * vectors found projected out (locking); one below the nev-th by more than tol is inserted in
+ * order and the check repeats.  A block solve with block >= the multiplicity needs no check. */
+omen_status omen_set_locking_check(omen_ctx* ctx, int enable);
+
 /* ---- structure (paper Section II-A: atoms of the domain and their neighbours) ---------- */
 
 typedef struct {
@@ -212,7 +221,8 @@ typedef struct {
   int block;                 /* block size b (>= largest multiplicity among wanted values) */
   int basis;                 /* maximum basis size m (a multiple of b, > nev + b) */
   const void* v0_host;       /* [block][nrows] start block in the vector type of the
-                                Hamiltonian's precision, or NULL for a fixed default */
+                                Hamiltonian's precision (FP64 for OMEN_F64_DF), or NULL for a
+                                fixed default */
   const void* v0_dev;        /* the same on the device (takes precedence over v0_host), e.g.
                                 a combination of the previous solve's eigenvectors */
 } omen_eig_opts;
@@ -230,9 +240,11 @@ typedef struct {
 
 /* nev eigenpairs of H by thick-restart block Lanczos with full (twice-applied classical
  * Gram–Schmidt) reorthogonalisation.  evals_host[nev] ascending; evecs_dev (or NULL)
- * receives [nev][nrows] FP64-precision vectors (double / complex128) for OMEN_F64 and
- * OMEN_F32_REFINE64, float / complex64 for OMEN_F32.  Returns ENOCONV with the best
- * current pairs if max_iter is reached. */
+ * receives [nev][nrows] FP64-precision vectors (double / complex128) for OMEN_F64,
+ * OMEN_F32_REFINE64 and OMEN_F64_DF, float / complex64 for OMEN_F32.  With an OMEN_F64_DF
+ * Hamiltonian (block 1 only; EUNSUPPORTED otherwise) the Krylov vectors are double-float pairs
+ * and every product, projection and update runs on the FP32 pipe at about 48-bit accuracy;
+ * v0 is given in FP64.  Returns ENOCONV with the best current pairs if max_iter is reached. */
 omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_eig_opts* opts,
                       double* evals_host, void* evecs_dev, omen_eig_info* info);
 

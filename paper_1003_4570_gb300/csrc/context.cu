@@ -42,6 +42,12 @@ extern "C" omen_status omen_set_reorthogonalization(omen_ctx* c, int policy) {
   return OMEN_OK;
 }
 
+extern "C" omen_status omen_set_locking_check(omen_ctx* c, int enable) {
+  if (!c) return OMEN_EINVAL;
+  c->lock_check = enable != 0;
+  return OMEN_OK;
+}
+
 extern "C" omen_status omen_set_graph_capture(omen_ctx* c, int enable) {
   if (!c) return OMEN_EINVAL;
   c->use_graphs = enable != 0;

@@ -20,6 +20,7 @@
 
 #include "omen_internal.h"
 #include "sk_device.cuh"
+#include "df.cuh"
 
 template <typename T> struct Cx;
 template <> struct Cx<double> { using t = double2; };
@@ -239,37 +240,8 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
 
 // ---------------------------------------------------------------------------------------
 // Double-float product (precision OMEN_F64_DF): every value is an FP32 pair (hi, lo) with
-// value = hi + lo.  A product a*b is formed exactly in its leading part (p = fl(a.hi b.hi),
-// e = fma(a.hi, b.hi, -p)) plus the cross terms; it is added to a running (S, C) pair with
-// Knuth's TwoSum, the error going into C.  The intrinsics (_rn) keep the compiler from fusing
-// the additions into FMAs, which would break the error-free transformations.  All arithmetic is
-// on the FP32 pipe (57x GB300's FP64 rate); the bytes moved equal those of FP64.
-__device__ __forceinline__ void df_mac(float& S, float& C, float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  float e = __fmaf_rn(a.x, b.x, -p);
-  e = __fmaf_rn(a.x, b.y, e);
-  e = __fmaf_rn(a.y, b.x, e);
-  const float s = __fadd_rn(S, p);
-  const float bb = __fsub_rn(s, S);
-  const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  C = __fadd_rn(C, __fadd_rn(t, e));
-  S = s;
-}
-__device__ __forceinline__ float2 df_norm(float S, float C) {
-  const float h = __fadd_rn(S, C);
-  return make_float2(h, __fsub_rn(C, __fsub_rn(h, S)));
-}
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);
-  const float bb = __fsub_rn(s, a.x);
-  const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
-  return df_norm(s, __fadd_rn(t, __fadd_rn(a.y, b.y)));
-}
-__device__ __forceinline__ float2 df_from_double(double v) {
-  const float hi = __double2float_rn(v);
-  return make_float2(hi, __double2float_rn(v - (double)hi));
-}
-
+// value = hi + lo, products and sums by the error-free transformations of df.cuh, all on the
+// FP32 pipe (57x GB300's FP64 rate); the bytes moved equal those of FP64.
 struct HxDfArgs {
   Geo g;
   NeighbourTables nt;

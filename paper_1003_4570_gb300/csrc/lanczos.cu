@@ -28,6 +28,7 @@
 #include "dense_eig.h"
 #include "omen_internal.h"
 #include "vec.cuh"
+#include "df.cuh"
 
 using cd = std::complex<double>;
 
@@ -487,6 +488,117 @@ __global__ void __launch_bounds__(256) combinen_kernel(const void* Av, long long
   }
 }
 
+// ---- double-float Krylov kernels (precision OMEN_F64_DF): real vectors of (hi, lo) pairs,
+// products and sums in double-float arithmetic on the FP32 pipe (df.cuh); partial sums and
+// coefficients cross to and from FP64 once per thread and row respectively.
+
+// Projections of NB (1, 2 or 4) right-hand columns on IG = 16 / NB basis vectors per CTA;
+// partials P[chunk][i][j] as dotsn_kernel writes them.
+template <int NB>
+__global__ void __launch_bounds__(256) dots_df_kernel(const float2* __restrict__ A, long long lda, int na,
+                                                      const float2* __restrict__ B, long long ldb, int nb, long long n,
+                                                      int rows_per_cta, double2* __restrict__ P) {
+  constexpr int IG = 16 / NB;
+  const int i0 = blockIdx.x * IG;
+  const int ni = min(IG, na - i0);
+  const long long r0 = (long long)blockIdx.y * rows_per_cta;
+  const long long r1 = min(n, r0 + rows_per_cta);
+  float S[IG][NB], Cc[IG][NB];
+#pragma unroll
+  for (int i = 0; i < IG; ++i)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) { S[i][j] = 0.f; Cc[i][j] = 0.f; }
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    float2 bv[NB], av[IG];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) bv[j] = (j < nb) ? B[(size_t)j * ldb + r] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < IG; ++i) av[i] = (i < ni) ? A[(size_t)(i0 + i) * lda + r] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < IG; ++i)
+#pragma unroll
+      for (int j = 0; j < NB; ++j) df_mac(S[i][j], Cc[i][j], av[i], bv[j]);
+  }
+  __shared__ double red[8][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < IG; ++i)
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      double v = (double)S[i][j] + (double)Cc[i][j];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][i * NB + j] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < IG * NB) {
+    const int i = threadIdx.x / NB, j = threadIdx.x % NB;
+    if (i < ni && j < nb) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+      P[((size_t)blockIdx.y * na + i0 + i) * nb + j] = make_double2(v, 0.0);
+    }
+  }
+}
+
+// Y_j = beta Y_j + alpha sum_i A_i M[i + j*na] for NB (1, 2 or 4) columns; coefficients
+// alpha*M (FP64) become double-float pairs once per CTA.
+template <int NB>
+__global__ void __launch_bounds__(256) combine_df_kernel(const float2* __restrict__ A, long long lda, int na,
+                                                         const double2* __restrict__ M, int nb, float2* __restrict__ Y,
+                                                         long long ldy, long long n, double alpha, double beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Ms = reinterpret_cast<float2*>(smem_raw);
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Ms[t] = df_from_double(alpha * M[t].x);
+  __syncthreads();
+  const float2 b2 = df_from_double(beta);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    float S[NB], Cc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) { S[j] = 0.f; Cc[j] = 0.f; }
+    int i = 0;
+    for (; i + 4 <= na; i += 4) {
+      float2 av[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) av[k] = A[(size_t)(i + k) * lda + r];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+          if (j < nb) df_mac(S[j], Cc[j], av[k], Ms[i + k + j * na]);
+    }
+    for (; i < na; ++i) {
+      const float2 a = A[(size_t)i * lda + r];
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        if (j < nb) df_mac(S[j], Cc[j], a, Ms[i + j * na]);
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+      if (j < nb) {
+        float2& out = Y[(size_t)j * ldy + r];
+        if (beta != 0.0) df_mac(S[j], Cc[j], out, b2);
+        out = df_norm(S[j], Cc[j]);
+      }
+  }
+}
+
+// V = W / ||W|| (double-float), ||W||^2 read from the device; the norm goes into T[row, col]
+__global__ void normalize_df_kernel(const float2* __restrict__ W, float2* __restrict__ Vo, long long n,
+                                    const double2* __restrict__ nrm2, double2* __restrict__ Tm, int ldT, int row, int col,
+                                    int* __restrict__ flag) {
+  const double b = sqrt(fmax(nrm2->x, 0.0));
+  const float2 inv = df_from_double((b > 1e-300) ? 1.0 / b : 0.0);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    float S = 0.f, Cc = 0.f;
+    df_mac(S, Cc, W[r], inv);
+    Vo[r] = df_norm(S, Cc);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (Tm) Tm[row + (size_t)col * ldT] = make_double2(b, 0.0);
+    if (!(b > 1e-300) || !isfinite(b)) *flag = 1;
+  }
+}
+
 // Device-side reduction of the partials into out (na x nb, column-major) and, optionally,
 // into columns col0.. of the projected matrix T (ldT x ldT, column-major).
 __global__ void reduce_dev_kernel(const double2* __restrict__ P, int nchunks, int na, int nb, double2* __restrict__ out,
@@ -629,6 +741,13 @@ __global__ void random_fill_kernel(void* Xv, long long n, unsigned long long see
   }
 }
 
+__global__ void random_fill_df_kernel(float2* __restrict__ X, long long n, unsigned long long seed) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long h = splitmix64(seed * 0x100000001B3ull + 2 * (unsigned long long)r);
+    X[r] = df_from_double((double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+  }
+}
+
 template <typename Tin, typename Tout, bool C>
 __global__ void convert_kernel(const void* Xv, void* Yv, long long n) {
   using Ei = Elem<Tin, C>;
@@ -704,7 +823,7 @@ struct KrylovOps {
   // out (host, na x nb column-major complex) = A^H B   (A: na columns, B: nb columns)
   omen_status dots(const void* A, int na, const void* B, int nb, std::vector<cd>& out) {
     out.assign((size_t)na * nb, cd(0));
-    if (nb <= 4 && (size_t)na * nb <= small_cap) {
+    if ((nb <= 4 || prec == OMEN_F64_DF) && (size_t)na * nb <= small_cap) {
       omen_status s1 = dots_dev(A, na, B, nb, d_small, nullptr, 0, 0);
       if (s1 != OMEN_OK) return s1;
       OMEN_CUDA(ctx, cudaMemcpyAsync(out.data(), d_small, (size_t)na * nb * sizeof(double2), cudaMemcpyDeviceToHost, ctx->stream));
@@ -751,7 +870,7 @@ struct KrylovOps {
 
   // Y = beta*Y + alpha * A M   (M host na x nb column-major)
   omen_status combine(const void* A, int na, const std::vector<cd>& M, int nb, void* Y, double alpha, double beta) {
-    if (nb <= 4 && (size_t)na * nb <= small_cap) {
+    if ((nb <= 4 || prec == OMEN_F64_DF) && (size_t)na * nb <= small_cap) {
       // pageable source: the copy has consumed M when the call returns; stream order protects d_small
       OMEN_CUDA(ctx, cudaMemcpyAsync(d_small, M.data(), (size_t)na * nb * sizeof(double2), cudaMemcpyHostToDevice, ctx->stream));
       return combine_dev(A, na, d_small, nb, Y, alpha, beta);
@@ -822,6 +941,28 @@ struct KrylovOps {
   // nothing is copied to the host and the stream is not synchronised.
   omen_status dots_dev(const void* A, int na, const void* B, int nb, double2* out_dev, double2* accT, int ldT, int col0) {
     if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "dots_dev: too many columns");
+    if (prec == OMEN_F64_DF) {
+      // double-float vectors: up to 4 right-hand columns per launch
+      for (int j0 = 0; j0 < nb; j0 += 4) {
+        const int nbj = std::min(4, nb - j0);
+        const int NBk = nbj == 1 ? 1 : (nbj == 2 ? 2 : 4);
+        const int ig = 16 / NBk;
+        const int rows = (int)dot_rows(na, ig);
+        const long long nchunks = (n + rows - 1) / rows;
+        omen_status s1 = ensure_partial((size_t)nchunks * na * nbj);
+        if (s1 != OMEN_OK) return s1;
+        dim3 grid((na + ig - 1) / ig, (unsigned)nchunks);
+        const float2* Af = static_cast<const float2*>(A);
+        const float2* Bf = static_cast<const float2*>(B) + (size_t)j0 * n;
+        if (NBk == 1) dots_df_kernel<1><<<grid, 256, 0, ctx->stream>>>(Af, n, na, Bf, n, nbj, n, rows, d_partial);
+        else if (NBk == 2) dots_df_kernel<2><<<grid, 256, 0, ctx->stream>>>(Af, n, na, Bf, n, nbj, n, rows, d_partial);
+        else dots_df_kernel<4><<<grid, 256, 0, ctx->stream>>>(Af, n, na, Bf, n, nbj, n, rows, d_partial);
+        reduce_dev_kernel<<<na * nbj, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, nbj, out_dev + (size_t)j0 * na, accT,
+                                                           ldT, col0 + j0);
+        OMEN_CHECK_LAUNCH(ctx);
+      }
+      return OMEN_OK;
+    }
     if (nb > 1 && nb <= 4) {
       // a few right-hand columns: one launch, each basis load serving every column
       const int ig = dots1_ig(cplx) / ((nb <= 2) ? 2 : 4);
@@ -880,6 +1021,27 @@ struct KrylovOps {
 
   // Y = beta*Y + alpha * A M with M (na x nb, column-major) already on the device
   omen_status combine_dev(const void* A, int na, const double2* M_dev, int nb, void* Y, double alpha, double beta) {
+    if (prec == OMEN_F64_DF) {
+      const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+      for (int j0 = 0; j0 < nb; j0 += 4) {
+        const int nbj = std::min(4, nb - j0);
+        const size_t shm = (size_t)na * nbj * sizeof(float2);
+        const float2* Af = static_cast<const float2*>(A);
+        float2* Yf = static_cast<float2*>(Y) + (size_t)j0 * n;
+        const double2* Mj = M_dev + (size_t)j0 * na;
+#define COMBDF(NBk)                                                                                     \
+  do {                                                                                                  \
+    smem_limit(combine_df_kernel<NBk>, shm);                                                            \
+    combine_df_kernel<NBk><<<grid, 256, shm, ctx->stream>>>(Af, n, na, Mj, nbj, Yf, n, n, alpha, beta); \
+  } while (0)
+        if (nbj == 1) COMBDF(1);
+        else if (nbj == 2) COMBDF(2);
+        else COMBDF(4);
+#undef COMBDF
+        OMEN_CHECK_LAUNCH(ctx);
+      }
+      return OMEN_OK;
+    }
     if (nb > kMaxBlockCols) return set_err(ctx, OMEN_EINVAL, "combine_dev: too many columns");
     if (nb > 1 && nb <= 4) {
       const size_t shmn = (size_t)na * nb * sizeof(double2);
@@ -955,6 +1117,12 @@ struct KrylovOps {
   omen_status normalize_dev(const void* W, void* V, const double2* nrm2, double2* Tm, int ldT, int row, int col) {
     const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
     int* flag = ctx->d_status + 1;
+    if (prec == OMEN_F64_DF) {
+      normalize_df_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float2*>(W), static_cast<float2*>(V), n, nrm2, Tm,
+                                                         ldT, row, col, flag);
+      OMEN_CHECK_LAUNCH(ctx);
+      return OMEN_OK;
+    }
     if (prec == OMEN_F64) {
       if (cplx) normalize_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(W, V, n, nrm2, Tm, ldT, row, col, flag);
       else normalize_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(W, V, n, nrm2, Tm, ldT, row, col, flag);
@@ -1032,6 +1200,11 @@ struct KrylovOps {
   omen_status random_fill(void* X, int ncols, unsigned long long seed) {
     const long long total = n * ncols;
     const unsigned grid = (unsigned)std::min<long long>((total + 255) / 256, (long long)sm_count * 8);
+    if (prec == OMEN_F64_DF) {
+      random_fill_df_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<float2*>(X), total, seed);
+      OMEN_CHECK_LAUNCH(ctx);
+      return OMEN_OK;
+    }
     if (prec == OMEN_F64) {
       if (cplx) random_fill_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(X, total, seed);
       else random_fill_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(X, total, seed);
@@ -1045,8 +1218,33 @@ struct KrylovOps {
 
   // operator: W = A X, A = H (folded = false) or (H - sigma)^2
   bool negate = false;   // operator -H (highest eigenvalues)
+  // locking: the nlock vectors at lock_X (columns) are projected out after every product, so
+  // the recurrence sees the operator restricted to their orthogonal complement
+  const void* lock_X = nullptr;
+  int nlock = 0;
+  double2* d_lock = nullptr;   // [nlock] projections (single column)
+  unsigned long long lock_seed = 0;   // start vector of a locked solve: a new draw every time
+  // a solve may stop early once its lowest Ritz value minus its residual exceeds this line
+  bool has_line = false;
+  double stop_line = 0.0;
+
+  omen_status deflate(void* W) {
+    if (nlock == 0) return OMEN_OK;
+    omen_status s1 = dots_dev(lock_X, nlock, W, 1, d_lock, nullptr, 0, 0);
+    if (s1 == OMEN_OK) s1 = combine_dev(lock_X, nlock, d_lock, 1, W, -1.0, 1.0);
+    return s1;
+  }
 
   omen_status apply(const void* X, void* W, void* tmp, int nb, bool folded, double sigma, long long& count) {
+    if (nlock > 0) {
+      if (nb != 1 || negate) return set_err(ctx, OMEN_EUNSUPPORTED, "locking needs the single-vector lowest solve");
+      omen_status s = apply_raw(X, W, tmp, nb, folded, sigma, count);
+      return s == OMEN_OK ? deflate(W) : s;
+    }
+    return apply_raw(X, W, tmp, nb, folded, sigma, count);
+  }
+
+  omen_status apply_raw(const void* X, void* W, void* tmp, int nb, bool folded, double sigma, long long& count) {
     if (!folded) {
       count += nb;
       omen_status s = launch_hx(ctx, ham, X, W, nb, 0.0, prec);
@@ -1494,13 +1692,21 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   double2* dn = dh + ldT;
   OMEN_CUDA(ctx, cudaMemsetAsync(dT, 0, sizeof(double2) * ldT * ldT, ctx->stream));
   OMEN_CUDA(ctx, cudaMemsetAsync(ctx->d_status + 1, 0, sizeof(int), ctx->stream));
-  if (o->v0_dev) {
-    OMEN_CUDA(ctx, cudaMemcpyAsync(W, o->v0_dev, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
-  } else if (o->v0_host) {
-    OMEN_CUDA(ctx, cudaMemcpyAsync(W, o->v0_host, vbytes, cudaMemcpyHostToDevice, ctx->stream));
+  if (o->v0_dev || o->v0_host) {
+    if (o->v0_dev) OMEN_CUDA(ctx, cudaMemcpyAsync(W, o->v0_dev, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    else OMEN_CUDA(ctx, cudaMemcpyAsync(W, o->v0_host, vbytes, cudaMemcpyHostToDevice, ctx->stream));
+    if (op.prec == OMEN_F64_DF) {
+      // the start vector comes in FP64: split it into double-float pairs in place (same size)
+      omen_status sc = omen_convert_vectors(ctx, W, OMEN_F64, W, OMEN_F64_DF, op.n);
+      if (sc != OMEN_OK) return sc;
+    }
   } else {
-    omen_status s = op.random_fill(W, 1, 0x5EEDull);
+    omen_status s = op.random_fill(W, 1, op.nlock ? 0x5EEDull + 0x9E3779B97F4A7C15ull * (op.lock_seed + 1) : 0x5EEDull);
     if (s != OMEN_OK) return s;
+  }
+  for (int pass = 0; pass < 2 && op.nlock; ++pass) {
+    omen_status sd = op.deflate(W);
+    if (sd != OMEN_OK) return sd;
   }
   omen_status s = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
   if (s != OMEN_OK) return s;
@@ -1518,9 +1724,10 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   std::vector<cd> Y;
   auto t_start = std::chrono::steady_clock::now();
   bool fresh = true;   // first step of a cycle: the new vector couples to every kept vector
+  bool line_crossed = false;
   // One step on the device: W = A v_js, orthogonalise W against v_0..v_{nb-1} (T column js),
   // v_nb = W / ||W|| (T[nb, js] = ||W||).  No host synchronisation.
-  const bool semi = ctx->reorth == OMEN_REORTH_SEMI;
+  const bool semi = ctx->reorth == OMEN_REORTH_SEMI && op.prec != OMEN_F64_DF;
   auto enqueue_step = [&](int js, int nb, bool fr) -> omen_status {
     long long unused = 0;
     omen_status s2 = op.apply(op.col(V, js), W, tmp, 1, folded, o->sigma, unused);
@@ -1624,6 +1831,11 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
         std::vector<double> lam(theta.begin(), theta.begin() + nev), res(resA.begin(), resA.begin() + nev), bd;
         error_bounds(theta, lam, res, bd);
         done = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+        // nothing of the operator below the line (Weyl): no lower eigenvalue left to find
+        if (op.has_line && theta[0] - resA[0] > op.stop_line) {
+          done = true;
+          line_crossed = true;
+        }
       } else {
         const double rmax = *std::max_element(resA.begin(), resA.begin() + nev);
         if (gateA < 0) gateA = std::max(o->tol, 1e-12) * 1e3;
@@ -1652,7 +1864,7 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
         }
       }
       if (done || iter >= max_iter_of(o)) {
-        converged = done;
+        converged = done && !line_crossed;
         break;
       }
       if (full) {
@@ -1848,14 +2060,15 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   if (o->max_iter < 1 || (long long)o->max_iter * b < o->nev)
     return set_err(ctx, OMEN_EINVAL, "max_iter * block must be >= nev");
   if ((long long)o->basis + b > ham->nrows) return set_err(ctx, OMEN_EINVAL, "basis larger than the problem");
-  if (ham->precision == OMEN_F64_DF) return set_err(ctx, OMEN_EUNSUPPORTED, "the eigensolver runs in F64, F32 or F32_REFINE64");
+  if (ham->precision == OMEN_F64_DF && b != 1)
+    return set_err(ctx, OMEN_EUNSUPPORTED, "double-float Krylov vectors are single-vector (block 1) only");
   OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
   auto t0 = std::chrono::steady_clock::now();
   omen_eig_info local{};
   omen_eig_info* inf = info ? info : &local;
   std::memset(inf, 0, sizeof(*inf));
 
-  const int solve_prec = (ham->precision == OMEN_F64) ? OMEN_F64 : OMEN_F32;
+  const int solve_prec = (ham->precision == OMEN_F64 || ham->precision == OMEN_F64_DF) ? ham->precision : OMEN_F32;
   KrylovOps op{ctx, ham, solve_prec, (bool)ham->is_complex, ham->nrows};
   omen_status s = op.init();
   if (s != OMEN_OK) return s;
@@ -1894,6 +2107,62 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   const int nev = o->nev;
   std::vector<double> lam(rr.lam.begin(), rr.lam.begin() + nev), res(rr.res.begin(), rr.res.begin() + nev);
   std::vector<double> bound(rr.bound.begin(), rr.bound.begin() + nev);
+  if (b == 1 && o->which == OMEN_LOWEST && ctx->lock_check && conv) {
+    // A single-vector Krylov space holds one direction of each eigenspace: of a degenerate
+    // level it finds one copy and may report the next eigenvalue in place of the others.  Check
+    // with the nev vectors found locked (projected out of every product): the lowest eigenvalue
+    // of what is left either lies above the nev-th (within tol: done) or is a missed one, which
+    // is inserted in order, the last pair dropping out; then check again.
+    DevBuf Zb, HZb, RZb, Lk;
+    const int kz = 2;
+    if (cudaMalloc(&Zb.p, (size_t)kz * ham->nrows * op.el) != cudaSuccess ||
+        cudaMalloc(&HZb.p, (size_t)ham->nrows * op.el) != cudaSuccess ||
+        cudaMalloc(&RZb.p, (size_t)ham->nrows * op.el) != cudaSuccess ||
+        cudaMalloc(&Lk.p, sizeof(double2) * nev) != cudaSuccess) {
+      cudaGetLastError();
+      op.release();
+      return set_err(ctx, OMEN_ENOMEM, "locking check vectors");
+    }
+    omen_eig_opts o1 = *o;
+    o1.nev = 1;
+    o1.basis = std::min(o->basis, std::max(16, nev + 8));
+    o1.v0_dev = nullptr;
+    o1.v0_host = nullptr;
+    for (int round = 0; round < nev; ++round) {
+      op.lock_X = Xb.p;
+      op.nlock = nev;
+      op.d_lock = static_cast<double2*>(Lk.p);
+      op.has_line = true;
+      op.stop_line = lam[nev - 1] - o->tol;
+      op.lock_seed = (unsigned long long)round;   // the previous start has no component left in a level partly found
+      omen_eig_info i1{};
+      bool c1 = false;
+      s = lanczos_solve_single(op, &o1, Zb.p, 1, &i1, c1);
+      op.nlock = 0;
+      op.has_line = false;
+      if (s != OMEN_OK) { op.release(); return s; }
+      inf->iterations += i1.iterations;
+      inf->hx_count += i1.hx_count + 1;
+      std::vector<double> lz, rz;
+      s = launch_hx(ctx, ham, Zb.p, HZb.p, 1, 0.0, solve_prec);
+      if (s == OMEN_OK) s = rayleigh_residuals(op, Zb.p, HZb.p, RZb.p, 1, lz, rz);
+      if (s != OMEN_OK) { op.release(); return s; }
+      if (!(c1 && lz[0] < lam[nev - 1] - o->tol)) break;
+      int j = nev - 1;
+      while (j > 0 && lam[j - 1] > lz[0]) {
+        lam[j] = lam[j - 1];
+        res[j] = res[j - 1];
+        OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(Xb.p, j), op.col(Xb.p, j - 1), (size_t)ham->nrows * op.el,
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+        --j;
+      }
+      lam[j] = lz[0];
+      res[j] = rz[0];
+      OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(Xb.p, j), Zb.p, (size_t)ham->nrows * op.el, cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+      error_bounds(lam, lam, res, bound);
+    }
+  }
   inf->max_residual_raw = *std::max_element(res.begin(), res.end());
   void* Xfinal = Xb.p;
   DevBuf X64;
@@ -1932,7 +2201,10 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   inf->max_residual = *std::max_element(res.begin(), res.end());
   inf->max_error_bound = *std::max_element(bound.begin(), bound.end());
   inf->converged = conv && inf->max_error_bound <= o->tol;
-  if (evecs_dev) {
+  if (evecs_dev && solve_prec == OMEN_F64_DF) {
+    // double-float Krylov vectors: the eigenvectors are returned in FP64
+    s = omen_convert_vectors(ctx, Xfinal, OMEN_F64_DF, evecs_dev, OMEN_F64, (long long)nev * ham->nrows);
+  } else if (evecs_dev) {
     const size_t eb = (ham->precision == OMEN_F32_REFINE64) ? vec_elem_bytes(ham, OMEN_F64) : op.el;
     s = OMEN_OK;
     cudaError_t e = cudaMemcpyAsync(evecs_dev, Xfinal, (size_t)nev * ham->nrows * eb, cudaMemcpyDeviceToDevice, ctx->stream);

@@ -20,6 +20,7 @@ struct omen_ctx {
   // Lanczos step sequences between host checks are captured once as CUDA graphs and replayed
   bool use_graphs = true;
   int reorth = OMEN_REORTH_FULL;        // full Gram–Schmidt pass policy of the Lanczos steps
+  bool lock_check = true;               // single-vector lowest solves check for missed copies
   cudaStream_t cap_stream = nullptr;   // private stream the captures are recorded on
   cudaStream_t copy_stream[2] = {nullptr, nullptr};  // host<->device copies overlapped with H·X
 };

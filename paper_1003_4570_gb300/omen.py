@@ -123,6 +123,7 @@ def lib():
             "omen_last_error": (C.c_char_p, [vp]),
             "omen_set_graph_capture": (i, [vp, i]),
             "omen_set_reorthogonalization": (i, [vp, i]),
+            "omen_set_locking_check": (i, [vp, i]),
             "omen_tune_hx": (i, [vp, vp, i, i, i, C.POINTER(TuneResult)]),
             "omen_tune_hx_kbatch": (i, [vp, vp, i, i, C.POINTER(TuneResult)]),
             "omen_hx_set_tile": (i, [vp, vp, i, i, i]),
@@ -219,6 +220,10 @@ OMEN_REORTH_FULL, OMEN_REORTH_SEMI = 0, 1
 
 def omen_set_reorthogonalization(ctx: Context, policy) -> None:
     ctx.check(lib().omen_set_reorthogonalization(ctx.handle, int(policy)))
+
+
+def omen_set_locking_check(ctx: Context, enable: bool) -> None:
+    ctx.check(lib().omen_set_locking_check(ctx.handle, int(bool(enable))))
 
 
 def omen_set_graph_capture(ctx: Context, enable: bool) -> None:

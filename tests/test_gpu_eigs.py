@@ -160,3 +160,49 @@ def test_semi_orthogonal_policy_matches_full_and_dense(ctx, which):
         np.testing.assert_allclose(ev, ref, atol=1e-9, rtol=0)
     with pytest.raises(omen.OmenError):
         omen.omen_set_reorthogonalization(ctx, 7)
+
+
+def test_double_float_krylov_matches_fp64_oracle(ctx):
+    """Krylov vectors as double-float pairs (products and projections on the FP32 pipe), on a
+    strained alloy (no degenerate levels for the single-vector solver to miss): lowest and
+    nearest-sigma eigenvalues to 1e-9 eV of a dense solve, FP64 eigenvectors with small
+    residuals, block > 1 refused."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(2, 3, 4, (0, 0, 0), seed=41, alloy_fraction=0.3, strain_amp=0.02)
+    p = synth.draw_tb_params(41, 10, 2)
+    H = hamiltonian.assemble(spec, p)
+    w = np.linalg.eigvalsh(H.toarray())
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F64_DF)
+    ev, info, st = omen.omen_eigs(ctx, ham, 8, tol=1e-9, block=1, basis=48, max_iter=4000)
+    assert info["converged"] == 1, info
+    np.testing.assert_allclose(ev, w[:8], atol=1e-9, rtol=0)
+    with pytest.raises(omen.OmenError) as e:
+        omen.omen_eigs(ctx, ham, 8, tol=1e-9, block=2, basis=48, max_iter=4000)
+    assert e.value.status == omen.OMEN_EUNSUPPORTED
+    sigma = round(0.5 * (w[0] + w[-1]) + synth.sigma_offset_fraction(41) * (w[-1] - w[0]), 3)
+    evd = torch.zeros((6, ham.nrows), dtype=torch.float64, device="cuda")
+    ev, info, st = omen.omen_eigs(ctx, ham, 6, which=omen.OMEN_NEAREST, sigma=sigma, tol=1e-9, block=1,
+                                  basis=96, max_iter=60000, evecs_dev=evd)
+    assert info["converged"] == 1, info
+    np.testing.assert_allclose(ev, eigs.nearest(w, sigma, 6), atol=1e-9, rtol=0)
+    X = evd.cpu().numpy().T
+    X = X / np.linalg.norm(X, axis=0)
+    r = np.linalg.norm(H @ X - X * ev[None, :], axis=0)
+    gaps = np.array([np.sort(np.abs(w - e))[1] for e in ev])
+    assert np.all(r ** 2 / gaps <= 1e-9)
+
+
+@pytest.mark.parametrize("prec", [0, 3])
+def test_single_vector_lowest_finds_every_degenerate_copy(ctx, prec):
+    """Periodic bulk Si 3^3: a 6-fold level sits among the lowest 8.  The single-vector solve
+    (FP64, or double-float Krylov vectors) with its locking check returns it with multiplicity."""
+    from paper_1003_4570_gb300 import omen
+    spec, p = synth.config_si_periodic(3, seed=1)
+    ref = bulk.folded_spectrum(p, 3, 3, 3, spec.a_nm)[:8]
+    assert np.sum(np.abs(ref - ref[2]) < 1e-9) >= 4
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=prec)
+    ev, info, st = omen.omen_eigs(ctx, ham, 8, tol=1e-9, block=1, basis=48, max_iter=20000)
+    assert info["converged"] == 1, info
+    np.testing.assert_allclose(ev, ref, atol=1e-9, rtol=0)
