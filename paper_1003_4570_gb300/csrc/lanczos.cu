@@ -127,7 +127,7 @@ static constexpr int kIG = 16;
 // basis vectors per CTA of dots1_kernel: 16 real, 8 complex (the complex accumulators would
 // otherwise hold the kernel to one CTA per SM)
 static constexpr int dots1_ig(bool cplx) { return cplx ? 8 : kIG; }
-template <typename T, bool C>
+template <typename T, bool C, int IG>
 __global__ void __launch_bounds__(256, C ? 1 : 2) dots1_kernel(const void* Av, long long lda, int na, const void* Bv,
                                                     long long n, int rows_per_cta, double2* __restrict__ P,
                                                     long long a_ps = 0, long long b_ps = 0, long long p_ps = 0,
@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(256, C ? 1 : 2) dots1_kernel(const void* Av, l
   using E = Elem<T, C>;
   using V = typename E::V;
   using Acc = std::conditional_t<sizeof(T) == 8, double, float>;
-  constexpr int IG = dots1_ig(C);
+  // IG basis vectors per CTA (at most dots1_ig(C)); chosen from na so that no accumulator
+  // sits idle under a predicate (predicated-off FP64 FMAs still occupy the pipe)
   // grid.z = independent problems (batched Lanczos): offsets a_ps, b_ps (elements), p_ps
   // (partials) per problem, or per-problem element offsets poff and lengths plen
   const long long off = poff ? poff[blockIdx.z] : 0;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(256, C ? 1 : 2) dots1_kernel(const void* Av, l
       }
     }
   }
-  __shared__ double red[8][IG][2];
+  __shared__ double red[8][IG > 0 ? IG : 1][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < IG; ++i) {
@@ -488,17 +489,49 @@ __global__ void __launch_bounds__(256) combinen_kernel(const void* Av, long long
   }
 }
 
+// Many-output combination of real FP64 vectors (restarts: kk Ritz vectors from m basis
+// vectors): nb FMAs per element read would hold it to GB300's FP64 rate, so each element is
+// split once into a double-float pair (one FP64 subtraction) and the nb products and sums run in
+// double-float arithmetic on the FP32 pipe; each result is rounded back to FP64 (about 48 of its
+// 53 bits exact — the next step re-orthogonalises anyway).
+template <int NBT>
+__global__ void __launch_bounds__(256) combine_split_kernel(const double* __restrict__ A, long long lda, int na,
+                                                            const double2* __restrict__ M, int nb, double* __restrict__ Y,
+                                                            long long ldy, long long n, double alpha, double beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Ms = reinterpret_cast<float2*>(smem_raw);
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Ms[t] = df_from_double(alpha * M[t].x);
+  __syncthreads();
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    float S[NBT], Cc[NBT];
+#pragma unroll
+    for (int j = 0; j < NBT; ++j) { S[j] = 0.f; Cc[j] = 0.f; }
+    for (int i = 0; i < na; ++i) {
+      const float2 a = df_from_double(A[(size_t)i * lda + r]);
+#pragma unroll
+      for (int j = 0; j < NBT; ++j)
+        if (j < nb) df_mac(S[j], Cc[j], a, Ms[i + j * na]);
+    }
+#pragma unroll
+    for (int j = 0; j < NBT; ++j)
+      if (j < nb) {
+        double v = (double)S[j] + (double)Cc[j];
+        if (beta != 0.0) v = fma(beta, Y[(size_t)j * ldy + r], v);
+        Y[(size_t)j * ldy + r] = v;
+      }
+  }
+}
+
 // ---- double-float Krylov kernels (precision OMEN_F64_DF): real vectors of (hi, lo) pairs,
 // products and sums in double-float arithmetic on the FP32 pipe (df.cuh); partial sums and
 // coefficients cross to and from FP64 once per thread and row respectively.
 
 // Projections of NB (1, 2 or 4) right-hand columns on IG = 16 / NB basis vectors per CTA;
 // partials P[chunk][i][j] as dotsn_kernel writes them.
-template <int NB>
+template <int NB, int IG>
 __global__ void __launch_bounds__(256) dots_df_kernel(const float2* __restrict__ A, long long lda, int na,
                                                       const float2* __restrict__ B, long long ldb, int nb, long long n,
                                                       int rows_per_cta, double2* __restrict__ P) {
-  constexpr int IG = 16 / NB;
   const int i0 = blockIdx.x * IG;
   const int ni = min(IG, na - i0);
   const long long r0 = (long long)blockIdx.y * rows_per_cta;
@@ -777,6 +810,29 @@ static void smem_limit(K kernel, size_t bytes) {
 
 // ---------------------------------------------------------------------------------------
 // Host-side helpers bound to one vector type.
+// basis vectors per CTA for a projection on na of them: the smallest power of two >= na,
+// capped at `cap`
+static int dots_ig_for(int na, int cap) {
+  int ig = 1;
+  while (ig < na && ig < cap) ig *= 2;
+  return ig;
+}
+
+template <typename T, bool C>
+static void launch_dots1(int ig, dim3 grid, cudaStream_t st, const void* A, long long lda, int na, const void* B,
+                         long long n, int rows, double2* P, long long a_ps = 0, long long b_ps = 0, long long p_ps = 0,
+                         const long long* poff = nullptr, const long long* plen = nullptr, const int* act = nullptr) {
+  switch (ig) {
+    case 1: dots1_kernel<T, C, 1><<<grid, 256, 0, st>>>(A, lda, na, B, n, rows, P, a_ps, b_ps, p_ps, poff, plen, act); break;
+    case 2: dots1_kernel<T, C, 2><<<grid, 256, 0, st>>>(A, lda, na, B, n, rows, P, a_ps, b_ps, p_ps, poff, plen, act); break;
+    case 4: dots1_kernel<T, C, 4><<<grid, 256, 0, st>>>(A, lda, na, B, n, rows, P, a_ps, b_ps, p_ps, poff, plen, act); break;
+    case 8: dots1_kernel<T, C, 8><<<grid, 256, 0, st>>>(A, lda, na, B, n, rows, P, a_ps, b_ps, p_ps, poff, plen, act); break;
+    default:
+      if constexpr (!C) dots1_kernel<T, C, 16><<<grid, 256, 0, st>>>(A, lda, na, B, n, rows, P, a_ps, b_ps, p_ps, poff, plen, act);
+      else dots1_kernel<T, C, 8><<<grid, 256, 0, st>>>(A, lda, na, B, n, rows, P, a_ps, b_ps, p_ps, poff, plen, act);
+  }
+}
+
 struct KrylovOps {
   omen_ctx* ctx;
   const omen_ham* ham;
@@ -890,7 +946,18 @@ struct KrylovOps {
     smem_limit(combine_kernel<T, Cc>, shm); \
     combine_kernel<T, Cc><<<grid, 256, shm, ctx->stream>>>(A, n, na, d_small, nbj, Yj, n, n, alpha, beta); \
   } while (0)
-      if (prec == OMEN_F64) { if (cplx) COMB_LAUNCH(double, true); else COMB_LAUNCH(double, false); }
+      if (prec == OMEN_F64 && !cplx) {
+        const size_t shs = (size_t)na * nbj * sizeof(float2);
+        const double* Ad = static_cast<const double*>(A);
+        double* Yd = static_cast<double*>(Yj);
+        if (nbj <= 8) {
+          smem_limit(combine_split_kernel<8>, shs);
+          combine_split_kernel<8><<<grid, 256, shs, ctx->stream>>>(Ad, n, na, d_small, nbj, Yd, n, n, alpha, beta);
+        } else {
+          smem_limit(combine_split_kernel<16>, shs);
+          combine_split_kernel<16><<<grid, 256, shs, ctx->stream>>>(Ad, n, na, d_small, nbj, Yd, n, n, alpha, beta);
+        }
+      } else if (prec == OMEN_F64) COMB_LAUNCH(double, true);
       else { if (cplx) COMB_LAUNCH(float, true); else COMB_LAUNCH(float, false); }
 #undef COMB_LAUNCH
       OMEN_CHECK_LAUNCH(ctx);
@@ -946,7 +1013,7 @@ struct KrylovOps {
       for (int j0 = 0; j0 < nb; j0 += 4) {
         const int nbj = std::min(4, nb - j0);
         const int NBk = nbj == 1 ? 1 : (nbj == 2 ? 2 : 4);
-        const int ig = 16 / NBk;
+        const int ig = dots_ig_for(na, 16 / NBk);
         const int rows = (int)dot_rows(na, ig);
         const long long nchunks = (n + rows - 1) / rows;
         omen_status s1 = ensure_partial((size_t)nchunks * na * nbj);
@@ -954,9 +1021,15 @@ struct KrylovOps {
         dim3 grid((na + ig - 1) / ig, (unsigned)nchunks);
         const float2* Af = static_cast<const float2*>(A);
         const float2* Bf = static_cast<const float2*>(B) + (size_t)j0 * n;
-        if (NBk == 1) dots_df_kernel<1><<<grid, 256, 0, ctx->stream>>>(Af, n, na, Bf, n, nbj, n, rows, d_partial);
-        else if (NBk == 2) dots_df_kernel<2><<<grid, 256, 0, ctx->stream>>>(Af, n, na, Bf, n, nbj, n, rows, d_partial);
-        else dots_df_kernel<4><<<grid, 256, 0, ctx->stream>>>(Af, n, na, Bf, n, nbj, n, rows, d_partial);
+#define DDF(NBc, IGc) dots_df_kernel<NBc, IGc><<<grid, 256, 0, ctx->stream>>>(Af, n, na, Bf, n, nbj, n, rows, d_partial)
+        if (NBk == 1) {
+          if (ig == 1) DDF(1, 1); else if (ig == 2) DDF(1, 2); else if (ig == 4) DDF(1, 4); else if (ig == 8) DDF(1, 8); else DDF(1, 16);
+        } else if (NBk == 2) {
+          if (ig == 1) DDF(2, 1); else if (ig == 2) DDF(2, 2); else if (ig == 4) DDF(2, 4); else DDF(2, 8);
+        } else {
+          if (ig == 1) DDF(4, 1); else if (ig == 2) DDF(4, 2); else DDF(4, 4);
+        }
+#undef DDF
         reduce_dev_kernel<<<na * nbj, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, nbj, out_dev + (size_t)j0 * na, accT,
                                                            ldT, col0 + j0);
         OMEN_CHECK_LAUNCH(ctx);
@@ -984,18 +1057,18 @@ struct KrylovOps {
       return OMEN_OK;
     }
     if (nb == 1) {
-      const int ig1 = dots1_ig(cplx);
+      const int ig1 = dots_ig_for(na, dots1_ig(cplx));
       const int rows = (int)dot_rows(na, ig1);
       const long long nchunks = (n + rows - 1) / rows;
       omen_status s1 = ensure_partial((size_t)nchunks * na);
       if (s1 != OMEN_OK) return s1;
       dim3 grid((na + ig1 - 1) / ig1, (unsigned)nchunks);
       if (prec == OMEN_F64) {
-        if (cplx) dots1_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
-        else dots1_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
+        if (cplx) launch_dots1<double, true>(ig1, grid, ctx->stream, A, n, na, B, n, rows, d_partial);
+        else launch_dots1<double, false>(ig1, grid, ctx->stream, A, n, na, B, n, rows, d_partial);
       } else {
-        if (cplx) dots1_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
-        else dots1_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(A, n, na, B, n, rows, d_partial);
+        if (cplx) launch_dots1<float, true>(ig1, grid, ctx->stream, A, n, na, B, n, rows, d_partial);
+        else launch_dots1<float, false>(ig1, grid, ctx->stream, A, n, na, B, n, rows, d_partial);
       }
       reduce_dev_kernel<<<na, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, 1, out_dev, accT, ldT, col0);
       OMEN_CHECK_LAUNCH(ctx);
@@ -1145,7 +1218,8 @@ struct KrylovOps {
   omen_status dots_dev_batch(int P, const void* A, long long lda, int na, const void* B, double2* out_dev,
                              long long out_ps, double2* accT, int ldT, long long t_ps, int col0) {
     // the P problems share the grid: chunks sized for about two CTAs per SM over the batch
-    const long long groups = (na + dots1_ig(cplx) - 1) / dots1_ig(cplx);
+    const int igb = dots_ig_for(na, dots1_ig(cplx));
+    const long long groups = (na + igb - 1) / igb;
     const long long want = std::max<long long>(1, (2LL * sm_count + groups * P - 1) / (groups * P));
     long long rows = (b_nmax + want - 1) / want;
     rows = std::min<long long>(8192, std::max<long long>(256, (rows + 255) / 256 * 256));
@@ -1156,7 +1230,7 @@ struct KrylovOps {
     if (s1 != OMEN_OK) return s1;
     dim3 grid((unsigned)groups, (unsigned)nchunks, P);
 #define DOTSB(T, Cc) \
-  dots1_kernel<T, Cc><<<grid, 256, 0, ctx->stream>>>(A, lda, na, B, b_nmax, (int)rows, d_partial, 0, 0, pps, b_off, b_len, b_act)
+  launch_dots1<T, Cc>(igb, grid, ctx->stream, A, lda, na, B, b_nmax, (int)rows, d_partial, 0, 0, pps, b_off, b_len, b_act)
     if (prec == OMEN_F64) { if (cplx) DOTSB(double, true); else DOTSB(double, false); }
     else { if (cplx) DOTSB(float, true); else DOTSB(float, false); }
 #undef DOTSB
