@@ -222,7 +222,7 @@ def measure_lanczos(ctx, omen, ham, iters=500, basis=64):
     return out
 
 
-def measure_eigs_1m(ctx, omen, lat, p, nev=16):
+def measure_eigs_1m(ctx, omen, lat, p, nev=16, only=None):
     """Seconds to nev converged eigenpairs at 1M atoms (lowest end of the spectrum, where the
     thick-restart Lanczos converges): FP64; FP64-accurate double-float Krylov vectors on the FP32
     pipe; and spin-orbit complex64 + FP64 refinement."""
@@ -230,6 +230,8 @@ def measure_eigs_1m(ctx, omen, lat, p, nev=16):
     out = {}
     for name, so, prec, tol in (("f64", False, omen.OMEN_F64, 1e-9), ("f64_double_float", False, omen.OMEN_F64_DF, 1e-9),
                                 ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)):
+        if only and name != only:
+            continue
         ham = omen.omen_assemble_H(ctx, lat, p, spin_orbit=so, precision=prec)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -652,7 +654,7 @@ def main():
                     "smaller only for profiling captures)")
     ap.add_argument("--kbatch-full", action="store_true",
                     help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
-    ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube"],
+    ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube", "so-eigs"],
                     help="profiling aid: run one side measurement alone and print its JSON")
     ap.add_argument("--tile", default="", metavar="THREADS,RB",
                     help="fix the H·X launch shape instead of tuning it (e.g. 64,2; profiling aid)")
@@ -675,6 +677,11 @@ def main():
         import torch
         from paper_1003_4570_gb300 import omen
         ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+        if args.only == "so-eigs":
+            spec, p = synth.config_sige_alloy(args.cells, seed=2)
+            lat = omen.omen_build_lattice(ctx, spec)
+            print(json.dumps({args.only: measure_eigs_1m(ctx, omen, lat, p, only="so_f32_refine64")}))
+            return
         fn = {"kbatch": measure_kbatch, "hx-kbatch": measure_hx_kbatch, "scf": measure_scf,
               "small-si": measure_small_si, "cube": measure_cube_500}[args.only]
         print(json.dumps({args.only: fn(ctx, omen)}))

@@ -702,18 +702,28 @@ __global__ void normalize_kernel(const void* Wv, void* Vv, long long n, const do
 template <typename T, bool C>
 __global__ void combine_kernel(const void* Av, long long lda, int na, const double2* __restrict__ M, int nb,
                                void* Yv, long long ldy, long long n, double alpha, double beta) {
+  // arithmetic in the vectors' precision (coefficients alpha*M rounded once): FP32 vectors keep
+  // their nb products per element off GB300's FP64 pipe
   using E = Elem<T, C>;
   using V = typename E::V;
+  using A2 = std::conditional_t<sizeof(T) == 8, double2, float2>;
+  using R = T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* Ms = reinterpret_cast<double2*>(smem_raw);
-  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Ms[t] = M[t];
+  A2* Ms = reinterpret_cast<A2*>(smem_raw);
+  for (int t = threadIdx.x; t < na * nb; t += blockDim.x) {
+    A2 m;
+    m.x = (R)(alpha * M[t].x);
+    m.y = (R)(alpha * M[t].y);
+    Ms[t] = m;
+  }
   __syncthreads();
   const V* A = static_cast<const V*>(Av);
   V* Y = static_cast<V*>(Yv);
+  const R rbeta = (R)beta;
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-    double yr[kMaxBlockCols], yi[kMaxBlockCols];
+    R yr[kMaxBlockCols], yi[kMaxBlockCols];
 #pragma unroll
-    for (int j = 0; j < kMaxBlockCols; ++j) { yr[j] = 0.0; yi[j] = 0.0; }
+    for (int j = 0; j < kMaxBlockCols; ++j) { yr[j] = 0; yi[j] = 0; }
     for (int i0 = 0; i0 < na; i0 += 4) {
       V av[4];
 #pragma unroll
@@ -723,11 +733,11 @@ __global__ void combine_kernel(const void* Av, long long lda, int na, const doub
       for (int k = 0; k < 4; ++k) {
         if (i0 + k >= na) break;
         const int i = i0 + k;
-        const double xr = E::re(av[k]), xi = E::im(av[k]);
+        const R xr = (R)E::re(av[k]), xi = (R)E::im(av[k]);
 #pragma unroll
         for (int j = 0; j < kMaxBlockCols; ++j) {
           if (j < nb) {
-            const double2 m = Ms[i + j * na];
+            const A2 m = Ms[i + j * na];
             yr[j] = fma(xr, m.x, yr[j]);
             if constexpr (C) {
               yr[j] = fma(-xi, m.y, yr[j]);
@@ -742,10 +752,10 @@ __global__ void combine_kernel(const void* Av, long long lda, int na, const doub
     for (int j = 0; j < kMaxBlockCols; ++j) {
       if (j < nb) {
         V& out = Y[j * ldy + r];
-        double orr = alpha * yr[j], oi = alpha * yi[j];
+        R orr = yr[j], oi = yi[j];
         if (beta != 0.0) {
-          orr += beta * E::re(out);
-          oi += beta * E::im(out);
+          orr = fma(rbeta, (R)E::re(out), orr);
+          oi = fma(rbeta, (R)E::im(out), oi);
         }
         out = E::make(orr, oi);
       }
@@ -1398,6 +1408,49 @@ struct KrylovOps {
 
   // Orthogonalise W (nb cols) against the first nv columns of V (twice); adds the
   // coefficients into hsum (nv x nb).
+  // Block three-term step: W -= V_j (V_j^H W) and W -= V_{j-1} Mprev (the known coupling), then
+  // one full classical Gram–Schmidt pass over the nv basis vectors.  hsum (nv x nb) receives
+  // every coefficient removed, Mprev included.
+  omen_status orthogonalise3(const void* V, int nv, int jstart, int jprev, const std::vector<cd>& Mprev, void* W, int nb,
+                             std::vector<cd>& hsum) {
+    hsum.assign((size_t)nv * nb, cd(0));
+    const size_t need = (size_t)nv * nb * 2 + (size_t)nb * nb;
+    if (need > hs_cap) {
+      cudaFree(d_hs);
+      d_hs = nullptr;
+      hs_cap = 0;
+      if (cudaMalloc(&d_hs, need * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, OMEN_ENOMEM, "projection sums");
+      }
+      hs_cap = need;
+    }
+    double2* h = d_hs;
+    double2* sum = d_hs + (size_t)nv * nb;
+    double2* mp = sum + (size_t)nv * nb;
+    OMEN_CUDA(ctx, cudaMemsetAsync(sum, 0, sizeof(double2) * nv * nb, ctx->stream));
+    omen_status s = dots_dev(col(const_cast<void*>(V), jstart), nb, W, nb, h, sum + jstart, nv, 0);
+    if (s == OMEN_OK) s = combine_dev(col(const_cast<void*>(V), jstart), nb, h, nb, W, -1.0, 1.0);
+    if (s != OMEN_OK) return s;
+    if (jprev >= 0) {
+      OMEN_CUDA(ctx, cudaMemcpyAsync(mp, Mprev.data(), sizeof(double2) * nb * nb, cudaMemcpyHostToDevice, ctx->stream));
+      s = combine_dev(col(const_cast<void*>(V), jprev), nb, mp, nb, W, -1.0, 1.0);
+      if (s != OMEN_OK) return s;
+    }
+    s = dots_dev(V, nv, W, nb, h, sum, nv, 0);
+    if (s == OMEN_OK) s = combine_dev(V, nv, h, nb, W, -1.0, 1.0);
+    if (s != OMEN_OK) return s;
+    OMEN_CUDA(ctx, cudaMemcpyAsync(hsum.data(), sum, sizeof(double2) * nv * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (jprev >= 0)
+      for (int j = 0; j < nb; ++j)
+        for (int i = 0; i < nb; ++i) hsum[(jprev + i) + (size_t)j * nv] += Mprev[i + (size_t)j * nb];
+    for (const cd& v : hsum)
+      if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+        return set_err(ctx, OMEN_ENUMERIC, "non-finite value in a Krylov inner product");
+    return OMEN_OK;
+  }
+
   omen_status orthogonalise(const void* V, int nv, void* W, int nb, std::vector<cd>* hsum) {
     if (hsum) hsum->assign((size_t)nv * nb, cd(0));
     if (nv == 0) return OMEN_OK;
@@ -1545,13 +1598,25 @@ static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X,
   std::vector<cd> Rlast;
   unsigned long long reseed = 1;
   auto t_start = std::chrono::steady_clock::now();
+  bool fresh = true;   // first step of a cycle: the new block couples to every kept vector
 
   while (true) {
     // expand
     s = op.apply(op.col(V, jstart), W, tmp, b, folded, o->sigma, hx);
     if (s != OMEN_OK) return s;
     std::vector<cd> hsum;
-    s = op.orthogonalise(V, nbas, W, b, &hsum);
+    if (fresh || jstart < b) {
+      // two full classical Gram–Schmidt passes
+      s = op.orthogonalise(V, nbas, W, b, &hsum);
+    } else {
+      // three-term block step (against the current and previous blocks), then one full pass
+      const int jprev = jstart - b;
+      std::vector<cd> Mprev((size_t)b * b);
+      for (int j = 0; j < b; ++j)
+        for (int i = 0; i < b; ++i) Mprev[i + (size_t)j * b] = Tat(jprev + i, jstart + j);
+      s = op.orthogonalise3(V, nbas, jstart, jprev, Mprev, W, b, hsum);
+    }
+    fresh = false;
     if (s != OMEN_OK) return s;
     for (int j = 0; j < b; ++j)
       for (int i = 0; i < nbas; ++i) {
@@ -1670,6 +1735,7 @@ static omen_status lanczos_solve(KrylovOps& op, const omen_eig_opts* o, void* X,
         jstart = kk;
         nbas = kk + b;
         ++restarts;
+        fresh = true;
         continue;
       }
     }
