@@ -425,13 +425,16 @@ def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         omen.omen_mlp_warm_start(ctx, net, grid, rho, phi1)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
         _, info1, s1 = solve(5000 + j, phi1)
         zi.append(info0["iterations"]); zt.append(s0)
-        li.append(info1["iterations"]); lt.append(s1 + 0.0)
+        li.append(info1["iterations"]); lt.append(s1 + t_inf)
     return {"workload": f"delta-doped Si 1x1x{nzc} cells ({spec.natoms} atoms, {spec.natoms * 10} rows), Gamma, "
                         f"grid {grid.nx}x{grid.ny}x{grid.nz}, Anderson mixing, tol 1e-6 V",
-            "zero_field": {"iterations": zi, "seconds": zt},
-            "learned": {"iterations": li, "seconds": lt},
+            "zero_field": {"iterations": zi, "seconds": zt, "mean_iterations": float(np.mean(zi))},
+            "learned": {"iterations": li, "seconds": lt, "mean_iterations": float(np.mean(li)),
+                        "includes": "network inference"},
             "time_ratio_zero_over_learned": float(np.sum(zt) / max(np.sum(lt), 1e-9)),
             "training": {"profiles": n_train, "dataset_seconds": t_data, "adam_steps": train_steps,
                          "train_seconds": t_train}}
@@ -652,6 +655,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the Lanczos and k-batch side measurements")
     ap.add_argument("--cells", type=int, default=N_CELLS, help="cells per edge (50 = the 1M-atom workload; "
                     "smaller only for profiling captures)")
+    ap.add_argument("--scf-full", action="store_true",
+                    help="one-off: warm-start network trained on 200 SCF solutions, 20 held-out profiles (minutes)")
     ap.add_argument("--kbatch-full", action="store_true",
                     help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
     ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube", "so-eigs"],
@@ -666,6 +671,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.scf_full:
+        import torch
+        from paper_1003_4570_gb300 import omen
+        ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+        print(json.dumps({"scf_full": measure_scf(ctx, omen, n_train=200, n_test=20, train_steps=2000)}))
         return
     if args.kbatch_full:
         import torch

@@ -522,6 +522,65 @@ __global__ void __launch_bounds__(256) combine_split_kernel(const double* __rest
   }
 }
 
+// Column-wise inner products <A_j, B_j> (j < ncols, columns n apart): CTA (c, j) sums chunk c of
+// column j; partials P[c][j] for reduce_dev_kernel (na = ncols, nb = 1).  The Rayleigh quotients
+// and residual norms of a set of vectors need only these, not the full Gram matrices.
+template <typename T, bool C>
+__global__ void __launch_bounds__(256) dots_cols_kernel(const void* Av, const void* Bv, long long n, int ncols,
+                                                        int rows_per_cta, double2* __restrict__ P) {
+  using E = Elem<T, C>;
+  using V = typename E::V;
+  const int j = blockIdx.y;
+  const V* A = static_cast<const V*>(Av) + (size_t)j * n;
+  const V* B = static_cast<const V*>(Bv) + (size_t)j * n;
+  const long long r0 = (long long)blockIdx.x * rows_per_cta;
+  const long long r1 = min(n, r0 + rows_per_cta);
+  double sr = 0.0, si = 0.0;
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const double ar = E::re(A[r]), ai = E::im(A[r]), br = E::re(B[r]), bi = E::im(B[r]);
+    sr = fma(ar, br, sr);
+    if constexpr (C) {
+      sr = fma(ai, bi, sr);
+      si = fma(ar, bi, si);
+      si = fma(-ai, br, si);
+    }
+  }
+  __shared__ double red[2][8];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[0][warp] = sr; red[1][warp] = si; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
+    P[(size_t)blockIdx.x * ncols + j] = make_double2(a, b);
+  }
+}
+
+__global__ void dots_cols_df_kernel(const float2* __restrict__ A, const float2* __restrict__ B, long long n, int ncols,
+                                    int rows_per_cta, double2* __restrict__ P) {
+  const int j = blockIdx.y;
+  A += (size_t)j * n;
+  B += (size_t)j * n;
+  const long long r0 = (long long)blockIdx.x * rows_per_cta;
+  const long long r1 = min(n, r0 + rows_per_cta);
+  float S = 0.f, Cc = 0.f;
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) df_mac(S, Cc, A[r], B[r]);
+  double v = (double)S + (double)Cc;
+  __shared__ double red[8];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+    P[(size_t)blockIdx.x * ncols + j] = make_double2(a, 0.0);
+  }
+}
+
 // ---- double-float Krylov kernels (precision OMEN_F64_DF): real vectors of (hi, lo) pairs,
 // products and sums in double-float arithmetic on the FP32 pipe (df.cuh); partial sums and
 // coefficients cross to and from FP64 once per thread and row respectively.
@@ -997,6 +1056,35 @@ struct KrylovOps {
         need = std::max(need, (size_t)((n + rows - 1) / rows) * na * 4);
       }
     return need;
+  }
+
+  // out (host, ncols) = <A_j, B_j> for each column j
+  omen_status dots_cols(const void* A, const void* B, int ncols, std::vector<cd>& out) {
+    out.assign(ncols, cd(0));
+    if ((size_t)ncols > small_cap) return set_err(ctx, OMEN_EINVAL, "too many columns");
+    const long long rows = dot_rows(ncols, 1);
+    const long long nchunks = (n + rows - 1) / rows;
+    omen_status s1 = ensure_partial((size_t)nchunks * ncols);
+    if (s1 != OMEN_OK) return s1;
+    dim3 grid((unsigned)nchunks, ncols);
+    if (prec == OMEN_F64_DF)
+      dots_cols_df_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const float2*>(A), static_cast<const float2*>(B), n, ncols,
+                                                          (int)rows, d_partial);
+    else if (prec == OMEN_F64) {
+      if (cplx) dots_cols_kernel<double, true><<<grid, 256, 0, ctx->stream>>>(A, B, n, ncols, (int)rows, d_partial);
+      else dots_cols_kernel<double, false><<<grid, 256, 0, ctx->stream>>>(A, B, n, ncols, (int)rows, d_partial);
+    } else {
+      if (cplx) dots_cols_kernel<float, true><<<grid, 256, 0, ctx->stream>>>(A, B, n, ncols, (int)rows, d_partial);
+      else dots_cols_kernel<float, false><<<grid, 256, 0, ctx->stream>>>(A, B, n, ncols, (int)rows, d_partial);
+    }
+    reduce_dev_kernel<<<ncols, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, ncols, 1, d_small, nullptr, 0, 0);
+    OMEN_CHECK_LAUNCH(ctx);
+    OMEN_CUDA(ctx, cudaMemcpyAsync(out.data(), d_small, sizeof(double2) * ncols, cudaMemcpyDeviceToHost, ctx->stream));
+    OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (const cd& v : out)
+      if (!std::isfinite(v.real()) || !std::isfinite(v.imag()))
+        return set_err(ctx, OMEN_ENUMERIC, "non-finite value in a Krylov inner product");
+    return OMEN_OK;
   }
 
   // grows geometrically (cudaFree synchronises the device, so it must not happen per step)
@@ -1523,23 +1611,27 @@ static omen_status rayleigh_residuals(KrylovOps& op, void* X, void* HX, void* R,
   for (int j0 = 0; j0 < k; j0 += kMaxBlockCols) {
     const int nb = std::min(kMaxBlockCols, k - j0);
     std::vector<cd> g, gh;
-    omen_status s = op.dots(op.col(X, j0), nb, op.col(X, j0), nb, g);
+    // only the diagonals of X^H X, X^H HX and R^H R are needed: column-wise products
+    omen_status s = op.dots_cols(op.col(X, j0), op.col(X, j0), nb, g);
     if (s != OMEN_OK) return s;
-    s = op.dots(op.col(X, j0), nb, op.col(HX, j0), nb, gh);
+    s = op.dots_cols(op.col(X, j0), op.col(HX, j0), nb, gh);
     if (s != OMEN_OK) return s;
     for (int j = 0; j < nb; ++j) {
-      xx[j0 + j] = std::real(g[j + (size_t)j * nb]);
-      lam[j0 + j] = std::real(gh[j + (size_t)j * nb]) / xx[j0 + j];
+      xx[j0 + j] = std::real(g[j]);
+      lam[j0 + j] = std::real(gh[j]) / xx[j0 + j];
     }
     OMEN_CUDA(op.ctx, cudaMemcpyAsync(op.col(R, j0), op.col(HX, j0), (size_t)nb * op.n * op.el, cudaMemcpyDeviceToDevice,
                                       op.ctx->stream));
-    std::vector<cd> D((size_t)nb * nb, cd(0));
-    for (int j = 0; j < nb; ++j) D[j + (size_t)j * nb] = cd(lam[j0 + j]);
-    s = op.combine(op.col(X, j0), nb, D, nb, op.col(R, j0), -1.0, 1.0);
+    // R_j -= lam_j X_j, one column at a time (the coefficient matrix is diagonal)
+    std::vector<double2> lj(nb);
+    for (int j = 0; j < nb; ++j) lj[j] = make_double2(lam[j0 + j], 0.0);
+    OMEN_CUDA(op.ctx, cudaMemcpyAsync(op.d_small, lj.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice, op.ctx->stream));
+    for (int j = 0; j < nb && s == OMEN_OK; ++j)
+      s = op.combine_dev(op.col(X, j0 + j), 1, op.d_small + j, 1, op.col(R, j0 + j), -1.0, 1.0);
     if (s != OMEN_OK) return s;
-    s = op.dots(op.col(R, j0), nb, op.col(R, j0), nb, g);
+    s = op.dots_cols(op.col(R, j0), op.col(R, j0), nb, g);
     if (s != OMEN_OK) return s;
-    for (int j = 0; j < nb; ++j) res[j0 + j] = std::sqrt(std::max(0.0, std::real(g[j + (size_t)j * nb])) / xx[j0 + j]);
+    for (int j = 0; j < nb; ++j) res[j0 + j] = std::sqrt(std::max(0.0, std::real(g[j])) / xx[j0 + j]);
   }
   return OMEN_OK;
 }
