@@ -228,20 +228,31 @@ def measure_eigs_1m(ctx, omen, lat, p, nev=16, only=None):
     pipe; and spin-orbit complex64 + FP64 refinement."""
     import torch
     out = {}
-    for name, so, prec, tol in (("f64", False, omen.OMEN_F64, 1e-9), ("f64_double_float", False, omen.OMEN_F64_DF, 1e-9),
-                                ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)):
-        if only and name != only:
+    variants = [("f64", False, omen.OMEN_F64, 1e-9), ("f64_double_float", False, omen.OMEN_F64_DF, 1e-9),
+                ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)]
+    if only == "so-all":
+        # the spin-orbit precision comparison: raw complex64, complex64 + FP64 refinement, and
+        # the complex128 solve as the reference for both
+        variants = [("so_f64", True, omen.OMEN_F64, 1e-9), ("so_f32_raw", True, omen.OMEN_F32, 1e-5),
+                    ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)]
+    evs = {}
+    for name, so, prec, tol in variants:
+        if only and only != "so-all" and name != only:
             continue
         ham = omen.omen_assemble_H(ctx, lat, p, spin_orbit=so, precision=prec)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev, info, st = omen.omen_eigs(ctx, ham, nev, omen.OMEN_LOWEST, tol=tol, block=1 if not so else 2,
-                                      basis=96, max_iter=4000, raise_on_noconv=False)
+                                      basis=96, max_iter=6000, raise_on_noconv=False)
         torch.cuda.synchronize()
         out[name] = {"seconds": time.perf_counter() - t0, "converged": info["converged"], "tol_eV": tol,
                      "iterations": info["iterations"], "hx_count": info["hx_count"],
                      "max_error_bound": info["max_error_bound"], "max_residual_raw": info["max_residual_raw"],
                      "max_residual": info["max_residual"], "lowest": float(ev[0])}
+        evs[name] = np.array(ev)
+        if "so_f64" in evs and name != "so_f64":
+            out[name]["max_abs_diff_vs_f64_eV"] = float(np.abs(evs[name] - evs["so_f64"]).max())
+            out[name]["time_vs_f64"] = out[name]["seconds"] / out["so_f64"]["seconds"]
         del ham
     return out
 
@@ -659,7 +670,8 @@ def main():
                     help="one-off: warm-start network trained on 200 SCF solutions, 20 held-out profiles (minutes)")
     ap.add_argument("--kbatch-full", action="store_true",
                     help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
-    ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube", "so-eigs"],
+    ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube", "so-eigs",
+                                                   "so-all"],
                     help="profiling aid: run one side measurement alone and print its JSON")
     ap.add_argument("--tile", default="", metavar="THREADS,RB",
                     help="fix the H·X launch shape instead of tuning it (e.g. 64,2; profiling aid)")
@@ -688,10 +700,11 @@ def main():
         import torch
         from paper_1003_4570_gb300 import omen
         ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
-        if args.only == "so-eigs":
+        if args.only in ("so-eigs", "so-all"):
             spec, p = synth.config_sige_alloy(args.cells, seed=2)
             lat = omen.omen_build_lattice(ctx, spec)
-            print(json.dumps({args.only: measure_eigs_1m(ctx, omen, lat, p, only="so_f32_refine64")}))
+            which = "so_f32_refine64" if args.only == "so-eigs" else "so-all"
+            print(json.dumps({args.only: measure_eigs_1m(ctx, omen, lat, p, only=which)}))
             return
         fn = {"kbatch": measure_kbatch, "hx-kbatch": measure_hx_kbatch, "scf": measure_scf,
               "small-si": measure_small_si, "cube": measure_cube_500}[args.only]

@@ -34,6 +34,10 @@ CASES = [
     ((5, 4, 7), (0, 0, 0), 10, 2, 0.3, 0.02, False, None, 1, False),
     ((3, 5, 9), (0, 1, 0), 10, 2, 0.3, 0.02, True, None, 1, False),
     ((4, 3, 11), (2, 2, 0), 10, 2, 0.3, 0.02, False, (0.31, -0.52, 0.0), 1, True),
+    # one-cell periodic directions (every lateral bond reaches a periodic image of the same cell)
+    ((1, 1, 6), (2, 2, 0), 10, 2, 0.3, 0.02, False, (1.1, -0.7, 0.0), 0, False),
+    ((1, 1, 1), (1, 1, 1), 5, 1, 0.0, 0.0, False, None, 0, False),
+    ((1, 2, 1), (0, 1, 2), 10, 2, 0.5, 0.02, True, (0.0, 0.0, 0.9), 1, False),
 ]
 
 
