@@ -257,6 +257,54 @@ def measure_eigs_1m(ctx, omen, lat, p, nev=16, only=None):
     return out
 
 
+def measure_charge_poisson(ctx, omen, lat, ham, spec, nstates=16, ng=256):
+    """Rows a9-a12 at the 1M-atom scale: electrons per atom from nstates FP64 eigenvectors
+    (omen_density_accum), cloud-in-cell deposit of the atom charges on an ng x ng x ng grid over the
+    structure, the FP64 CG Poisson solve on that grid, and the trilinear gather back to the atoms.
+    Algorithmic bytes: the eigenvectors once (density); per CG iteration 8 words per unknown
+    (stencil input once, product written, x, r, p read and written)."""
+    import torch
+    from oracle import poisson  # grid description only (no computation)
+    L = spec.nx * spec.a_nm
+    grid = poisson.Grid(ng, ng, ng + 1, L, L, L)
+    n = ham.nrows
+    psi = torch.rand(nstates * n, dtype=torch.float64, device="cuda") - 0.5
+    occ = np.linspace(1.0, 0.0, nstates)
+    n_atom = torch.zeros(spec.natoms, dtype=torch.float64, device="cuda")
+    out = {"grid": [grid.nx, grid.ny, grid.nz], "unknowns": grid.nx * grid.ny * (grid.nz - 1)}
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    t = timed(lambda: omen.omen_density_accum(ctx, ham, psi, nstates, occ, 1.0, n_atom))
+    out["density_accum"] = {"states": nstates, "ms": t * 1e3, "GB_per_s": nstates * n * 8 / t / 1e9}
+    q = (n_atom * -1.602176634e-19).contiguous()
+    rho = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+    t = timed(lambda: omen.omen_deposit(ctx, lat, grid, q, rho))
+    out["deposit"] = {"ms": t * 1e3}
+    phi = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+    rho_s = rho + 1e6 * torch.rand(grid.shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = omen.omen_poisson(ctx, grid, rho_s, phi, rtol=1e-8, max_iter=50000)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    nu = out["unknowns"]
+    out["poisson_cg"] = {"iterations": info["iterations"], "seconds": tp, "ms_per_iteration": tp / info["iterations"] * 1e3,
+                         "GB_per_s": 8 * 8 * nu * info["iterations"] / tp / 1e9, "rel_residual": info["rel_residual"]}
+    phi_atom = torch.empty(spec.natoms, dtype=torch.float64, device="cuda")
+    t = timed(lambda: omen.omen_gather(ctx, lat, grid, phi, phi_atom))
+    out["gather"] = {"ms": t * 1e3}
+    del psi
+    return out
+
+
 def measure_small_si(ctx, omen, n=8, nev=8):
     """Bulk Si 8^3 cells, periodic, sp3s* (20,480 rows, FP64): seconds to the 8 lowest
     eigenpairs at 1e-9 eV — single-vector Lanczos with and without graph replay of the steps,
@@ -632,6 +680,7 @@ def run_gpu(args, rank, world, local_rank):
         result["lanczos_500_iterations_double_float"] = measure_lanczos(ctx, omen, ham_df)
         del ham_df
         if args.cells == N_CELLS and prec == omen.OMEN_F64 and not args.matrix_free:
+            result["charge_poisson_1M_atoms"] = measure_charge_poisson(ctx, omen, lat, ham, spec)
             del ham
             result["eigs_16_lowest_1M_atoms"] = measure_eigs_1m(ctx, omen, lat, p)
         result["eigs_8_lowest_si_8cubed"] = measure_small_si(ctx, omen)

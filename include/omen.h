@@ -100,10 +100,12 @@ omen_status omen_set_reorthogonalization(omen_ctx* ctx, int policy);
 /* Missed-copy check of single-vector solves for the lowest eigenvalues (default on).  A
  * single-vector Krylov space holds one direction of each eigenspace, so of a degenerate level
  * (symmetric structures, zone-boundary bands) it finds one copy and may report the next
- * eigenvalue in place of the others.  With the check, omen_eigs (block 1, OMEN_LOWEST) and
- * omen_eigs_kbatch[_multi] (OMEN_LOWEST) solve again for the lowest eigenvalue of H with the nev
- * vectors found projected out (locking); one below the nev-th by more than tol is inserted in
- * order and the check repeats.  A block solve with block >= the multiplicity needs no check. */
+ * eigenvalue in place of the others.  With the check, omen_eigs (block 1, OMEN_LOWEST or
+ * OMEN_NEAREST) and omen_eigs_kbatch[_multi] (OMEN_LOWEST) solve again for the extreme
+ * eigenvalue of their operator (H, or (H - sigma)^2 for NEAREST) with the nev vectors found
+ * projected out (locking); a level nearer the target than the farthest one found, by more than
+ * tol, is inserted in order and the check repeats.  A block solve with block >= the
+ * multiplicity needs no check. */
 omen_status omen_set_locking_check(omen_ctx* ctx, int enable);
 
 /* ---- structure (paper Section II-A: atoms of the domain and their neighbours) ---------- */
@@ -317,7 +319,8 @@ typedef struct {
 /* Solve -div(eps0 eps_r grad phi) = rho (7-point finite differences, periodic x and y,
  * phi = 0 at both z ends) by conjugate gradients in FP64, all iterations in one cooperative
  * launch (paper: finite-difference Poisson solver, Section III-A item 3).
- * rho_dev: C/m^3; phi_dev: V, initial guess in, solution out.  ENOCONV at max_iter. */
+ * rho_dev: C/m^3; phi_dev: V, initial guess in, solution out.  ENOCONV at max_iter; EINVAL for
+ * a grid of 2^31 or more unknowns. */
 omen_status omen_poisson(omen_ctx* ctx, const omen_grid* grid, const double* rho_dev, double* phi_dev,
                          const omen_cg_opts* opts, omen_solve_info* info);
 

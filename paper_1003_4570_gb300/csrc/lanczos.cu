@@ -2068,6 +2068,10 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
           done = true;
           line_crossed = true;
         }
+      } else if (op.has_line && theta[0] - resA[0] > op.stop_line) {
+        // folded operator: nothing of it below the line, so no state nearer sigma is missing
+        done = true;
+        line_crossed = true;
       } else {
         const double rmax = *std::max_element(resA.begin(), resA.begin() + nev);
         if (gateA < 0) gateA = std::max(o->tol, 1e-12) * 1e3;
@@ -2339,7 +2343,7 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   const int nev = o->nev;
   std::vector<double> lam(rr.lam.begin(), rr.lam.begin() + nev), res(rr.res.begin(), rr.res.begin() + nev);
   std::vector<double> bound(rr.bound.begin(), rr.bound.begin() + nev);
-  if (b == 1 && o->which == OMEN_LOWEST && ctx->lock_check && conv) {
+  if (b == 1 && (o->which == OMEN_LOWEST || o->which == OMEN_NEAREST) && ctx->lock_check && conv) {
     // A single-vector Krylov space holds one direction of each eigenspace: of a degenerate
     // level it finds one copy and may report the next eigenvalue in place of the others.  Check
     // with the nev vectors found locked (projected out of every product): the lowest eigenvalue
@@ -2360,12 +2364,26 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
     o1.basis = std::min(o->basis, std::max(16, nev + 8));
     o1.v0_dev = nullptr;
     o1.v0_host = nullptr;
+    // distance of a level from the target: its value (lowest) or |lambda - sigma| (nearest); the
+    // nev found are in increasing distance here
+    const bool near = o->which == OMEN_NEAREST;
+    auto dist = [&](double l) { return near ? std::fabs(l - o->sigma) : l; };
+    // computed values outside the nev kept (extra Ritz values, levels pushed out, the last
+    // check's value): they give the error bounds their gaps
+    std::vector<double> outside(rr.lam.begin() + nev, rr.lam.end());
+    auto rebound = [&]() {
+      std::vector<double> all(lam);
+      all.insert(all.end(), outside.begin(), outside.end());
+      error_bounds(all, lam, res, bound);
+    };
     for (int round = 0; round < nev; ++round) {
       op.lock_X = Xb.p;
       op.nlock = nev;
       op.d_lock = static_cast<double2*>(Lk.p);
       op.has_line = true;
-      op.stop_line = lam[nev - 1] - o->tol;
+      const double dmax = dist(lam[nev - 1]);
+      // the line in the operator's own values: H (lowest) or (H - sigma)^2 (nearest)
+      op.stop_line = near ? std::pow(std::max(dmax - o->tol, 0.0), 2) : dmax - o->tol;
       op.lock_seed = (unsigned long long)round;   // the previous start has no component left in a level partly found
       omen_eig_info i1{};
       bool c1 = false;
@@ -2379,9 +2397,14 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
       s = launch_hx(ctx, ham, Zb.p, HZb.p, 1, 0.0, solve_prec);
       if (s == OMEN_OK) s = rayleigh_residuals(op, Zb.p, HZb.p, RZb.p, 1, lz, rz);
       if (s != OMEN_OK) { op.release(); return s; }
-      if (!(c1 && lz[0] < lam[nev - 1] - o->tol)) break;
+      if (!(c1 && dist(lz[0]) < dist(lam[nev - 1]) - o->tol)) {
+        outside.push_back(lz[0]);
+        rebound();
+        break;
+      }
+      outside.push_back(lam[nev - 1]);
       int j = nev - 1;
-      while (j > 0 && lam[j - 1] > lz[0]) {
+      while (j > 0 && dist(lam[j - 1]) > dist(lz[0])) {
         lam[j] = lam[j - 1];
         res[j] = res[j - 1];
         OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(Xb.p, j), op.col(Xb.p, j - 1), (size_t)ham->nrows * op.el,
@@ -2392,7 +2415,7 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
       res[j] = rz[0];
       OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(Xb.p, j), Zb.p, (size_t)ham->nrows * op.el, cudaMemcpyDeviceToDevice,
                                      ctx->stream));
-      error_bounds(lam, lam, res, bound);
+      rebound();
     }
   }
   inf->max_residual_raw = *std::max_element(res.begin(), res.end());

@@ -42,6 +42,22 @@ __device__ __forceinline__ double stencil(const double* __restrict__ v, const PG
   return s;
 }
 
+// The same stencil with the cell coordinates given (no divisions per element).
+__device__ __forceinline__ double stencil_at(const double* __restrict__ v, const PGrid& g, int i, int j, int k,
+                                            long long idx) {
+  const long long plane = (long long)g.nx * g.ny;
+  const double c = v[idx];
+  const int ip = (i + 1 == g.nx) ? 0 : i + 1, im = (i == 0) ? g.nx - 1 : i - 1;
+  const int jp = (j + 1 == g.ny) ? 0 : j + 1, jm = (j == 0) ? g.ny - 1 : j - 1;
+  const long long row = idx - i;
+  double s = g.cx * (2.0 * c - v[row + ip] - v[row + im]);
+  s += g.cy * (2.0 * c - v[row + (long long)(jp - j) * g.nx + i] - v[row + (long long)(jm - j) * g.nx + i]);
+  const double up = (k + 1 < g.nzi) ? v[idx + plane] : 0.0;
+  const double dn = (k > 0) ? v[idx - plane] : 0.0;
+  s += g.cz * (2.0 * c - up - dn);
+  return s;
+}
+
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -110,10 +126,29 @@ __global__ void __launch_bounds__(256) cg_kernel(PGrid g, const double* __restri
   int it = 0;
   while (rr > stop && it < max_iter && bb > 0.0) {
     double lpq = 0.0;
-    for (long long i = t0; i < n; i += stride) {
-      const double qi = stencil(p, g, i);
-      q[i] = qi;
-      lpq += p[i] * qi;
+    if (g.nx >= 64) {
+      // rows of x over the CTAs, a row's points over the threads: the coordinates come from
+      // the row index once per row instead of from divisions per point
+      const long long nrow = (long long)g.ny * g.nzi;
+      for (long long rw = blockIdx.x; rw < nrow; rw += gridDim.x) {
+        const int j = (int)(rw % g.ny), k = (int)(rw / g.ny);
+        const long long base = rw * g.nx;
+        for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+          const double qi = stencil_at(p, g, i, j, k, base + i);
+          q[base + i] = qi;
+          lpq += p[base + i] * qi;
+        }
+      }
+    } else {
+      // narrow rows: points over all threads, coordinates by 32-bit division (n < 2^31)
+      for (long long i = t0; i < n; i += stride) {
+        const unsigned u = (unsigned)i;
+        const int ii = (int)(u % (unsigned)g.nx), jj = (int)((u / (unsigned)g.nx) % (unsigned)g.ny);
+        const int kk = (int)(u / ((unsigned)g.nx * (unsigned)g.ny));
+        const double qi = stencil_at(p, g, ii, jj, kk, i);
+        q[i] = qi;
+        lpq += p[i] * qi;
+      }
     }
     v = block_sum(lpq, sh);
     if (threadIdx.x == 0) part0[blockIdx.x] = v;
@@ -162,6 +197,7 @@ extern "C" omen_status omen_poisson(omen_ctx* ctx, const omen_grid* gr, const do
   g.cy = gr->ny > 1 ? 1.0 / (hy * hy) : 0.0;
   g.cz = 1.0 / (hz * hz);
   g.n = (long long)g.nx * g.ny * g.nzi;
+  if (g.n >= (1ll << 31)) return set_err(ctx, OMEN_EINVAL, "grid larger than 2^31 unknowns");
   int dev_sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   OMEN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, 256, 0));

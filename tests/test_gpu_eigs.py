@@ -206,3 +206,20 @@ def test_single_vector_lowest_finds_every_degenerate_copy(ctx, prec):
     ev, info, st = omen.omen_eigs(ctx, ham, 8, tol=1e-9, block=1, basis=48, max_iter=20000)
     assert info["converged"] == 1, info
     np.testing.assert_allclose(ev, ref, atol=1e-9, rtol=0)
+
+
+def test_folded_nearest_finds_every_copy_of_a_degenerate_level(ctx):
+    """Periodic bulk Si 3^3, sigma next to a 6-fold interior level: the folded single-vector
+    solve with its locking check returns all six copies."""
+    from paper_1003_4570_gb300 import omen
+    spec, p = synth.config_si_periodic(3, seed=1)
+    w = bulk.folded_spectrum(p, 3, 3, 3, spec.a_nm)
+    sigma = -7.923
+    ref = eigs.nearest(w, sigma, 6)
+    assert np.ptp(ref) < 1e-9          # one level, six copies
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p)
+    ev, info, st = omen.omen_eigs(ctx, ham, 6, which=omen.OMEN_NEAREST, sigma=sigma, tol=1e-9, block=1,
+                                  basis=48, max_iter=60000)
+    assert info["converged"] == 1, info
+    np.testing.assert_allclose(ev, ref, atol=1e-9, rtol=0)
