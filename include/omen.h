@@ -172,7 +172,10 @@ omen_status omen_hx(omen_ctx* ctx, const omen_ham* ham, const void* x_dev, void*
 omen_status omen_convert_vectors(omen_ctx* ctx, const void* src_dev, int src_precision, void* dst_dev,
                                  int dst_precision, long long n);
 
-/* The same product with host buffers (copies in and out on the ctx stream; synchronous). */
+/* The same product with host buffers; synchronous.  The copies overlap the product: z-slabs of
+ * x go up on one copy stream while earlier slabs compute on the ctx stream and their rows of y go
+ * down on another (pinned host memory makes the copies asynchronous).  The device buffers and
+ * events are kept in the context between calls. */
 omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* ham, const void* x_host, void* y_host,
                          int nvec, double sigma);
 

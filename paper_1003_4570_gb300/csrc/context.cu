@@ -32,6 +32,8 @@ extern "C" void omen_destroy(omen_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (cudaStream_t st : c->copy_stream)
     if (st) cudaStreamDestroy(st);
+  if (c->host_scratch) cudaFree(c->host_scratch);
+  for (cudaEvent_t e : c->host_events) cudaEventDestroy(e);
   delete c;
 }
 

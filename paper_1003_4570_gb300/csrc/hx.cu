@@ -643,20 +643,21 @@ static omen_status hx_host_pipelined(omen_ctx* ctx, const omen_ham* h, const voi
       return set_err(ctx, OMEN_ECUDA, "could not create a copy stream");
     }
   cudaStream_t sin = ctx->copy_stream[0], sout = ctx->copy_stream[1];
-  std::vector<cudaEvent_t> ev(2 * S + 2, nullptr);
   omen_status st = OMEN_OK;
-  for (auto& e : ev)
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-      e = nullptr;
-      st = set_err(ctx, OMEN_ECUDA, "event creation failed");
-    }
+  while (st == OMEN_OK && ctx->host_events.size() < (size_t)(2 * S + 2)) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = set_err(ctx, OMEN_ECUDA, "event creation failed");
+    else ctx->host_events.push_back(e);
+  }
+  if (st != OMEN_OK) return st;
+  std::vector<cudaEvent_t>& ev = ctx->host_events;
   auto z0 = [&](int i) { return (int)((long long)L->nz * i / S); };
   cudaEvent_t* ein = ev.data();
   cudaEvent_t* ecomp = ev.data() + S;
   cudaEvent_t start = ev[2 * S], done = ev[2 * S + 1];
   cudaError_t e = cudaSuccess;
   if (st == OMEN_OK) {
-    // the buffers were allocated on the context's stream: order the copy streams after it
+    // order the copy streams after the context's stream (earlier work on the buffers)
     e = cudaEventRecord(start, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, start, 0);
@@ -691,8 +692,6 @@ static omen_status hx_host_pipelined(omen_ctx* ctx, const omen_ham* h, const voi
     cudaStreamSynchronize(sin);
     cudaStreamSynchronize(sout);
   }
-  for (cudaEvent_t q : ev)
-    if (q) cudaEventDestroy(q);
   return st;
 }
 
@@ -724,15 +723,23 @@ extern "C" omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* h, const void
       return set_err(ctx, OMEN_ECUDA, "host H·X failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     return OMEN_OK;
   }
-  void *dx = nullptr, *dy = nullptr;
-  if (cudaMallocAsync(&dx, bytes, ctx->stream) != cudaSuccess || cudaMallocAsync(&dy, bytes, ctx->stream) != cudaSuccess) {
-    cudaGetLastError();
-    if (dx) cudaFreeAsync(dx, ctx->stream);
-    return set_err(ctx, OMEN_ENOMEM, "device allocation of %zu bytes failed", bytes);
+  const size_t half = (bytes + 255) / 256 * 256;
+  if (ctx->host_scratch_bytes < 2 * half) {
+    // grow the context's scratch (synchronises the device once; later calls reuse it)
+    OMEN_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->host_scratch) cudaFree(ctx->host_scratch);
+    ctx->host_scratch = nullptr;
+    ctx->host_scratch_bytes = 0;
+    if (cudaMalloc(&ctx->host_scratch, 2 * half) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->host_scratch = nullptr;
+      return set_err(ctx, OMEN_ENOMEM, "device allocation of %zu bytes failed", 2 * half);
+    }
+    ctx->host_scratch_bytes = 2 * half;
   }
+  void* dx = ctx->host_scratch;
+  void* dy = static_cast<char*>(ctx->host_scratch) + half;
   omen_status st = hx_host_pipelined(ctx, h, xh, yh, dx, dy, nvec, sigma);
-  cudaFreeAsync(dx, ctx->stream);
-  cudaFreeAsync(dy, ctx->stream);
   cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
   if (st != OMEN_OK) return st;
   if (e2 != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "host H·X failed: %s", cudaGetErrorString(e2));

@@ -23,6 +23,11 @@ struct omen_ctx {
   bool lock_check = true;               // single-vector lowest solves check for missed copies
   cudaStream_t cap_stream = nullptr;   // private stream the captures are recorded on
   cudaStream_t copy_stream[2] = {nullptr, nullptr};  // host<->device copies overlapped with H·X
+  // device buffers of the host-buffer product, kept between calls (grown, never shrunk): a fresh
+  // allocation per call costs more than the copies it serves
+  void* host_scratch = nullptr;
+  size_t host_scratch_bytes = 0;
+  std::vector<cudaEvent_t> host_events;  // the pipeline's events, created once
 };
 
 struct omen_lattice {
