@@ -100,8 +100,8 @@ omen_status omen_set_reorthogonalization(omen_ctx* ctx, int policy);
 /* Missed-copy check of single-vector solves for the lowest eigenvalues (default on).  A
  * single-vector Krylov space holds one direction of each eigenspace, so of a degenerate level
  * (symmetric structures, zone-boundary bands) it finds one copy and may report the next
- * eigenvalue in place of the others.  With the check, omen_eigs (block 1, OMEN_LOWEST or
- * OMEN_NEAREST) and omen_eigs_kbatch[_multi] (OMEN_LOWEST) solve again for the extreme
+ * eigenvalue in place of the others.  With the check, omen_eigs (block 1) and
+ * omen_eigs_kbatch[_multi] (OMEN_LOWEST or OMEN_NEAREST) solve again for the extreme
  * eigenvalue of their operator (H, or (H - sigma)^2 for NEAREST) with the nev vectors found
  * projected out (locking); a level nearer the target than the farthest one found, by more than
  * tol, is inserted in order and the check repeats.  A block solve with block >= the

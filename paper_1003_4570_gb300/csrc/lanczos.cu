@@ -2773,7 +2773,11 @@ static omen_status kbatch_core(omen_ctx* ctx, const std::vector<KbatchInput>& in
       conv[p] = *std::max_element(bd.begin(), bd.end()) <= o->tol;
       // nothing of the deflated operator below the line: done (Weyl: an eigenvalue lies
       // within the residual of the lowest Ritz value, and Lanczos finds the lowest first)
-      if (lock.stop_above && !folded && theta[p][0] - res[0] > (*lock.stop_above)[p]) conv[p] = 1;
+      if (lock.stop_above) {
+        // the line is in the operator's own values: H, or (H - sigma)^2 for the folded solve
+        const double r0 = folded ? std::fabs(betas[p]) * std::abs(Y[p][jstart]) : res[0];
+        if (theta[p][0] - r0 > (*lock.stop_above)[p]) conv[p] = 1;
+      }
     }
     bool all = true;
     for (int p = 0; p < P; ++p) {
@@ -2914,8 +2918,18 @@ static omen_status kbatch_solve(omen_ctx* ctx, const std::vector<KbatchInput>& i
   int iters = main.iterations, restarts = main.restarts, rounds = 0, inserted = 0;
   long long hx = main.hx;
   std::vector<char> conv = main.conv;
-  if (o->which == OMEN_LOWEST) {
+  if (o->which == OMEN_LOWEST || o->which == OMEN_NEAREST) {
     const double margin = o->tol;
+    const bool near = o->which == OMEN_NEAREST;
+    auto dist = [&](double l) { return near ? std::fabs(l - o->sigma) : l; };
+    // the kept level farthest from the target (the last for the lowest eigenvalues)
+    auto farthest = [&](int p) {
+      const double* lp = main.lam.data() + (size_t)p * nev;
+      int f = nev - 1;
+      for (int i = 0; i < nev; ++i)
+        if (dist(lp[i]) > dist(lp[f])) f = i;
+      return f;
+    };
     omen_eig_opts o1 = *o;
     o1.nev = 1;
     o1.v0_dev = nullptr;
@@ -2924,8 +2938,11 @@ static omen_status kbatch_solve(omen_ctx* ctx, const std::vector<KbatchInput>& i
     // run only the problems the previous round changed
     std::vector<char> todo(P, 1);
     for (; rounds < nev; ++rounds) {
-      std::vector<double> line(P);
-      for (int p = 0; p < P; ++p) line[p] = main.lam[(size_t)p * nev + nev - 1] - margin;
+      std::vector<double> line(P), dline(P);
+      for (int p = 0; p < P; ++p) {
+        dline[p] = dist(main.lam[(size_t)p * nev + farthest(p)]) - margin;
+        line[p] = near ? std::pow(std::max(dline[p], 0.0), 2) : dline[p];
+      }
       KLock lk;
       lk.X = X.p;
       lk.n = nev;
@@ -2943,11 +2960,18 @@ static omen_status kbatch_solve(omen_ctx* ctx, const std::vector<KbatchInput>& i
         if (!todo[p]) continue;
         todo[p] = 0;
         const double mu = chk.lam[p];
-        if (!(mu < line[p])) continue;
+        if (!(dist(mu) < dline[p])) continue;
         if (!chk.conv[p]) { conv[p] = 0; continue; }
-        // insert mu at its place in problem p's ascending list; the last pair drops out
+        // the farthest kept pair drops out; mu goes in at its place in the ascending list
         double* lp = main.lam.data() + (size_t)p * nev;
         double* rp = main.res.data() + (size_t)p * nev;
+        for (int i = farthest(p); i < nev - 1; ++i) {
+          lp[i] = lp[i + 1];
+          rp[i] = rp[i + 1];
+          OMEN_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(X.p) + (size_t)i * blk + (size_t)off[p] * el,
+                                         static_cast<char*>(X.p) + (size_t)(i + 1) * blk + (size_t)off[p] * el,
+                                         (size_t)len[p] * el, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
         int j = nev - 1;
         while (j > 0 && lp[j - 1] > mu) {
           lp[j] = lp[j - 1];

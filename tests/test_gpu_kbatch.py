@@ -164,3 +164,23 @@ def test_kbatch_finds_every_copy_of_degenerate_levels(ctx, prec):
     for q, kv in enumerate(ks):
         dense = np.linalg.eigvalsh(hamiltonian.assemble(spec, p, kvec=kv).toarray())[:6]
         np.testing.assert_allclose(ev[q], dense, atol=(1e-9 if prec == 0 else 2e-5), rtol=0)
+
+
+def test_kbatch_nearest_finds_every_copy_of_degenerate_levels(ctx):
+    """Folded (nearest-sigma) lockstep solve on the symmetric pure-Si slab: at the zone boundary
+    the 6 levels nearest sigma are three degenerate pairs; the locking check must return both
+    copies of each (and the non-degenerate set at an interior k)."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(2, 2, 4, (2, 2, 0), seed=64)
+    p = synth.gapped_si_params()
+    Lx = spec.nx * spec.a_nm
+    ks = np.array([[np.pi / Lx, 0.0, 0.0], [0.3 * np.pi / Lx, 0.0, 0.0]])
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, k=(0.0, 0.0, 0.0))
+    sigma = -1.0
+    ev, info, st = omen.omen_eigs_kbatch(ctx, ham, ks, 6, which=omen.OMEN_NEAREST, sigma=sigma, tol=1e-8,
+                                         max_iter=60000, basis=64)
+    assert info["converged"] == 1, info
+    for q, kv in enumerate(ks):
+        dense = np.linalg.eigvalsh(hamiltonian.assemble(spec, p, kvec=kv).toarray())
+        np.testing.assert_allclose(ev[q], eigs.nearest(dense, sigma, 6), atol=1e-8, rtol=0)
