@@ -674,7 +674,8 @@ def run_gpu(args, rank, world, local_rank):
               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": ham.nrows * el,
                       "d2h_bytes_per_step": ham.nrows * el},
               "clocks": clk.summary()}
-    if not args.no_extras:
+    if not args.no_extras and world == 1:
+        # side measurements on one GPU only (a multi-GPU run measures the replicated product)
         result["hx_variants"] = measure_variants(ctx, omen, lat, p, natoms, nbonds)
         result["lanczos_500_iterations"] = measure_lanczos(ctx, omen, ham)
         ham_df = omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F64_DF)
@@ -690,7 +691,7 @@ def run_gpu(args, rank, world, local_rank):
         result["hx_kbatch"] = measure_hx_kbatch(ctx, omen)
         result["kbatch"] = measure_kbatch(ctx, omen)
         result["scf_learned_vs_zero"] = measure_scf(ctx, omen)
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:
         t0 = time.perf_counter()
         cspec, H, cnb = cpu_sample()
         v, dtc = time_cpu_oracle(H, cnb, cspec.natoms, 10)

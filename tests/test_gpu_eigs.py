@@ -193,10 +193,11 @@ def test_double_float_krylov_matches_fp64_oracle(ctx):
     assert np.all(r ** 2 / gaps <= 1e-9)
 
 
-@pytest.mark.parametrize("prec", [0, 3])
+@pytest.mark.parametrize("prec", [0, 2, 3])
 def test_single_vector_lowest_finds_every_degenerate_copy(ctx, prec):
     """Periodic bulk Si 3^3: a 6-fold level sits among the lowest 8.  The single-vector solve
-    (FP64, or double-float Krylov vectors) with its locking check returns it with multiplicity."""
+    (FP64, FP32 refined in FP64, or double-float Krylov vectors) with its locking check returns
+    it with multiplicity."""
     from paper_1003_4570_gb300 import omen
     spec, p = synth.config_si_periodic(3, seed=1)
     ref = bulk.folded_spectrum(p, 3, 3, 3, spec.a_nm)[:8]
