@@ -247,3 +247,37 @@ def mlp_init(seed: int, sizes=(256, 512, 512, 256)) -> np.ndarray:
         parts.append(g.uniform(-a, a, size=fan_out * fan_in))
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts).astype(np.float32)
+
+
+# Effective-mass grids ------------------------------------------------------------------------
+
+STREAM_EFFMASS = 8
+SI_M_LONG, SI_M_TRANS = 0.916, 0.19          # Si conduction-band valley masses (units of m0)
+
+
+@dataclass
+class EffMassSpec:
+    """Uniform nx x ny x nz grid for the single-band effective-mass Hamiltonian.  Point index
+    i = (iz*ny + iy)*nx + ix; U (eV per point, flat in that order) or None."""
+    nx: int
+    ny: int
+    nz: int
+    h_nm: tuple = (0.2, 0.2, 0.2)
+    m_rel: tuple = (SI_M_TRANS, SI_M_TRANS, SI_M_LONG)
+    periodic: tuple = (0, 0, 0)
+    ec_eV: float = 0.0
+    kvec: tuple = None
+    U: np.ndarray = None
+
+    @property
+    def npoints(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def effmass_spec(nx: int, ny: int, nz: int, seed: int = 0, periodic=(0, 0, 0), h_nm=(0.2, 0.2, 0.2),
+                 m_rel=(SI_M_TRANS, SI_M_TRANS, SI_M_LONG), ec_eV: float = 0.0, kvec=None,
+                 u_amp: float = 0.1) -> EffMassSpec:
+    """A grid with a seeded random potential U ~ U[-u_amp, u_amp] eV per point (stream 8)."""
+    U = rng(seed, STREAM_EFFMASS).uniform(-u_amp, u_amp, size=nx * ny * nz) if u_amp > 0 else None
+    return EffMassSpec(nx, ny, nz, tuple(h_nm), tuple(m_rel), tuple(periodic), ec_eV,
+                       None if kvec is None else tuple(kvec), U)
