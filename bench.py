@@ -381,6 +381,46 @@ def measure_hx_kbatch(ctx, omen, nxy=4, nz=80, nk=32, seed=7, reps=20):
     return {"rows": ham.nrows, "k": nk, "ms": ms, "alg_GB": alg / 1e9, "GB_per_s": alg / ms / 1e6}
 
 
+def measure_effmass(ctx, omen, n=256, reps=50, n_eig=64, nev=16):
+    """The effective-mass product (7-point stencil) on an n^3 grid of Si conduction-band
+    masses (periodic x, y; hard walls in z), FP64 / FP32 / complex (Bloch) vectors, one and four
+    per launch; then the 16 lowest levels of an n_eig^3 box with a seeded random potential."""
+    import torch
+    hbm = float(measured_peaks().get("hbm_gbs", 6800.0))
+    out = {"grid": [n, n, n], "points": n ** 3}
+    for name, prec, bloch, nvec in (("f64", omen.OMEN_F64, False, 1), ("f32", omen.OMEN_F32, False, 1),
+                                    ("c128_bloch", omen.OMEN_F64, True, 1), ("f64_4_vectors", omen.OMEN_F64, False, 4)):
+        spec = synth.effmass_spec(n, n, n, seed=3, periodic=(2, 2, 0) if bloch else (1, 1, 0),
+                                  kvec=(0.4, -0.3, 0.0) if bloch else None)
+        ham = omen.omen_assemble_effmass(ctx, spec, precision=prec, U_dev=torch.from_numpy(spec.U).cuda())
+        el = (4 if prec == omen.OMEN_F32 else 8) * (2 if bloch else 1)
+        x = torch.ones(nvec * ham.nrows * el // 4, dtype=torch.float32, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            omen.omen_hx(ctx, ham, x, y, nvec=nvec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            omen.omen_hx(ctx, ham, x, y, nvec=nvec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        # x read once and y written once per vector, the potential once per launch
+        alg = nvec * 2 * el * ham.nrows + (4 if prec == omen.OMEN_F32 else 8) * ham.nrows
+        out[name] = {"ms": ms, "alg_GB": alg / 1e9, "GB_per_s": alg / ms / 1e6,
+                     "frac_of_measured_hbm": alg / ms / 1e6 / hbm}
+        del ham, x, y
+    spec = synth.effmass_spec(n_eig, n_eig, n_eig, seed=5, u_amp=0.05)
+    ham = omen.omen_assemble_effmass(ctx, spec, U_dev=torch.from_numpy(spec.U).cuda())
+    t0 = time.perf_counter()
+    ev, info, _ = omen.omen_eigs(ctx, ham, nev, tol=1e-9, block=1, basis=64, max_iter=20000)
+    out[f"eigs_{nev}_lowest_{n_eig}cubed_box"] = {
+        "seconds": time.perf_counter() - t0, "converged": info["converged"], "iterations": info["iterations"],
+        "hx_count": info["hx_count"], "max_error_bound": info["max_error_bound"], "lowest": float(ev[0])}
+    return out
+
+
 def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
     """Bands/s of the lockstep k-batched solve against one solve per k (same solver, nk = 1)."""
     import torch
@@ -691,6 +731,7 @@ def run_gpu(args, rank, world, local_rank):
         result["hx_kbatch"] = measure_hx_kbatch(ctx, omen)
         result["kbatch"] = measure_kbatch(ctx, omen)
         result["scf_learned_vs_zero"] = measure_scf(ctx, omen)
+        result["effective_mass"] = measure_effmass(ctx, omen)
     if rank == 0 and world == 1 and not args.no_cpu:
         t0 = time.perf_counter()
         cspec, H, cnb = cpu_sample()
@@ -722,7 +763,7 @@ def main():
     ap.add_argument("--kbatch-full", action="store_true",
                     help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
     ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube", "so-eigs",
-                                                   "so-all"],
+                                                   "so-all", "effmass"],
                     help="profiling aid: run one side measurement alone and print its JSON")
     ap.add_argument("--tile", default="", metavar="THREADS,RB",
                     help="fix the H·X launch shape instead of tuning it (e.g. 64,2; profiling aid)")
@@ -758,7 +799,7 @@ def main():
             print(json.dumps({args.only: measure_eigs_1m(ctx, omen, lat, p, only=which)}))
             return
         fn = {"kbatch": measure_kbatch, "hx-kbatch": measure_hx_kbatch, "scf": measure_scf,
-              "small-si": measure_small_si, "cube": measure_cube_500}[args.only]
+              "small-si": measure_small_si, "cube": measure_cube_500, "effmass": measure_effmass}[args.only]
         print(json.dumps({args.only: fn(ctx, omen)}))
         return
     if args.lanczos_only:

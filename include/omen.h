@@ -57,7 +57,9 @@ enum {
   OMEN_F32 = 1,          /* FP32 bond blocks and Krylov vectors (complex64 when complex);
                             Lanczos dots, orthogonalisation coefficients and the projected
                             eigenproblem in FP64 */
-  OMEN_F32_REFINE64 = 2, /* OMEN_F32 solve, then an FP64 Rayleigh–Ritz refinement */
+  OMEN_F32_REFINE64 = 2, /* OMEN_F32 solve, then an FP64 Rayleigh–Ritz refinement inside
+                            omen_eigs; the vectors of omen_hx, omen_hx_host and v0 are FP32
+                            (complex64), the eigenvectors omen_eigs returns are FP64 */
   OMEN_F64_DF = 3        /* FP64-accurate H·X on the FP32 pipe: blocks and vectors stored as
                             double-float pairs (hi, lo) of FP32 (value = hi + lo, about 48
                             significant bits), products and sums with error-free
@@ -160,8 +162,38 @@ omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, const omen_t
 void omen_free_ham(omen_ham* ham);
 /* Rows of H, whether it is complex, and the element size in bytes of its vectors. */
 omen_status omen_ham_shape(const omen_ham* ham, long long* nrows, int* is_complex, int* elem_bytes);
-/* Replace the onsite potential (eV per atom, device) without rebuilding bonds. */
+/* Replace the onsite potential (eV per atom, or per grid point of an effective-mass
+ * Hamiltonian; device) without rebuilding bonds. */
 omen_status omen_ham_set_potential(omen_ctx* ctx, omen_ham* ham, const double* U_atom_dev);
+
+/* ---- effective-mass Hamiltonian (paper Section III-A item 1: the Schrödinger solver takes
+ * either the tight-binding or an effective-mass Hamiltonian) ------------------------------ */
+
+typedef struct {
+  int nx, ny, nz;            /* grid points along x, y, z (each >= 1, fewer than 2^30 in all) */
+  double h_nm[3];            /* grid spacings (nm) */
+  double m_rel[3];           /* diagonal effective masses m_d / m0 */
+  int periodic[3];           /* OMEN_HARD_WALL (psi = 0 one spacing past the end points),
+                                OMEN_PERIODIC, or OMEN_BLOCH: psi(r + L_d e_d) =
+                                exp(i k_d L_d) psi(r), L_d = n_d h_d (complex vectors) */
+  double ec_eV;              /* band edge E_c (eV) */
+  double k[3];               /* Bloch wave vector (1/nm), used on OMEN_BLOCH axes */
+  int precision;             /* OMEN_F64, OMEN_F32 or OMEN_F32_REFINE64 (EUNSUPPORTED for
+                                OMEN_F64_DF) */
+} omen_effmass_desc;
+
+/* Single-band effective-mass Hamiltonian with a constant diagonal mass tensor, discretised by
+ * second-order central differences:
+ *   (H psi)_i = (E_c + U_i + 2 sum_d t_d) psi_i - sum_d t_d (psi_{i+e_d} + psi_{i-e_d}),
+ *   t_d = hbar^2 / (2 m0 m_d h_d^2).
+ * Row index i = (iz*ny + iy)*nx + ix.  U_dev: NULL or [nx*ny*nz] potential energy per point
+ * (eV, device, copied).  The result is an omen_ham: omen_hx, omen_hx_host, omen_eigs (all
+ * orderings and block sizes), omen_density_accum (one value per point) and
+ * omen_ham_set_potential (one value per point) take it; the k-batch and launch-shape calls
+ * return EUNSUPPORTED.  Errors: EINVAL (sizes, spacings, masses, flags), EUNSUPPORTED,
+ * ENOMEM. */
+omen_status omen_assemble_effmass(omen_ctx* ctx, const omen_effmass_desc* desc, const double* U_dev,
+                                  omen_ham** out);
 
 /* y = (H - sigma) x for nvec vectors in the Hamiltonian's vector type (device).
  * x and y must not overlap.  This is the operation the Lanczos recurrence repeats. */

@@ -96,6 +96,7 @@ static void free_ham_buffers(omen_ham* h) {
   cudaFree(h->d_onsite);
   cudaFree(h->d_onsite_df);
   cudaFree(h->d_U);
+  cudaFree(h->d_U32);
   cudaFree(h->d_lambda);
 }
 
@@ -251,6 +252,7 @@ extern "C" omen_status omen_ham_shape(const omen_ham* h, long long* nrows, int* 
 
 extern "C" omen_status omen_ham_set_potential(omen_ctx* ctx, omen_ham* h, const double* U) {
   if (!ctx || !h) return set_err(ctx, OMEN_EINVAL, "null argument");
+  if (h->effmass) return effmass_set_potential(ctx, h, U);
   if (U)
     OMEN_CUDA(ctx, cudaMemcpyAsync(h->d_U, U, sizeof(double) * h->lat->natoms, cudaMemcpyDeviceToDevice, ctx->stream));
   else

@@ -130,7 +130,7 @@ extern "C" omen_status omen_density_accum(omen_ctx* ctx, const omen_ham* h, cons
     return set_err(ctx, OMEN_ENOMEM, "occupations");
   }
   OMEN_CUDA(ctx, cudaMemcpyAsync(d_occ, occ_host, sizeof(double) * nstates, cudaMemcpyHostToDevice, ctx->stream));
-  const int N = h->lat->natoms;
+  const int N = (int)(h->nrows / h->nb);   // atoms, or grid points of an effective-mass Hamiltonian
   const unsigned grid = (unsigned)std::min(1024, (N + 255) / 256);
   if (h->is_complex) density_kernel<true><<<grid, 256, 0, ctx->stream>>>(psi, h->nrows, N, h->nb, nstates, d_occ, w, n_atom);
   else density_kernel<false><<<grid, 256, 0, ctx->stream>>>(psi, h->nrows, N, h->nb, nstates, d_occ, w, n_atom);

@@ -608,12 +608,15 @@ static omen_status launch_hx_cells(omen_ctx* ctx, const omen_ham* h, const void*
 }
 
 omen_status launch_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma, int vec_precision) {
+  if (h->effmass) return launch_hx_effmass(ctx, h, x, y, nvec, sigma, vec_precision, ctx->stream);
   return launch_hx_cells(ctx, h, x, y, nvec, sigma, vec_precision, 0, h->lat->ncells, ctx->stream);
 }
 
+// The vector type of the Hamiltonian's products: FP32 for OMEN_F32 and OMEN_F32_REFINE64 (the
+// refinement is internal to omen_eigs), double-float pairs for OMEN_F64_DF, else FP64.
 static int native_precision(const omen_ham* h) {
   if (h->precision == OMEN_F64_DF) return OMEN_F64_DF;
-  return h->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64;
+  return (h->precision == OMEN_F32 || h->precision == OMEN_F32_REFINE64) ? OMEN_F32 : OMEN_F64;
 }
 
 extern "C" omen_status omen_hx(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma) {
@@ -739,7 +742,16 @@ extern "C" omen_status omen_hx_host(omen_ctx* ctx, const omen_ham* h, const void
   }
   void* dx = ctx->host_scratch;
   void* dy = static_cast<char*>(ctx->host_scratch) + half;
-  omen_status st = hx_host_pipelined(ctx, h, xh, yh, dx, dy, nvec, sigma);
+  omen_status st = OMEN_OK;
+  if (h->effmass) {
+    // one copy up, the product, one copy down
+    cudaError_t e = cudaMemcpyAsync(dx, xh, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) st = launch_hx(ctx, h, dx, dy, nvec, sigma, native_precision(h));
+    if (e == cudaSuccess && st == OMEN_OK) e = cudaMemcpyAsync(yh, dy, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess && st == OMEN_OK) st = set_err(ctx, OMEN_ECUDA, "host H·X copies: %s", cudaGetErrorString(e));
+  } else {
+    st = hx_host_pipelined(ctx, h, xh, yh, dx, dy, nvec, sigma);
+  }
   cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
   if (st != OMEN_OK) return st;
   if (e2 != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "host H·X failed: %s", cudaGetErrorString(e2));
@@ -851,6 +863,7 @@ extern "C" omen_status omen_hx_kbatch_multi(omen_ctx* ctx, int nitems, const ome
   omen_status s = OMEN_OK;
   for (int i = 0; i < nitems && s == OMEN_OK; ++i) {
     if (!it[i].ham || !it[i].k_host || it[i].nk < 1) { s = set_err(ctx, OMEN_EINVAL, "structure %d: null argument or nk < 1", i); break; }
+    if (it[i].ham->effmass) { s = set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs on tight-binding Hamiltonians"); break; }
     if (!it[i].ham->bloch) { s = set_err(ctx, OMEN_EINVAL, "structure %d has no Bloch-periodic direction", i); break; }
     s = make_phases(ctx, it[i].ham, it[i].nk, it[i].k_host, &ph[i]);
     items[i] = KItem{it[i].ham, it[i].nk, ph[i], off};
@@ -870,6 +883,7 @@ extern "C" omen_status omen_hx_kbatch_multi(omen_ctx* ctx, int nitems, const ome
 extern "C" omen_status omen_hx_kbatch(omen_ctx* ctx, const omen_ham* h, int nk, const double* k_host, const void* x,
                                       void* y, double sigma) {
   if (!ctx || !h || !k_host || !x || !y || nk < 1) return set_err(ctx, OMEN_EINVAL, "null argument or nk < 1");
+  if (h->effmass) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs on tight-binding Hamiltonians");
   if (!h->bloch) return set_err(ctx, OMEN_EINVAL, "k batch needs a structure with Bloch-periodic directions");
   double2* ph = nullptr;
   omen_status s = make_phases(ctx, h, nk, k_host, &ph);

@@ -72,7 +72,21 @@ struct omen_ham {
   double* d_lambda = nullptr;             // [ns]
   HxTile tile[2];                         // H·X launch shape for FP64 [0] and FP32 [1] vectors
   HxTile ktile[2];                        // the same for the k-batched product
+  // single-band effective-mass Hamiltonian on a uniform grid (lat is null; nb = 1, d_U holds
+  // one potential per grid point, d_U32 its FP32 copy for FP32 vectors)
+  int effmass = 0;
+  int gdim[3] = {0, 0, 0};
+  int gper[3] = {0, 0, 0};
+  double t_hop[3] = {0, 0, 0};            // hbar^2 / (2 m0 m_d h_d^2) (eV)
+  double ec = 0.0;
+  float* d_U32 = nullptr;
 };
+
+// effective-mass product y = (H - sigma) x (effmass.cu)
+omen_status launch_hx_effmass(omen_ctx* ctx, const omen_ham* h, const void* x, void* y, int nvec, double sigma,
+                              int vec_precision, cudaStream_t st);
+// U per grid point (device, eV) or null for zero; refreshes the FP32 copy
+omen_status effmass_set_potential(omen_ctx* ctx, omen_ham* h, const double* U);
 
 // status / error helpers ---------------------------------------------------------------------
 omen_status set_err(omen_ctx* ctx, omen_status s, const char* fmt, ...);

@@ -96,6 +96,7 @@ omen_status tune_loop(omen_ctx* ctx, const std::vector<HxTile>& cand, int reps, 
 
 extern "C" omen_status omen_hx_set_tile(omen_ctx* ctx, omen_ham* h, int vec_precision, int threads, int rb) {
   if (!ctx || !h) return set_err(ctx, OMEN_EINVAL, "null argument");
+  if (h->effmass) return set_err(ctx, OMEN_EUNSUPPORTED, "the effective-mass product has one launch shape");
   if (vec_precision != OMEN_F64 && vec_precision != OMEN_F32) return set_err(ctx, OMEN_EINVAL, "vector precision must be F64 or F32");
   if (!hx_tile_valid(h, vec_precision, threads, rb))
     return set_err(ctx, OMEN_EINVAL, "launch shape (%d threads, %d rows per batch) is not compiled for this Hamiltonian", threads, rb);
@@ -105,6 +106,7 @@ extern "C" omen_status omen_hx_set_tile(omen_ctx* ctx, omen_ham* h, int vec_prec
 
 extern "C" omen_status omen_hx_kbatch_set_tile(omen_ctx* ctx, omen_ham* h, int vec_precision, int threads, int kb) {
   if (!ctx || !h) return set_err(ctx, OMEN_EINVAL, "null argument");
+  if (h->effmass) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs on tight-binding Hamiltonians");
   if (vec_precision != OMEN_F64 && vec_precision != OMEN_F32) return set_err(ctx, OMEN_EINVAL, "vector precision must be F64 or F32");
   if (!hx_kbatch_tile_valid(vec_precision, threads, kb))
     return set_err(ctx, OMEN_EINVAL, "k-batch launch shape (%d threads, %d wave vectors per thread) is not compiled", threads, kb);
@@ -116,6 +118,7 @@ extern "C" omen_status omen_tune_hx(omen_ctx* ctx, omen_ham* h, int vec_precisio
                                     omen_tune_result* out) {
   if (!ctx || !h || nvec < 1 || nvec > 65535 || reps < 1) return set_err(ctx, OMEN_EINVAL, "null argument, nvec or reps out of range");
   if (vec_precision != OMEN_F64 && vec_precision != OMEN_F32) return set_err(ctx, OMEN_EINVAL, "vector precision must be F64 or F32");
+  if (h->effmass) return set_err(ctx, OMEN_EUNSUPPORTED, "the effective-mass product has one launch shape");
   if (!has_blocks(h, vec_precision)) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no blocks of that precision");
   OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
   const size_t bytes = vec_elem_bytes(h, vec_precision) * (size_t)h->nrows * nvec;
@@ -138,7 +141,7 @@ extern "C" omen_status omen_tune_hx(omen_ctx* ctx, omen_ham* h, int vec_precisio
 
 extern "C" omen_status omen_tune_hx_kbatch(omen_ctx* ctx, omen_ham* h, int nk, int reps, omen_tune_result* out) {
   if (!ctx || !h || nk < 1 || nk > 65535 || reps < 1) return set_err(ctx, OMEN_EINVAL, "null argument, nk or reps out of range");
-  if (!h->bloch || h->spin_orbit || h->matrix_free) return set_err(ctx, OMEN_EINVAL, "k batch needs a Bloch Hamiltonian with stored blocks and no spin-orbit");
+  if (h->effmass || !h->bloch || h->spin_orbit || h->matrix_free) return set_err(ctx, OMEN_EINVAL, "k batch needs a Bloch tight-binding Hamiltonian with stored blocks and no spin-orbit");
   const int prec = h->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64;
   if (!has_blocks(h, prec)) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no blocks of its precision");
   OMEN_CUDA(ctx, cudaSetDevice(ctx->device));

@@ -101,6 +101,12 @@ class SCFInfo(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class EffMassDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h_nm", C.c_double * 3),
+                ("m_rel", C.c_double * 3), ("periodic", C.c_int * 3), ("ec_eV", C.c_double),
+                ("k", C.c_double * 3), ("precision", C.c_int)]
+
+
 class MLPDesc(C.Structure):
     _fields_ = [("n_in", C.c_int), ("n_hidden1", C.c_int), ("n_hidden2", C.c_int), ("n_out", C.c_int),
                 ("feat_log10_shift", C.c_double), ("feat_log10_scale", C.c_double), ("target_scale", C.c_double)]
@@ -133,6 +139,7 @@ def lib():
             "omen_lattice_counts": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
             "omen_assemble_H": (i, [vp, vp, C.POINTER(TBParams), C.POINTER(HamOpts), C.POINTER(vp)]),
             "omen_free_ham": (None, [vp]),
+            "omen_assemble_effmass": (i, [vp, C.POINTER(EffMassDesc), vp, C.POINTER(vp)]),
             "omen_ham_shape": (i, [vp, C.POINTER(ll), C.POINTER(i), C.POINTER(i)]),
             "omen_ham_set_potential": (i, [vp, vp, vp]),
             "omen_hx": (i, [vp, vp, vp, vp, i, d]),
@@ -300,6 +307,24 @@ def omen_assemble_H(ctx: Context, lat: Lattice, params, spin_orbit=False, precis
     h = C.c_void_p()
     ctx.check(lib().omen_assemble_H(ctx.handle, lat.handle, C.byref(tp), C.byref(o), C.byref(h)))
     return Hamiltonian(ctx, h, lat)
+
+
+def omen_assemble_effmass(ctx: Context, spec, precision=OMEN_F64, U_dev=None) -> Hamiltonian:
+    """Single-band effective-mass Hamiltonian on a uniform grid.  spec: nx, ny, nz, h_nm[3],
+    m_rel[3], periodic[3], ec_eV, kvec ([3] 1/nm or None); U_dev: device potential per point."""
+    d = EffMassDesc()
+    d.nx, d.ny, d.nz = int(spec.nx), int(spec.ny), int(spec.nz)
+    kv = (0.0, 0.0, 0.0) if spec.kvec is None else spec.kvec
+    for a in range(3):
+        d.h_nm[a] = float(spec.h_nm[a])
+        d.m_rel[a] = float(spec.m_rel[a])
+        d.periodic[a] = int(spec.periodic[a])
+        d.k[a] = float(kv[a])
+    d.ec_eV = float(spec.ec_eV)
+    d.precision = int(precision)
+    h = C.c_void_p()
+    ctx.check(lib().omen_assemble_effmass(ctx.handle, C.byref(d), _ptr(U_dev), C.byref(h)))
+    return Hamiltonian(ctx, h, None)
 
 
 def omen_ham_set_potential(ctx: Context, ham: Hamiltonian, U_atom_dev):

@@ -1,0 +1,176 @@
+"""Effective-mass Hamiltonian on the GPU against the oracle's explicit CSR.
+
+Products element by element (FP64 1e-12 of max|y|, FP32 2e-6 of max|y|: seven terms per row),
+on grids that span several 256-thread blocks with ragged tails, grids larger than one pass of
+the grid-stride loop (so the point coordinates are advanced with carries), one- and two-point
+periodic axes, and Bloch phases.  Eigenvalues against dense LAPACK on the same matrix
+(random potentials lift every degeneracy) and against the closed-form box levels.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import charge, effmass, eigs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1003_4570_gb300 import omen
+    return omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+
+
+def build(ctx, spec, precision):
+    from paper_1003_4570_gb300 import omen
+    Ud = None if spec.U is None else torch.from_numpy(np.ascontiguousarray(spec.U)).cuda()
+    ham = omen.omen_assemble_effmass(ctx, spec, precision=precision, U_dev=Ud)
+    return ham
+
+
+CASES = [
+    # (dims, periodic, kvec, precision, nvec)
+    ((37, 23, 19), (0, 0, 0), None, 0, 1),
+    ((37, 23, 19), (1, 1, 0), None, 0, 3),
+    ((29, 17, 13), (2, 2, 0), (0.8, -1.7, 0.0), 0, 2),
+    ((29, 17, 13), (2, 1, 2), (0.8, 0.0, 2.9), 1, 2),
+    ((37, 23, 19), (1, 0, 1), None, 1, 1),
+    ((70, 67, 71), (1, 1, 0), None, 0, 1),          # 333k points: more than one grid-stride pass
+    ((1000, 3, 121), (2, 0, 1), (0.3, 0.0, 0.0), 0, 1),
+    ((1, 1, 40), (1, 1, 0), None, 0, 2),
+    ((2, 1, 33), (2, 2, 0), (1.3, 0.4, 0.0), 0, 1),
+    ((1, 2, 1), (2, 2, 2), (0.5, -0.6, 0.7), 1, 1),
+    ((5, 1, 1), (0, 0, 0), None, 0, 1),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"c{i}" for i in range(len(CASES))])
+def test_effmass_hx_matches_oracle(ctx, case):
+    from paper_1003_4570_gb300 import omen
+    dims, per, k, prec, nvec = case
+    spec = synth.effmass_spec(*dims, seed=21, periodic=per, kvec=k, h_nm=(0.21, 0.19, 0.23), ec_eV=0.05)
+    H = effmass.assemble(spec)
+    ham = build(ctx, spec, prec)
+    assert ham.nrows == H.shape[0] and ham.is_complex == (H.dtype == np.complex128)
+    sigma = 0.37
+    x = synth.random_vectors(5, H.shape[0], nvec, dtype=complex if ham.is_complex else float)
+    xd = torch.from_numpy(x.astype(ham.numpy_dtype)).cuda()
+    yd = torch.empty_like(xd)
+    omen.omen_hx(ctx, ham, xd, yd, nvec=nvec, sigma=sigma)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    tol = 1e-12 if prec == 0 else 2e-6
+    for v in range(nvec):
+        xv = x[v].astype(ham.numpy_dtype).astype(complex if ham.is_complex else float)
+        ref = H @ xv - sigma * xv
+        err = np.abs(y[v] - ref).max() / np.abs(ref).max()
+        assert err <= tol, (v, err)
+
+
+def test_effmass_host_product_and_potential_update(ctx):
+    from paper_1003_4570_gb300 import omen
+    spec = synth.effmass_spec(31, 9, 27, seed=4, periodic=(1, 1, 0))
+    ham = build(ctx, spec, 0)
+    x = synth.random_vectors(6, ham.nrows, 2)
+    y = omen.omen_hx_host(ctx, ham, x, sigma=-0.2)
+    H = effmass.assemble(spec)
+    for v in range(2):
+        ref = H @ x[v] + 0.2 * x[v]
+        assert np.abs(y[v] - ref).max() <= 1e-12 * np.abs(ref).max()
+    # a new potential, without rebuilding
+    spec.U = synth.rng(9, 99).uniform(-0.3, 0.3, ham.nrows)
+    omen.omen_ham_set_potential(ctx, ham, torch.from_numpy(spec.U).cuda())
+    y = omen.omen_hx_host(ctx, ham, x)
+    H = effmass.assemble(spec)
+    assert np.abs(y[0] - H @ x[0]).max() <= 1e-12 * np.abs(H @ x[0]).max()
+
+
+@pytest.mark.parametrize("prec,which,block", [(0, 0, 1), (0, 0, 4), (0, 1, 1), (2, 0, 1), (1, 0, 2)])
+def test_effmass_eigs_match_dense(ctx, prec, which, block):
+    from paper_1003_4570_gb300 import omen
+    spec = synth.effmass_spec(12, 11, 13, seed=8, periodic=(1, 1, 0), h_nm=(0.25, 0.25, 0.2), ec_eV=0.0)
+    H = effmass.assemble(spec)
+    w = np.linalg.eigvalsh(H.toarray())
+    ham = build(ctx, spec, prec)
+    nev = 8
+    tol = 1e-5 if prec == 1 else 1e-9
+    if which == 0:
+        ref = w[:nev]
+        ev, info, _ = omen.omen_eigs(ctx, ham, nev, tol=tol, block=block, basis=48, max_iter=20000)
+    else:
+        sigma = float(0.5 * (w[60] + w[61]) + 0.003)
+        ref = eigs.nearest(w, sigma, nev)
+        ev, info, _ = omen.omen_eigs(ctx, ham, nev, which=omen.OMEN_NEAREST, sigma=sigma, tol=tol, block=block,
+                                     basis=48, max_iter=60000)
+    assert info["converged"] == 1, info
+    np.testing.assert_allclose(np.sort(ev), ref, atol=10 * tol, rtol=0)
+
+
+def test_effmass_bloch_eigs_and_density(ctx):
+    """Complex (Bloch) grid: the lowest levels against dense LAPACK; the density of the returned
+    eigenvectors against the oracle's from dense eigenvectors (random potential: no degeneracy),
+    within the Davis–Kahan bound ||d psi|| <= r / gap of each vector's error."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.effmass_spec(9, 8, 14, seed=12, periodic=(2, 2, 0), kvec=(0.9, -0.4, 0.0))
+    H = effmass.assemble(spec)
+    w, V = np.linalg.eigh(H.toarray())
+    ham = build(ctx, spec, 0)
+    nev = 6
+    ev_d = torch.empty((nev, ham.nrows), dtype=torch.complex128, device="cuda")
+    ev, info, _ = omen.omen_eigs(ctx, ham, nev, tol=1e-10, block=1, basis=40, max_iter=20000, evecs_dev=ev_d)
+    assert info["converged"] == 1, info
+    np.testing.assert_allclose(ev, w[:nev], atol=1e-9, rtol=0)
+    occ = np.array([1.0, 0.8, 0.5, 0.25, 0.1, 0.0])
+    n_d = torch.zeros(ham.nrows, dtype=torch.float64, device="cuda")
+    omen.omen_density_accum(ctx, ham, ev_d, nev, occ, 2.0, n_d)
+    torch.cuda.synchronize()
+    ref = 2.0 * charge.atom_density(V[:, :nev], occ, ham.nrows)
+    gap = min(np.min(np.abs(np.delete(w, j) - w[j])) for j in range(nev))
+    dpsi = info["max_residual"] / gap
+    bound = 2.0 * sum(f * (2 * np.abs(V[:, j]).max() * dpsi + dpsi ** 2) for j, f in enumerate(occ))
+    assert np.abs(n_d.cpu().numpy() - ref).max() <= 2 * bound + 1e-14
+    assert abs(n_d.sum().item() - 2.0 * occ.sum()) < 1e-10
+
+
+def test_effmass_box_levels_closed_form(ctx):
+    """Constant potential, hard walls, incommensurate masses and spacings: the lowest levels are
+    sums of the three chains' levels 2t(1 - cos(j pi/(n+1)))."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.effmass_spec(40, 33, 57, periodic=(0, 0, 0), h_nm=(0.2, 0.23, 0.17), m_rel=(0.19, 0.26, 0.916),
+                              ec_eV=1.1, u_amp=0.0)
+    t = effmass.hopping(spec)
+    lv = [2 * t[d] * (1 - np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))
+          for d, n in enumerate((spec.nx, spec.ny, spec.nz))]
+    ref = np.sort([1.1 + a + b + c for a, b, c in itertools.product(lv[0][:6], lv[1][:6], lv[2][:6])])[:10]
+    ham = build(ctx, spec, 0)
+    ev, info, _ = omen.omen_eigs(ctx, ham, 10, tol=1e-9, block=1, basis=48, max_iter=20000)
+    assert info["converged"] == 1, info
+    np.testing.assert_allclose(ev, ref, atol=1e-8, rtol=0)
+
+
+def test_effmass_rejections(ctx):
+    from paper_1003_4570_gb300 import omen
+    spec = synth.effmass_spec(4, 4, 4, periodic=(2, 2, 0), kvec=(0.1, 0.2, 0.0))
+    with pytest.raises(omen.OmenError) as e:
+        build(ctx, spec, omen.OMEN_F64_DF)
+    assert e.value.status == omen.OMEN_EUNSUPPORTED
+    bad = synth.effmass_spec(0, 4, 4)
+    with pytest.raises(omen.OmenError) as e:
+        build(ctx, bad, 0)
+    assert e.value.status == omen.OMEN_EINVAL
+    bad = synth.effmass_spec(4, 4, 4, m_rel=(0.2, -1.0, 0.9))
+    with pytest.raises(omen.OmenError) as e:
+        build(ctx, bad, 0)
+    assert e.value.status == omen.OMEN_EINVAL
+    ham = build(ctx, spec, 0)
+    x = torch.zeros((1, ham.nrows), dtype=torch.complex128, device="cuda")
+    with pytest.raises(omen.OmenError) as e:
+        omen.omen_hx_kbatch(ctx, ham, np.zeros((1, 3)), x, torch.empty_like(x))
+    assert e.value.status == omen.OMEN_EUNSUPPORTED
+    with pytest.raises(omen.OmenError) as e:
+        omen.omen_tune_hx(ctx, ham)
+    assert e.value.status == omen.OMEN_EUNSUPPORTED
