@@ -2190,7 +2190,7 @@ static omen_status refine64(KrylovOps& op, void* X, int k, const omen_eig_opts* 
   }
   const bool nearest = o->which == OMEN_NEAREST;
   omen_status s;
-  for (int it = 0; it < 6; ++it) {
+  for (int it = 0; it < 12; ++it) {
     // S = [X, R], R = H X - X Lambda
     OMEN_CUDA(ctx, cudaMemcpyAsync(Sb.p, X, k * vb, cudaMemcpyDeviceToDevice, ctx->stream));
     std::vector<cd> Rq;
@@ -2211,7 +2211,8 @@ static omen_status refine64(KrylovOps& op, void* X, int k, const omen_eig_opts* 
     }
     // append the residuals, orthogonalise them against X and each other
     OMEN_CUDA(ctx, cudaMemcpyAsync(op.col(Sb.p, k), Rb.p, k * vb, cudaMemcpyDeviceToDevice, ctx->stream));
-    s = op.orthogonalise(Sb.p, k, op.col(Sb.p, k), k, nullptr);
+    for (int j0 = 0; j0 < k && s == OMEN_OK; j0 += kMaxBlockCols)
+      s = op.orthogonalise(Sb.p, k, op.col(Sb.p, k + j0), std::min(kMaxBlockCols, k - j0), nullptr);
     if (s != OMEN_OK) return s;
     std::vector<cd> R2;
     s = op.cholqr(op.col(Sb.p, k), k, R2, def);
@@ -2316,9 +2317,15 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
     op.release();
     return set_err(ctx, OMEN_ENOMEM, "Ritz vectors");
   }
+  // An FP32 solve that the FP64 refinement polishes runs to a tighter target: the refinement
+  // (Rayleigh–Ritz on [X, residuals]) removes the FP32 rounding of the vectors quickly but an
+  // unconverged Krylov direction only slowly, so the FP32 phase should end near its own floor.
+  omen_eig_opts oin = *o;
+  if (ham->precision == OMEN_F32_REFINE64) oin.tol = o->tol * 1e-2;
   RitzResult rr;
   bool conv = false;
-  s = (b == 1) ? lanczos_solve_single(op, o, Xb.p, kout, inf, conv) : lanczos_solve(op, o, Xb.p, kout, rr, inf, o->v0_host, conv);
+  s = (b == 1) ? lanczos_solve_single(op, &oin, Xb.p, kout, inf, conv)
+               : lanczos_solve(op, &oin, Xb.p, kout, rr, inf, o->v0_host, conv);
   if (s != OMEN_OK) { op.release(); return s; }
   // evaluate the kout Ritz vectors in the solve precision
   DevBuf HXb, Rb;
@@ -2359,7 +2366,7 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
       op.release();
       return set_err(ctx, OMEN_ENOMEM, "locking check vectors");
     }
-    omen_eig_opts o1 = *o;
+    omen_eig_opts o1 = oin;
     o1.nev = 1;
     o1.basis = std::min(o->basis, std::max(16, nev + 8));
     o1.v0_dev = nullptr;
