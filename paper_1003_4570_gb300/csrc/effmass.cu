@@ -145,7 +145,22 @@ cudaError_t launch_em(const omen_ham* h, const T* U, const void* x, void* y, int
     p.ph[d] = h->phase[d];
   }
   p.d0 = (T)(h->ec + 2.0 * (h->t_hop[0] + h->t_hop[1] + h->t_hop[2]) - sigma);
-  const int blocks = (int)std::min<long long>((h->nrows + 255) / 256, 152LL * 8);
+  // One wave of resident blocks: the grid-stride sweep then advances through the grid as one
+  // front, and the plane below and above the points in flight are still in L2 when read.  (A
+  // second wave would start after the first finished its whole sweep and re-read from DRAM
+  // the planes next to every window the first wave left.)
+  static int resident = 0, sms = 0;
+  if (!resident) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, effmass_hx_kernel<T, C>, 256, 0) != cudaSuccess ||
+        resident < 1 || sms < 1) {
+      cudaGetLastError();
+      resident = 1;
+      sms = 152;
+    }
+  }
+  const int blocks = (int)std::min<long long>((h->nrows + 255) / 256, (long long)sms * resident);
   effmass_hx_kernel<T, C><<<blocks, 256, 0, st>>>(p, U, static_cast<const V*>(x), static_cast<V*>(y), nvec);
   return cudaGetLastError();
 }
