@@ -15,6 +15,7 @@
 // integer division.  The six neighbour indices and a mask of the ones reached across a face are
 // formed once per point and reused for every vector; the hopping energies and phases are
 // kernel parameters, and only an amplitude that crosses a face is multiplied by its phase.
+// Overflow: N < 2^30 and three strides stay far below 2^31.
 #include <algorithm>
 #include <cmath>
 
@@ -75,6 +76,50 @@ __device__ __forceinline__ typename Elem<T, C>::V across(typename Elem<T, C>::V 
   }
 }
 
+// Neighbours q = 2d (low side) and 2d+1 (high side) of axis d of point i at (ix, iy, iz): the
+// index, or -1 past a hard wall; bit q of `wrap` marks a neighbour reached across a face.
+__device__ __forceinline__ void neighbours(const EmGeo& g, int plane, int i, int ix, int iy, int iz, int (&j)[6],
+                                           unsigned& wrap) {
+  const int c[3] = {ix, iy, iz};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const int step[3] = {1, g.nx, plane};
+  wrap = 0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int span = (n[d] - 1) * step[d];
+    if (c[d] > 0) j[2 * d] = i - step[d];
+    else if (g.per[d]) { j[2 * d] = i + span; wrap |= 1u << (2 * d); }
+    else j[2 * d] = -1;
+    if (c[d] < n[d] - 1) j[2 * d + 1] = i + step[d];
+    else if (g.per[d]) { j[2 * d + 1] = i - span; wrap |= 2u << (2 * d); }
+    else j[2 * d + 1] = -1;
+  }
+}
+
+// (dg x_i - sum_q t_q x_j(q)) for one point; WRAP: apply the face phases marked in `wrap`
+template <typename T, bool C, bool WRAP>
+__device__ __forceinline__ typename Elem<T, C>::V stencil(const EmParams<T>& p, const typename Elem<T, C>::V* __restrict__ xv,
+                                                          int i, const int (&j)[6], unsigned wrap, T dg) {
+  using V = typename Elem<T, C>::V;
+  V acc = scale(dg, xv[i]);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (j[q] < 0) continue;
+    V a = xv[j[q]];
+    if constexpr (WRAP) {
+      if (wrap & (1u << q)) a = (q & 1) ? across<T, C, false>(a, p.ph[q / 2]) : across<T, C, true>(a, p.ph[q / 2]);
+    } else {
+      (void)wrap;
+    }
+    mac(acc, -p.t[q / 2], a);
+  }
+  return acc;
+}
+
+// Each thread takes two points per pass, i and i + S (S = the grid's thread count), and issues
+// the loads of both before either sum: twice the bytes in flight per thread.  Complex vectors
+// take the phase path only in the passes that touch a face, so the interior carries no complex
+// rotation.
 template <typename T, bool C>
 __global__ void __launch_bounds__(256) effmass_hx_kernel(EmParams<T> p, const T* __restrict__ U,
                                                          const typename Elem<T, C>::V* __restrict__ x,
@@ -90,42 +135,45 @@ __global__ void __launch_bounds__(256) effmass_hx_kernel(EmParams<T> p, const T*
   int iy = r / g.nx, ix = r - iy * g.nx;
   const int sz = S / plane, rs = S - sz * plane;
   const int sy = rs / g.nx, sx = rs - sy * g.nx;
-  const int step[3] = {1, g.nx, plane};
   for (; i < N;) {
-    // neighbour q = 2d (low side) and 2d+1 (high side) of axis d: index, or -1 past a hard wall;
-    // bit q of `wrap` marks a neighbour reached across a face
-    const int c[3] = {ix, iy, iz};
-    const int n[3] = {g.nx, g.ny, g.nz};
-    int j[6];
-    unsigned wrap = 0;
+    // the second point, one stride on
+    int ib = i + S, bx = ix + sx, by = iy + sy, bz = iz + sz;
+    if (bx >= g.nx) { bx -= g.nx; ++by; }
+    if (by >= g.ny) { by -= g.ny; ++bz; }
+    const bool has_b = ib < N;
+    int ja[6], jb[6];
+    unsigned wa, wb;
+    neighbours(g, plane, i, ix, iy, iz, ja, wa);
+    if (has_b) {
+      neighbours(g, plane, ib, bx, by, bz, jb, wb);
+    } else {
+      // no second point: a stand-in with no neighbours at a valid index, never stored
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int span = (n[d] - 1) * step[d];
-      if (c[d] > 0) j[2 * d] = i - step[d];
-      else if (g.per[d]) { j[2 * d] = i + span; wrap |= 1u << (2 * d); }
-      else j[2 * d] = -1;
-      if (c[d] < n[d] - 1) j[2 * d + 1] = i + step[d];
-      else if (g.per[d]) { j[2 * d + 1] = i - span; wrap |= 2u << (2 * d); }
-      else j[2 * d + 1] = -1;
+      for (int q = 0; q < 6; ++q) jb[q] = -1;
+      wb = 0;
     }
-    const T dg = p.d0 + U[i];
+    const int ibs = has_b ? ib : i;
+    const T dga = p.d0 + U[i], dgb = p.d0 + U[ibs];
+    const bool faces = C && (wa | wb) != 0;
     const V* xv = x;
     V* yv = y;
     for (int v = 0; v < nvec; ++v, xv += N, yv += N) {
-      V acc = scale(dg, xv[i]);
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        if (j[q] < 0) continue;
-        V a = xv[j[q]];
-        if (wrap & (1u << q)) a = (q & 1) ? across<T, C, false>(a, p.ph[q / 2]) : across<T, C, true>(a, p.ph[q / 2]);
-        mac(acc, -p.t[q / 2], a);
+      V ra, rb;
+      if (faces) {
+        ra = stencil<T, C, true>(p, xv, i, ja, wa, dga);
+        rb = stencil<T, C, true>(p, xv, ibs, jb, wb, dgb);
+      } else {
+        ra = stencil<T, C, false>(p, xv, i, ja, 0u, dga);
+        rb = stencil<T, C, false>(p, xv, ibs, jb, 0u, dgb);
       }
-      yv[i] = acc;
+      yv[i] = ra;
+      if (has_b) yv[ib] = rb;
     }
-    i += S;
-    ix += sx;
-    iy += sy;
-    iz += sz;
+    // on to the next pair: two strides from i is one stride from the second point
+    i = ib + S;
+    ix = bx + sx;
+    iy = by + sy;
+    iz = bz + sz;
     if (ix >= g.nx) { ix -= g.nx; ++iy; }
     if (iy >= g.ny) { iy -= g.ny; ++iz; }
   }
