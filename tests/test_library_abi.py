@@ -46,3 +46,41 @@ def test_binding_loads(built_lib):
     L = omen.lib()
     for n in declared_entry_points():
         assert hasattr(L, n)
+
+
+STRUCTS = {
+    "LatticeDesc": "omen_lattice_desc", "TBParams": "omen_tb_params", "HamOpts": "omen_ham_opts",
+    "EigOpts": "omen_eig_opts", "EigInfo": "omen_eig_info", "Grid": "omen_grid", "CGOpts": "omen_cg_opts",
+    "TuneResult": "omen_tune_result", "SolveInfo": "omen_solve_info", "SCFDesc": "omen_scf_desc",
+    "SCFInfo": "omen_scf_info", "EffMassDesc": "omen_effmass_desc", "MLPDesc": "omen_mlp_desc",
+    "KbatchItem": "omen_kbatch_item",
+}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets the C compiler gives
+    the header's struct of the same name (a field renamed, reordered or retyped on one side
+    fails here instead of corrupting arguments at run time)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1003_4570_gb300 import omen
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "omen.h"', "int main(void) {"]
+    expected = []
+    for py, c in STRUCTS.items():
+        cls = getattr(omen, py)
+        lines.append(f'  printf("%zu\\n", sizeof({c}));')
+        expected.append(ctypes.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({c}, {name}));')
+            expected.append(getattr(cls, name).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expected
