@@ -23,4 +23,5 @@ eigs         dense eigensolve, plain Lanczos and folded-spectrum Lanczos with fu
 poisson      3-D finite-difference Poisson (periodic x,y; Dirichlet z) by direct solve and CG.
 charge       Fermi–Dirac filling, Fermi level by bisection, cloud-in-cell deposit and gather.
 effmass      single-band effective-mass Hamiltonian on a uniform grid (explicit CSR).
+vff          Keating valence force field: strain energy, forces, relaxation, bond strains.
 """

@@ -281,3 +281,29 @@ def effmass_spec(nx: int, ny: int, nz: int, seed: int = 0, periodic=(0, 0, 0), h
     U = rng(seed, STREAM_EFFMASS).uniform(-u_amp, u_amp, size=nx * ny * nz) if u_amp > 0 else None
     return EffMassSpec(nx, ny, nz, tuple(h_nm), tuple(m_rel), tuple(periodic), ec_eV,
                        None if kvec is None else tuple(kvec), U)
+
+
+# Valence-force-field parameters ----------------------------------------------------------------
+
+STREAM_VFF = 9
+GE_A_NM = 0.5658                              # germanium lattice constant (nm)
+N_PER_M_IN_EV_PER_NM2 = 1.0 / 1.602176634e-19 * 1e-18   # 1 N/m = 6.2415 eV/nm^2
+
+
+@dataclass
+class VFFParams:
+    """Keating force constants per species: natural lattice constant a (nm), bond stretching
+    alpha and bond bending beta (eV/nm^2)."""
+    a_nm: np.ndarray
+    alpha: np.ndarray
+    beta: np.ndarray
+
+
+def draw_vff_params(seed: int, nspecies: int = 2) -> VFFParams:
+    """Species 0 at the Si lattice constant, species 1 at Ge's; alpha ~ U[38, 50] N/m and
+    beta ~ U[10, 15] N/m per species (stream 9)."""
+    g = rng(seed, STREAM_VFF)
+    a = np.array([SI_A_NM, GE_A_NM, SI_A_NM, GE_A_NM][:nspecies])
+    alpha = g.uniform(38.0, 50.0, size=nspecies) * N_PER_M_IN_EV_PER_NM2
+    beta = g.uniform(10.0, 15.0, size=nspecies) * N_PER_M_IN_EV_PER_NM2
+    return VFFParams(a, alpha, beta)
