@@ -116,11 +116,12 @@ __device__ __forceinline__ typename Elem<T, C>::V stencil(const EmParams<T>& p, 
   return acc;
 }
 
-// Each thread takes two points per pass, i and i + S (S = the grid's thread count), and issues
-// the loads of both before either sum: twice the bytes in flight per thread.  Complex vectors
-// take the phase path only in the passes that touch a face, so the interior carries no complex
-// rotation.
-template <typename T, bool C>
+// PAIR: each thread takes two points per pass, i and i + S (S = the grid's thread count), and
+// issues the loads of both before either sum: twice the bytes in flight per thread; complex
+// vectors take the phase path only in the passes that touch a face, so the interior carries no
+// complex rotation.  Without PAIR (real FP64, which GB300's FP64 pipe bounds and the pair only
+// slows) one point per pass.
+template <typename T, bool C, bool PAIR>
 __global__ void __launch_bounds__(256) effmass_hx_kernel(EmParams<T> p, const T* __restrict__ U,
                                                          const typename Elem<T, C>::V* __restrict__ x,
                                                          typename Elem<T, C>::V* __restrict__ y, int nvec) {
@@ -135,47 +136,65 @@ __global__ void __launch_bounds__(256) effmass_hx_kernel(EmParams<T> p, const T*
   int iy = r / g.nx, ix = r - iy * g.nx;
   const int sz = S / plane, rs = S - sz * plane;
   const int sy = rs / g.nx, sx = rs - sy * g.nx;
-  for (; i < N;) {
-    // the second point, one stride on
-    int ib = i + S, bx = ix + sx, by = iy + sy, bz = iz + sz;
-    if (bx >= g.nx) { bx -= g.nx; ++by; }
-    if (by >= g.ny) { by -= g.ny; ++bz; }
-    const bool has_b = ib < N;
-    int ja[6], jb[6];
-    unsigned wa, wb;
-    neighbours(g, plane, i, ix, iy, iz, ja, wa);
-    if (has_b) {
-      neighbours(g, plane, ib, bx, by, bz, jb, wb);
-    } else {
-      // no second point: a stand-in with no neighbours at a valid index, never stored
-#pragma unroll
-      for (int q = 0; q < 6; ++q) jb[q] = -1;
-      wb = 0;
+  if constexpr (!PAIR) {
+    for (; i < N;) {
+      int ja[6];
+      unsigned wa;
+      neighbours(g, plane, i, ix, iy, iz, ja, wa);
+      const T dga = p.d0 + U[i];
+      const V* xv = x;
+      V* yv = y;
+      for (int v = 0; v < nvec; ++v, xv += N, yv += N) yv[i] = stencil<T, C, true>(p, xv, i, ja, wa, dga);
+      i += S;
+      ix += sx;
+      iy += sy;
+      iz += sz;
+      if (ix >= g.nx) { ix -= g.nx; ++iy; }
+      if (iy >= g.ny) { iy -= g.ny; ++iz; }
     }
-    const int ibs = has_b ? ib : i;
-    const T dga = p.d0 + U[i], dgb = p.d0 + U[ibs];
-    const bool faces = C && (wa | wb) != 0;
-    const V* xv = x;
-    V* yv = y;
-    for (int v = 0; v < nvec; ++v, xv += N, yv += N) {
-      V ra, rb;
-      if (faces) {
-        ra = stencil<T, C, true>(p, xv, i, ja, wa, dga);
-        rb = stencil<T, C, true>(p, xv, ibs, jb, wb, dgb);
+  } else {
+    for (; i < N;) {
+      // the second point, one stride on
+      int ib = i + S, bx = ix + sx, by = iy + sy, bz = iz + sz;
+      if (bx >= g.nx) { bx -= g.nx; ++by; }
+      if (by >= g.ny) { by -= g.ny; ++bz; }
+      const bool has_b = ib < N;
+      int ja[6], jb[6];
+      unsigned wa, wb;
+      neighbours(g, plane, i, ix, iy, iz, ja, wa);
+      if (has_b) {
+        neighbours(g, plane, ib, bx, by, bz, jb, wb);
       } else {
-        ra = stencil<T, C, false>(p, xv, i, ja, 0u, dga);
-        rb = stencil<T, C, false>(p, xv, ibs, jb, 0u, dgb);
+        // no second point: a stand-in with no neighbours at a valid index, never stored
+#pragma unroll
+        for (int q = 0; q < 6; ++q) jb[q] = -1;
+        wb = 0;
       }
-      yv[i] = ra;
-      if (has_b) yv[ib] = rb;
+      const int ibs = has_b ? ib : i;
+      const T dga = p.d0 + U[i], dgb = p.d0 + U[ibs];
+      const bool faces = C && (wa | wb) != 0;
+      const V* xv = x;
+      V* yv = y;
+      for (int v = 0; v < nvec; ++v, xv += N, yv += N) {
+        V ra, rb;
+        if (faces) {
+          ra = stencil<T, C, true>(p, xv, i, ja, wa, dga);
+          rb = stencil<T, C, true>(p, xv, ibs, jb, wb, dgb);
+        } else {
+          ra = stencil<T, C, false>(p, xv, i, ja, 0u, dga);
+          rb = stencil<T, C, false>(p, xv, ibs, jb, 0u, dgb);
+        }
+        yv[i] = ra;
+        if (has_b) yv[ib] = rb;
+      }
+      // on to the next pair: two strides from i is one stride from the second point
+      i = ib + S;
+      ix = bx + sx;
+      iy = by + sy;
+      iz = bz + sz;
+      if (ix >= g.nx) { ix -= g.nx; ++iy; }
+      if (iy >= g.ny) { iy -= g.ny; ++iz; }
     }
-    // on to the next pair: two strides from i is one stride from the second point
-    i = ib + S;
-    ix = bx + sx;
-    iy = by + sy;
-    iz = bz + sz;
-    if (ix >= g.nx) { ix -= g.nx; ++iy; }
-    if (iy >= g.ny) { iy -= g.ny; ++iz; }
   }
 }
 
@@ -186,6 +205,7 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
 template <typename T, bool C>
 cudaError_t launch_em(const omen_ham* h, const T* U, const void* x, void* y, int nvec, double sigma, cudaStream_t st) {
   using V = typename Elem<T, C>::V;
+  constexpr bool kPair = !(sizeof(T) == 8 && !C);
   EmParams<T> p;
   p.g = EmGeo{h->gdim[0], h->gdim[1], h->gdim[2], (int)h->nrows, {h->gper[0], h->gper[1], h->gper[2]}};
   for (int d = 0; d < 3; ++d) {
@@ -201,7 +221,7 @@ cudaError_t launch_em(const omen_ham* h, const T* U, const void* x, void* y, int
   if (!resident) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, effmass_hx_kernel<T, C>, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, effmass_hx_kernel<T, C, kPair>, 256, 0) != cudaSuccess ||
         resident < 1 || sms < 1) {
       cudaGetLastError();
       resident = 1;
@@ -209,7 +229,7 @@ cudaError_t launch_em(const omen_ham* h, const T* U, const void* x, void* y, int
     }
   }
   const int blocks = (int)std::min<long long>((h->nrows + 255) / 256, (long long)sms * resident);
-  effmass_hx_kernel<T, C><<<blocks, 256, 0, st>>>(p, U, static_cast<const V*>(x), static_cast<V*>(y), nvec);
+  effmass_hx_kernel<T, C, kPair><<<blocks, 256, 0, st>>>(p, U, static_cast<const V*>(x), static_cast<V*>(y), nvec);
   return cudaGetLastError();
 }
 
