@@ -2547,7 +2547,8 @@ static omen_status kbatch_core(omen_ctx* ctx, const std::vector<KbatchInput>& in
   for (size_t i = 0; i < in.size(); ++i) {
     const omen_ham* h = in[i].ham;
     if (!h || !in[i].k_host || in[i].nk < 1) return set_err(ctx, OMEN_EINVAL, "structure %zu: null argument or nk < 1", i);
-    if (h->effmass || !h->bloch || h->spin_orbit || h->matrix_free)
+    if (h->effmass) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs on tight-binding Hamiltonians");
+    if (!h->bloch || h->spin_orbit || h->matrix_free)
       return set_err(ctx, OMEN_EINVAL, "k batch needs Bloch Hamiltonians with stored blocks and no spin-orbit");
     if (h->precision == OMEN_F32_REFINE64) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs in F64 or F32");
     if (h->precision != h0->precision || h->norb != h0->norb)

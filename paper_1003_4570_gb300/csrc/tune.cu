@@ -141,7 +141,8 @@ extern "C" omen_status omen_tune_hx(omen_ctx* ctx, omen_ham* h, int vec_precisio
 
 extern "C" omen_status omen_tune_hx_kbatch(omen_ctx* ctx, omen_ham* h, int nk, int reps, omen_tune_result* out) {
   if (!ctx || !h || nk < 1 || nk > 65535 || reps < 1) return set_err(ctx, OMEN_EINVAL, "null argument, nk or reps out of range");
-  if (h->effmass || !h->bloch || h->spin_orbit || h->matrix_free) return set_err(ctx, OMEN_EINVAL, "k batch needs a Bloch tight-binding Hamiltonian with stored blocks and no spin-orbit");
+  if (h->effmass) return set_err(ctx, OMEN_EUNSUPPORTED, "k batch runs on tight-binding Hamiltonians");
+  if (!h->bloch || h->spin_orbit || h->matrix_free) return set_err(ctx, OMEN_EINVAL, "k batch needs a Bloch Hamiltonian with stored blocks and no spin-orbit");
   const int prec = h->precision == OMEN_F32 ? OMEN_F32 : OMEN_F64;
   if (!has_blocks(h, prec)) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no blocks of its precision");
   OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
