@@ -84,3 +84,12 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == expected
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the shared library missing, the first call raises."""
+    from paper_1003_4570_gb300 import omen
+    monkeypatch.setattr(omen, "_lib", None)
+    monkeypatch.setattr(omen, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        omen.lib()
