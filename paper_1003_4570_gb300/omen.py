@@ -181,6 +181,24 @@ def exported_symbols():
     return [n for n in dir(_lib) if n.startswith("omen_")]
 
 
+def _nbytes(buf):
+    """Size in bytes of a buffer object (torch tensor or numpy array); None for a raw address."""
+    if buf is None or isinstance(buf, int):
+        return None
+    if hasattr(buf, "numel") and hasattr(buf, "element_size"):
+        return int(buf.numel()) * int(buf.element_size())
+    if isinstance(buf, np.ndarray):
+        return int(buf.nbytes)
+    return None
+
+
+def _need(buf, nbytes, what):
+    """Refuse a buffer smaller than what the library will read or write through it."""
+    have = _nbytes(buf)
+    if have is not None and have < nbytes:
+        raise ValueError(f"{what}: buffer of {have} bytes, the call uses {nbytes}")
+
+
 def _ptr(x):
     if x is None:
         return None
@@ -279,11 +297,20 @@ def tb_params_struct(p) -> TBParams:
 
 
 class Hamiltonian:
-    def __init__(self, ctx, handle, lat):
+    def __init__(self, ctx, handle, lat, precision=OMEN_F64):
         self.ctx, self.handle, self.lattice = ctx, handle, lat
+        self.precision = int(precision)
         n, c, e = C.c_longlong(), C.c_int(), C.c_int()
         lib().omen_ham_shape(handle, C.byref(n), C.byref(c), C.byref(e))
         self.nrows, self.is_complex, self.elem_bytes = n.value, bool(c.value), e.value
+
+    @property
+    def evec_bytes(self):
+        """Bytes per element of the eigenvectors omen_eigs returns: FP64 (complex128) except for
+        OMEN_F32 Hamiltonians, whose eigenvectors are in their own vector type."""
+        if self.precision == OMEN_F32:
+            return self.elem_bytes
+        return 16 if self.is_complex else 8
 
     @property
     def numpy_dtype(self):
@@ -306,7 +333,7 @@ def omen_assemble_H(ctx: Context, lat: Lattice, params, spin_orbit=False, precis
                 None if karr is None else karr.ctypes.data, _ptr(U_atom_dev))
     h = C.c_void_p()
     ctx.check(lib().omen_assemble_H(ctx.handle, lat.handle, C.byref(tp), C.byref(o), C.byref(h)))
-    return Hamiltonian(ctx, h, lat)
+    return Hamiltonian(ctx, h, lat, precision)
 
 
 def omen_assemble_effmass(ctx: Context, spec, precision=OMEN_F64, U_dev=None) -> Hamiltonian:
@@ -324,7 +351,7 @@ def omen_assemble_effmass(ctx: Context, spec, precision=OMEN_F64, U_dev=None) ->
     d.precision = int(precision)
     h = C.c_void_p()
     ctx.check(lib().omen_assemble_effmass(ctx.handle, C.byref(d), _ptr(U_dev), C.byref(h)))
-    return Hamiltonian(ctx, h, None)
+    return Hamiltonian(ctx, h, None, precision)
 
 
 def omen_ham_set_potential(ctx: Context, ham: Hamiltonian, U_atom_dev):
@@ -333,6 +360,8 @@ def omen_ham_set_potential(ctx: Context, ham: Hamiltonian, U_atom_dev):
 
 def omen_hx(ctx: Context, ham: Hamiltonian, x_dev, y_dev, nvec=1, sigma=0.0):
     """y = (H - sigma) x on device buffers (asynchronous on the context's stream)."""
+    _need(x_dev, int(nvec) * ham.nrows * ham.elem_bytes, "omen_hx x")
+    _need(y_dev, int(nvec) * ham.nrows * ham.elem_bytes, "omen_hx y")
     ctx.check(lib().omen_hx(ctx.handle, ham.handle, _ptr(x_dev), _ptr(y_dev), int(nvec), float(sigma)))
 
 
@@ -348,6 +377,8 @@ def omen_hx_host(ctx: Context, ham: Hamiltonian, x: np.ndarray, sigma=0.0) -> np
 def omen_eigs(ctx: Context, ham: Hamiltonian, nev, which=OMEN_LOWEST, sigma=0.0, tol=1e-9, max_iter=1000,
               block=1, basis=None, v0=None, evecs_dev=None, raise_on_noconv=True, v0_dev=None):
     """Eigenpairs by thick-restart block Lanczos.  Returns (evals ndarray, info dict, status)."""
+    _need(evecs_dev, int(nev) * ham.nrows * ham.evec_bytes, "omen_eigs evecs")
+    _need(v0_dev, int(block) * ham.nrows * ham.elem_bytes, "omen_eigs v0")
     if basis is None:
         basis = max(4 * block, ((2 * nev + 2 * block + block - 1) // block) * block, 32 // block * block)
     v0a = None
@@ -378,6 +409,7 @@ def omen_poisson(ctx: Context, grid, rho_dev, phi_dev, rtol=1e-12, max_iter=1000
 
 
 def omen_density_accum(ctx: Context, ham: Hamiltonian, psi_dev, nstates, occ, weight, n_atom_dev):
+    _need(psi_dev, int(nstates) * ham.nrows * (16 if ham.is_complex else 8), "omen_density_accum psi")
     occ = np.ascontiguousarray(occ, dtype=np.float64)
     ctx.check(lib().omen_density_accum(ctx.handle, ham.handle, _ptr(psi_dev), int(nstates), occ.ctypes.data,
                                        float(weight), _ptr(n_atom_dev)))
@@ -451,6 +483,8 @@ def omen_hx_kbatch_set_tile(ctx: Context, ham: Hamiltonian, vec_precision, threa
 def omen_hx_kbatch(ctx: Context, ham: Hamiltonian, kpts, x_dev, y_dev, sigma=0.0):
     """y_k = (H(k) - sigma) x_k for every wave vector (device buffers [nk][nrows])."""
     k = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 3)
+    _need(x_dev, len(k) * ham.nrows * ham.elem_bytes, "omen_hx_kbatch x")
+    _need(y_dev, len(k) * ham.nrows * ham.elem_bytes, "omen_hx_kbatch y")
     ctx.check(lib().omen_hx_kbatch(ctx.handle, ham.handle, len(k), k.ctypes.data, _ptr(x_dev), _ptr(y_dev), float(sigma)))
 
 

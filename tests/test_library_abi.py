@@ -93,3 +93,26 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(omen, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         omen.lib()
+
+
+def test_binding_refuses_buffers_smaller_than_the_call_uses():
+    """Too small a buffer is refused in the binding, before the library could read or write past
+    its end; raw addresses pass unchecked."""
+    import numpy as np
+    from paper_1003_4570_gb300 import omen
+    ham = object.__new__(omen.Hamiltonian)
+    ham.handle = None
+    ham.nrows, ham.is_complex, ham.elem_bytes, ham.precision = 1000, True, 8, omen.OMEN_F32_REFINE64
+    assert ham.evec_bytes == 16                      # refined solves return complex128
+    ham.precision = omen.OMEN_F32
+    assert ham.evec_bytes == 8
+    small = np.zeros(2 * 1000 - 1, dtype=np.complex64)
+    with pytest.raises(ValueError):
+        omen.omen_hx(None, ham, small, small, nvec=2)
+    with pytest.raises(ValueError):
+        omen.omen_eigs(None, ham, 4, evecs_dev=np.zeros((3, 1000), dtype=np.complex64))
+    with pytest.raises(ValueError):
+        omen.omen_density_accum(None, ham, np.zeros((2, 1000), dtype=np.complex64), 2, [1.0, 1.0], 1.0, None)
+    with pytest.raises(ValueError):
+        omen.omen_hx_kbatch(None, ham, np.zeros((3, 3)), np.zeros(2999, np.complex64), np.zeros(3000, np.complex64))
+    assert omen._nbytes(12345) is None and omen._nbytes(np.zeros(4)) == 32
