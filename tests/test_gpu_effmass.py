@@ -97,17 +97,21 @@ def test_effmass_eigs_match_dense(ctx, prec, which, block):
     w = np.linalg.eigvalsh(H.toarray())
     ham = build(ctx, spec, prec)
     nev = 8
-    tol = {1: 1e-5, 2: 1e-8}.get(prec, 1e-9)       # FP32, FP32 refined in FP64, FP64
+    # the stated accuracy of each path: FP32 raw, FP32 refined in FP64, FP64 (eV)
+    tol = {1: 1e-5, 2: 1e-8}.get(prec, 1e-9)
+    # the solver's bound is on its own operator; raw FP32 adds the rounding of the FP32
+    # stencil (about 1e-6 eV here), so that path asks for half the stated accuracy
+    solve_tol = 0.5 * tol if prec == 1 else tol
     if which == 0:
         ref = w[:nev]
-        ev, info, _ = omen.omen_eigs(ctx, ham, nev, tol=tol, block=block, basis=48, max_iter=20000)
+        ev, info, _ = omen.omen_eigs(ctx, ham, nev, tol=solve_tol, block=block, basis=48, max_iter=20000)
     else:
         sigma = float(0.5 * (w[60] + w[61]) + 0.003)
         ref = eigs.nearest(w, sigma, nev)
-        ev, info, _ = omen.omen_eigs(ctx, ham, nev, which=omen.OMEN_NEAREST, sigma=sigma, tol=tol, block=block,
-                                     basis=48, max_iter=60000)
+        ev, info, _ = omen.omen_eigs(ctx, ham, nev, which=omen.OMEN_NEAREST, sigma=sigma, tol=solve_tol,
+                                     block=block, basis=48, max_iter=60000)
     assert info["converged"] == 1, info
-    np.testing.assert_allclose(np.sort(ev), ref, atol=10 * tol, rtol=0)
+    np.testing.assert_allclose(np.sort(ev), ref, atol=tol, rtol=0)
 
 
 def test_effmass_bloch_eigs_and_density(ctx):

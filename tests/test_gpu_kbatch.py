@@ -158,12 +158,14 @@ def test_kbatch_finds_every_copy_of_degenerate_levels(ctx, prec):
     ks = np.array([[0.0, 0.0, 0.0], [np.pi / Lx, 0.0, 0.0], [0.3 * np.pi / Lx, 0.0, 0.0]])
     lat = omen.omen_build_lattice(ctx, spec)
     ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, k=(0.0, 0.0, 0.0))
-    tol = 1e-9 if prec == 0 else 1e-5
-    ev, info, st = omen.omen_eigs_kbatch(ctx, ham, ks, 6, tol=tol, max_iter=20000, basis=40)
+    tol = 1e-9 if prec == 0 else 1e-5          # stated accuracy: FP64, raw FP32 (eV)
+    # raw FP32 adds the rounding of the FP32 blocks to the solver's own bound: ask for half
+    ev, info, st = omen.omen_eigs_kbatch(ctx, ham, ks, 6, tol=(tol if prec == 0 else 0.5 * tol), max_iter=20000,
+                                         basis=40)
     assert info["converged"] == 1, info
     for q, kv in enumerate(ks):
         dense = np.linalg.eigvalsh(hamiltonian.assemble(spec, p, kvec=kv).toarray())[:6]
-        np.testing.assert_allclose(ev[q], dense, atol=(1e-9 if prec == 0 else 2e-5), rtol=0)
+        np.testing.assert_allclose(ev[q], dense, atol=tol, rtol=0)
 
 
 def test_kbatch_nearest_finds_every_copy_of_degenerate_levels(ctx):

@@ -60,3 +60,26 @@ def test_profile_maps():
     back = mlp.inject(grid, t, scale=0.1)[:, 0, 0]
     inner = (z > zj[0]) & (z < zj[-2])
     np.testing.assert_allclose(back[inner], 0.3 * z[inner], rtol=1e-12)
+
+
+def test_profile_maps_hand_computed():
+    """Three interior planes of two lateral points each, values worked out by hand: the lateral
+    means are (1, 3, 5) x scale; the grounded planes add 0 at t = 0 and t = 4 (units of hz).
+    Four samples sit at t = 0.5, 1.5, 2.5, 3.5, i.e. halfway between neighbouring planes."""
+    grid = poisson.Grid(2, 1, 4, 1.0, 1.0, 4.0)
+    phi = np.array([0.5, 1.5, 2.0, 4.0, 6.0, 4.0]).reshape(grid.shape) * 0.1   # means 0.1, 0.3, 0.5 V
+    t = mlp.targets(grid, phi, n=4, scale=0.1)
+    np.testing.assert_allclose(t, [0.5, 2.0, 4.0, 2.5], rtol=1e-14)
+    t2 = mlp.targets(grid, phi, n=2, scale=0.1)                      # samples at t = 1 and t = 3
+    np.testing.assert_allclose(t2, [1.0, 5.0], rtol=1e-14)
+    # features: log10 of the donor density (m^-3), floored at 1e15, minus 21, over 6
+    nd = np.array([1e20, 1e20, 1e22, 1e22, 1e12, 1e12]).reshape(grid.shape)
+    f = mlp.features(grid, nd * mlp.Q_E, n=2)
+    np.testing.assert_allclose(f, [(20 - 21) / 6, (15 - 21) / 6], rtol=1e-12)
+    f4 = mlp.features(grid, nd * mlp.Q_E, n=4)
+    expect = [np.log10(0.5e20), np.log10(0.5 * (1e20 + 1e22)), np.log10(0.5 * (1e22 + 1e12)), 15.0]
+    np.testing.assert_allclose(f4, (np.array(expect) - 21) / 6, rtol=1e-12)
+    # inject: samples at z/Lz = 1/4 and 3/4 land on planes 1 and 3; plane 2 is their mean
+    back = mlp.inject(grid, np.array([2.0, -1.0]), scale=0.1)
+    np.testing.assert_allclose(back[:, 0, 0], [0.2, 0.05, -0.1], rtol=1e-14)
+    assert np.all(back == back[:, :1, :1])

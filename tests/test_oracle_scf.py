@@ -4,7 +4,18 @@
   have the stored gap (re-checked on a coarse folded grid);
 * the donor sheet on the grid carries exactly e N_s per unit area;
 * the oracle SCF reaches its fixed point (max |phi_out - phi| < tol) and conserves charge:
-  electrons per atom sum to the electron count, and the total charge is neutral.
+  electrons per atom sum to the electron count, and the total charge is neutral;
+* the physics of the coupling between the Poisson potential and the Hamiltonian (Section
+  III-A items 2-3), checked on the converged potential so that a flipped sign of the
+  electron's potential energy (U = -phi) or of the electron charge fails:
+  - discrete Gauss law: for the 7-point operator with phi = 0 on both z ends, the interior
+    charge equals eps0 eps_r hx hy / hz times the sum of phi over the first and last interior
+    planes.  A neutral fixed point has (almost) no net charge, so the end fields cancel; with
+    the electron charge's sign flipped the net charge would be twice the donors';
+  - electrons (charge -e) are drawn to high potential: the atomic plane holding the most
+    electrons sits at the donor sheet, and the electron-weighted mean of phi at the atoms
+    exceeds the plain mean; with U = +phi they would be pushed away from the sheet;
+  - the positive donor sheet makes phi a hill with its top at the sheet.
 """
 import json
 import os
@@ -13,7 +24,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import bulk, poisson, scf
+from oracle import bulk, charge, poisson, scf
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "gapped_si_params.json")
 
@@ -60,6 +71,49 @@ def test_oracle_scf_fixed_point_and_neutrality():
     area = c["grid"].Lx_nm * c["grid"].Ly_nm * 1e-18
     donors = c["donor_rho"][:, 0, 0].sum() * hz * area
     assert abs(donors - synth.Q_E * c["n_electrons"]) < 1e-9 * donors
+
+
+@pytest.fixture(scope="module")
+def converged_delta():
+    c = small_delta_case()
+    phi, info = scf.scf(c["spec"], c["params"], c["grid"], c["donor_rho"], c["n_electrons"], c["kT"], c["kpts"],
+                        c["kweights"], c["nev"], c["sigma"], c["e_cut"], mix=0.3, tol_V=1e-8, max_iter=300,
+                        mix_history=5)
+    assert info["dV_inf"] < 1e-8
+    return c, phi, info
+
+
+def net_charge_from_end_fields(grid, phi):
+    """Discrete Gauss law: summing the 7-point operator over all interior unknowns leaves only
+    the z-boundary terms (the x, y differences telescope to zero on the periodic axes and
+    phi = 0 on the z = 0, Lz planes), so sum_k rho_k V_cell = eps hx hy / hz * sum(phi_1 + phi_nz-1)."""
+    hx, hy, hz = grid.h_m
+    return poisson.EPS0 * grid.eps_r * hx * hy / hz * (phi[0].sum() + phi[-1].sum())
+
+
+def check_coupling_physics(c, phi, info):
+    grid = c["grid"]
+    hx, hy, hz = grid.h_m
+    q_donor = c["donor_rho"].sum() * hx * hy * hz
+    # neutral: what is left is the few electrons on atoms within a spacing of the grounded planes
+    assert abs(net_charge_from_end_fields(grid, phi)) < 1e-3 * q_donor
+    pos = scf.atom_positions_nm(c["spec"])
+    n = info["n_atom"]
+    planes = np.unique(np.round(pos[:, 2], 9))
+    per_plane = np.array([n[np.abs(pos[:, 2] - z) < 1e-6].sum() for z in planes])
+    z_sheet = 0.5 * grid.Lz_nm
+    _, w = synth.delta_layer(1, 12, seed=5)[2]
+    assert abs(planes[per_plane.argmax()] - z_sheet) <= 0.25 * w
+    phi_at = charge.gather(grid, phi, pos)
+    assert (n * phi_at).sum() / n.sum() > phi_at.mean() + 0.1 * np.ptp(phi_at)
+    prof = phi.reshape(grid.nz - 1, -1).mean(axis=1)
+    z = np.arange(1, grid.nz) * grid.Lz_nm / grid.nz
+    assert prof.max() > 0 and abs(z[prof.argmax()] - z_sheet) <= 0.25 * w
+    assert prof.max() > 10 * np.abs(prof[[0, -1]]).max()
+
+
+def test_oracle_scf_coupling_signs(converged_delta):
+    check_coupling_physics(*converged_delta)
 
 
 def test_oracle_scf_anderson_reaches_same_fixed_point():
