@@ -367,8 +367,9 @@ omen_status omen_poisson(omen_ctx* ctx, const omen_grid* grid, const double* rho
  * exits (OMEN_POISSON_STATIC_MAX_UNKNOWNS unknowns, about 6.4 MB).  The caller still passes
  * rho_dev and phi_dev (initial guess in, solution out) and the stream to work on; the
  * current device is used.
- *  - The first call on a device looks up the array's device address once (with that device
- *    current); make that first call before any stream capture.
+ *  - Every call looks up the array's device address on the current device (a pointer kept
+ *    across a cudaDeviceReset would be stale); the first call on a device loads the library's
+ *    device code there, so make that first call before any stream capture.
  *  - Grids with more than OMEN_POISSON_STATIC_MAX_UNKNOWNS interior unknowns
  *    (nx*ny*(nz-1)) are rejected with OMEN_EINVAL; other argument errors also return
  *    OMEN_EINVAL, CUDA failures OMEN_ECUDA, hitting max_iter OMEN_ENOCONV.  No message

@@ -11,7 +11,6 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
-#include <mutex>
 
 #include "omen_internal.h"
 
@@ -245,29 +244,23 @@ extern "C" omen_status omen_poisson(omen_ctx* ctx, const omen_grid* gr, const do
 // them the CG work vectors live in the statically sized device array below instead.  Every
 // GPU that loads this library holds the array (about 6.4 MB) until the process exits.
 // The array's name in host code is only a host-side stand-in for the symbol, so the device
-// address is looked up with cudaGetSymbolAddress, once per device, with that device current,
-// the first time the entry point runs there.
+// address is looked up with cudaGetSymbolAddress, with the caller's device current, on every
+// call.  The lookup is cheap once the module is loaded, and a pointer kept from an earlier call
+// could be stale after cudaDeviceReset or a primary context that was torn down and recreated.
+// The first call on a device loads the module there; make it before any stream capture.
 static constexpr long long kStaticMaxUnknowns = 1ll << 18;   // nx*ny*(nz-1) limit
 static constexpr int kStaticMaxBlocks = 4096;
 static constexpr long long kStaticWords = 3 * kStaticMaxUnknowns + 3 * kStaticMaxBlocks + 8;
 static __device__ __align__(256) double g_poisson_scratch[kStaticWords];
 
-static std::mutex g_scratch_mu;
-static double* g_scratch_addr[128] = {};
-
-static omen_status scratch_address(int dev, double** out) {
-  if (dev < 0 || dev >= 128) return OMEN_EUNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_poisson_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return OMEN_ECUDA;
-    }
-    g_scratch_addr[dev] = static_cast<double*>(p);
+static omen_status scratch_address(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_poisson_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return OMEN_ECUDA;
   }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(p);
   return OMEN_OK;
 }
 
@@ -287,7 +280,7 @@ extern "C" omen_status omen_poisson_static(const omen_grid* gr, const double* rh
     return OMEN_ECUDA;
   }
   double* base = nullptr;
-  const omen_status s = scratch_address(dev, &base);
+  const omen_status s = scratch_address(&base);
   if (s != OMEN_OK) return s;
   PGrid g;
   g.nx = gr->nx;
