@@ -131,6 +131,62 @@ void omen_free_lattice(omen_lattice* lat);
 /* Number of atoms and of existing bonds (after the hard-wall rule). */
 omen_status omen_lattice_counts(const omen_lattice* lat, long long* natoms, long long* nbonds);
 
+/* Replace the structure's bond strains (relative bond-length change per bond slot, device,
+ * [16*ncells], slot layout as above; slots of absent bonds are ignored), e.g. with the relaxed
+ * strains of omen_relax_vff.  Hamiltonians assembled afterwards use them; a matrix-free
+ * Hamiltonian already built on this structure reads them in its next product, stored blocks keep
+ * the strain they were assembled with.  Asynchronous on ctx's stream. */
+omen_status omen_lattice_set_strain(omen_ctx* ctx, omen_lattice* lat, const double* strain_dev);
+
+/* ---- valence-force-field strain relaxation (paper Section II-B: atomistic VFF strain before
+ * the electronic structure; Fig. 4 benchmarks it) ------------------------------------------- */
+/* Keating's form (Phys. Rev. 145, 637 (1966)), per bond b and per pair of bonds p, q at an atom:
+ *   E = sum_b 3 alpha_b/(8 d_b^2) (r_b.r_b - d_b^2)^2
+ *     + sum_atoms sum_{p<q} 3 beta_pq/(8 d_p d_q) (r_p.r_q + d_p d_q/3)^2,
+ * r_p the vector from the atom to its neighbour along bond p, d_b = sqrt(3)/4 times the mean
+ * natural lattice constant of the bond's two species, alpha_b (beta_b) the mean of the two
+ * species' constants, beta_pq the mean of beta_p and beta_q.  Positions are F x0 + u: x0 the
+ * ideal sites at the structure's a_nm, F a homogeneous box deformation (periodic images move
+ * with it), u the displacements.  Bonds leaving a hard wall are absent (free surface).
+ * u and forces are [3][natoms] device arrays: the x components of all atoms, then y, then z (nm,
+ * eV/nm).  Species indices are the structure's.  Units: nm, eV; alpha, beta in eV/nm^2. */
+typedef struct {
+  int nspecies;              /* 1..4 */
+  double a_nm[4];            /* natural lattice constant per species (nm) */
+  double alpha[4];           /* bond-stretching constant per species (eV/nm^2) */
+  double beta[4];            /* bond-bending constant per species (eV/nm^2) */
+} omen_vff_params;
+
+typedef struct {
+  double gtol;               /* stop when every force component is below gtol (eV/nm) */
+  int max_iter;              /* maximum conjugate-gradient iterations */
+} omen_vff_opts;
+
+typedef struct {
+  int iterations;
+  int converged;
+  double energy_start, energy;  /* eV, before and after */
+  double max_force;          /* max |force component| at exit (eV/nm) */
+  double seconds;
+} omen_vff_info;
+
+/* Energy (E_host, may be NULL) and forces -dE/du (force_dev [3][natoms], may be NULL) at
+ * displacements u_dev; F_host [9] row-major, NULL = identity.  Synchronous.  EINVAL for bad
+ * parameters (nspecies, a_nm <= 0, negative constants). */
+omen_status omen_vff_energy_forces(omen_ctx* ctx, const omen_lattice* lat, const omen_vff_params* p,
+                                   const double* F_host, const double* u_dev, double* E_host, double* force_dev);
+
+/* Relax u_dev (start in, relaxed displacements out) at fixed F by nonlinear conjugate gradients
+ * (Polak–Ribiere, clipped at zero) with an exact line search: along a direction every Keating
+ * term is the square of a quadratic in the step, so the energy is a quartic whose minimum is
+ * found from its derivative's coefficients (accumulated term by term, no energy differences).
+ * strain_dev (or NULL) receives |r_b|/d_b - 1 per bond slot ([16*ncells], absent bonds 0), the
+ * input of omen_lattice_set_strain.  Allocates its work vectors (9 doubles per atom) on ctx's
+ * stream; synchronous.  ENOCONV (u and strain still written) at max_iter, ENUMERIC on a
+ * non-finite force. */
+omen_status omen_relax_vff(omen_ctx* ctx, const omen_lattice* lat, const omen_vff_params* p, const double* F_host,
+                           const omen_vff_opts* opts, double* u_dev, double* strain_dev, omen_vff_info* info);
+
 /* ---- Hamiltonian (paper Section I: empirical sp3s* and sp3d5s* tight binding with strain) - */
 
 typedef struct {

@@ -135,3 +135,10 @@ extern "C" omen_status omen_lattice_counts(const omen_lattice* L, long long* nat
   if (nbonds) *nbonds = L->nbonds;
   return OMEN_OK;
 }
+
+extern "C" omen_status omen_lattice_set_strain(omen_ctx* ctx, omen_lattice* L, const double* strain_dev) {
+  if (!ctx || !L || !strain_dev) return set_err(ctx, OMEN_EINVAL, "null argument");
+  OMEN_CUDA(ctx, cudaMemcpyAsync(L->d_strain, strain_dev, sizeof(double) * 16 * (size_t)L->ncells,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+  return OMEN_OK;
+}

@@ -107,6 +107,22 @@ class EffMassDesc(C.Structure):
                 ("k", C.c_double * 3), ("precision", C.c_int)]
 
 
+class VFFParams(C.Structure):
+    _fields_ = [("nspecies", C.c_int), ("a_nm", C.c_double * 4), ("alpha", C.c_double * 4), ("beta", C.c_double * 4)]
+
+
+class VFFOpts(C.Structure):
+    _fields_ = [("gtol", C.c_double), ("max_iter", C.c_int)]
+
+
+class VFFInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("energy_start", C.c_double),
+                ("energy", C.c_double), ("max_force", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class MLPDesc(C.Structure):
     _fields_ = [("n_in", C.c_int), ("n_hidden1", C.c_int), ("n_hidden2", C.c_int), ("n_out", C.c_int),
                 ("feat_log10_shift", C.c_double), ("feat_log10_scale", C.c_double), ("target_scale", C.c_double)]
@@ -137,6 +153,9 @@ def lib():
             "omen_build_lattice": (i, [vp, C.POINTER(LatticeDesc), C.POINTER(vp)]),
             "omen_free_lattice": (None, [vp]),
             "omen_lattice_counts": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
+            "omen_lattice_set_strain": (i, [vp, vp, vp]),
+            "omen_vff_energy_forces": (i, [vp, vp, C.POINTER(VFFParams), vp, vp, C.POINTER(d), vp]),
+            "omen_relax_vff": (i, [vp, vp, C.POINTER(VFFParams), vp, C.POINTER(VFFOpts), vp, vp, C.POINTER(VFFInfo)]),
             "omen_assemble_H": (i, [vp, vp, C.POINTER(TBParams), C.POINTER(HamOpts), C.POINTER(vp)]),
             "omen_free_ham": (None, [vp]),
             "omen_assemble_effmass": (i, [vp, C.POINTER(EffMassDesc), vp, C.POINTER(vp)]),
@@ -279,6 +298,66 @@ def omen_build_lattice(ctx: Context, spec) -> Lattice:
     h = C.c_void_p()
     ctx.check(lib().omen_build_lattice(ctx.handle, C.byref(d), C.byref(h)))
     return Lattice(ctx, h, (species, strain))
+
+
+def omen_lattice_set_strain(ctx: Context, lat: Lattice, strain_dev) -> None:
+    """Replace the structure's per-slot bond strains (device, [16*ncells] float64)."""
+    natoms, _ = lat.counts()
+    _need(strain_dev, 16 * (natoms // 8) * 8, "strain_dev")
+    ctx.check(lib().omen_lattice_set_strain(ctx.handle, lat.handle, _ptr(strain_dev)))
+
+
+def vff_params_struct(vp) -> VFFParams:
+    """vp: a_nm, alpha, beta per species (arrays of equal length <= 4; eV/nm^2 for alpha, beta)."""
+    a = np.asarray(vp.a_nm, dtype=np.float64).ravel()
+    t = VFFParams()
+    t.nspecies = len(a)
+    for q in range(len(a)):
+        t.a_nm[q] = float(a[q])
+        t.alpha[q] = float(np.asarray(vp.alpha).ravel()[q])
+        t.beta[q] = float(np.asarray(vp.beta).ravel()[q])
+    return t
+
+
+def _box(F):
+    if F is None:
+        return None
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(3, 3)
+    return F
+
+
+def omen_vff_energy_forces(ctx: Context, lat: Lattice, vp, u_dev, F=None, force_dev=None):
+    """Keating energy (eV) at displacements u_dev ([3][natoms] float64, nm); forces -dE/du into
+    force_dev ([3][natoms]) when given."""
+    natoms, _ = lat.counts()
+    _need(u_dev, 3 * natoms * 8, "u_dev")
+    if force_dev is not None:
+        _need(force_dev, 3 * natoms * 8, "force_dev")
+    t = vff_params_struct(vp)
+    Fb = _box(F)
+    E = C.c_double()
+    ctx.check(lib().omen_vff_energy_forces(ctx.handle, lat.handle, C.byref(t), None if Fb is None else Fb.ctypes.data,
+                                           _ptr(u_dev), C.byref(E), _ptr(force_dev)))
+    return E.value
+
+
+def omen_relax_vff(ctx: Context, lat: Lattice, vp, u_dev, F=None, gtol=1e-10, max_iter=20000, strain_dev=None,
+                   raise_on_noconv=True):
+    """Relax u_dev in place at box deformation F; relaxed bond strains into strain_dev ([16*ncells])
+    when given.  Returns (info dict, status)."""
+    natoms, _ = lat.counts()
+    _need(u_dev, 3 * natoms * 8, "u_dev")
+    if strain_dev is not None:
+        _need(strain_dev, 16 * (natoms // 8) * 8, "strain_dev")
+    t = vff_params_struct(vp)
+    Fb = _box(F)
+    o = VFFOpts(float(gtol), int(max_iter))
+    info = VFFInfo()
+    s = lib().omen_relax_vff(ctx.handle, lat.handle, C.byref(t), None if Fb is None else Fb.ctypes.data, C.byref(o),
+                             _ptr(u_dev), _ptr(strain_dev), C.byref(info))
+    if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
+        ctx.check(s)
+    return info.as_dict(), s
 
 
 def tb_params_struct(p) -> TBParams:

@@ -53,7 +53,8 @@ STRUCTS = {
     "EigOpts": "omen_eig_opts", "EigInfo": "omen_eig_info", "Grid": "omen_grid", "CGOpts": "omen_cg_opts",
     "TuneResult": "omen_tune_result", "SolveInfo": "omen_solve_info", "SCFDesc": "omen_scf_desc",
     "SCFInfo": "omen_scf_info", "EffMassDesc": "omen_effmass_desc", "MLPDesc": "omen_mlp_desc",
-    "KbatchItem": "omen_kbatch_item",
+    "KbatchItem": "omen_kbatch_item", "VFFParams": "omen_vff_params", "VFFOpts": "omen_vff_opts",
+    "VFFInfo": "omen_vff_info",
 }
 
 
