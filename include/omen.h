@@ -133,9 +133,9 @@ omen_status omen_lattice_counts(const omen_lattice* lat, long long* natoms, long
 
 /* Replace the structure's bond strains (relative bond-length change per bond slot, device,
  * [16*ncells], slot layout as above; slots of absent bonds are ignored), e.g. with the relaxed
- * strains of omen_relax_vff.  Hamiltonians assembled afterwards use them; a matrix-free
- * Hamiltonian already built on this structure reads them in its next product, stored blocks keep
- * the strain they were assembled with.  Asynchronous on ctx's stream. */
+ * strains of omen_relax_vff.  Hamiltonians assembled afterwards use them; Hamiltonians already
+ * assembled (stored or matrix-free) keep the strain they were assembled with.  Asynchronous on
+ * ctx's stream. */
 omen_status omen_lattice_set_strain(omen_ctx* ctx, omen_lattice* lat, const double* strain_dev);
 
 /* ---- valence-force-field strain relaxation (paper Section II-B: atomistic VFF strain before
@@ -205,7 +205,8 @@ typedef struct {
   int spin_orbit;            /* 0/1: double the basis and add lambda L.sigma on p */
   int precision;             /* OMEN_F64, OMEN_F32 or OMEN_F32_REFINE64 */
   int matrix_free;           /* 0: store every bond block; 1: regenerate blocks in H·X from
-                                species, direction and strain */
+                                the species pair, the direction and a per-bond factor
+                                (d0/d)^eta taken from the structure's strain at assembly */
   const double* k;           /* NULL or [3] Bloch wave vector (1/nm) for OMEN_BLOCH axes */
   const double* U_atom_dev;  /* NULL or [natoms] onsite potential energy (eV), e.g. -phi */
 } omen_ham_opts;
@@ -293,8 +294,8 @@ omen_status omen_tune_hx_kbatch(omen_ctx* ctx, omen_ham* ham, int nk, int reps, 
 
 /* Set a launch shape directly: threads a multiple of 32 in 32..128 (0 = default 128) and
  * rows_per_batch from the compiled set (FP32 stored blocks 1, 2, 5, and 10 without spin-orbit
- * for sp3d5s*; FP64 stored 1, 2; 0 = the built-in rule; rows_per_batch must divide the
- * orbital count).  k batch: wave vectors per thread 1, 2 (FP64 and FP32) or 4 (FP32), 0 =
+ * for sp3d5s*; FP64 stored 1, 2; matrix-free 1, 2; 0 = the built-in rule; rows_per_batch must
+ * divide the orbital count).  k batch: wave vectors per thread 1, 2 (FP64 and FP32) or 4 (FP32), 0 =
  * default 2.  EINVAL for a shape that is not compiled. */
 omen_status omen_hx_set_tile(omen_ctx* ctx, omen_ham* ham, int vec_precision, int threads, int rows_per_batch);
 omen_status omen_hx_kbatch_set_tile(omen_ctx* ctx, omen_ham* ham, int vec_precision, int threads,

@@ -7,6 +7,7 @@
 //    (blk[(tile*ne + e)*32 + lane]): a warp reads 32 slots of one entry with one coalesced
 //    128-byte load, and one bond block of a warp is a single contiguous run.  Matrix-free Hamiltonians skip this step and H·X
 //    regenerates the block from the b0 table, the two species and the strain.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -80,6 +81,17 @@ __global__ void assemble_bonds_kernel(Geo g, NeighbourTables nt, const uint8_t* 
   }
 }
 
+// Matrix-free Hamiltonians: the bond-length factor (d0/d)^eta of every slot, d = d0 (1 + strain),
+// kept in both precisions (the product regenerates each block as factor x b0[pair][dir]).
+__global__ void mf_scale_kernel(const double* __restrict__ strain, long long nslots, double eta,
+                                double* __restrict__ s64, float* __restrict__ s32) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nslots; i += (long long)gridDim.x * blockDim.x) {
+    const double f = pow(1.0 + strain[i], -eta);
+    s64[i] = f;
+    s32[i] = (float)f;
+  }
+}
+
 __global__ void max_species_kernel(const uint8_t* __restrict__ sp, int n, int* __restrict__ out) {
   int m = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) m = max(m, (int)sp[i]);
@@ -93,7 +105,10 @@ static void free_ham_buffers(omen_ham* h) {
   cudaFree(h->d_blkdf);
   cudaFree(h->d_b0_64);
   cudaFree(h->d_b0_32);
+  cudaFree(h->d_scale64);
+  cudaFree(h->d_scale32);
   cudaFree(h->d_onsite);
+  cudaFree(h->d_onsite32);
   cudaFree(h->d_onsite_df);
   cudaFree(h->d_U);
   cudaFree(h->d_U32);
@@ -169,6 +184,7 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
   ALLOC_OR_FAIL(h->d_b0_64, ntab * sizeof(double));
   ALLOC_OR_FAIL(h->d_b0_32, ntab * sizeof(float));
   ALLOC_OR_FAIL(h->d_onsite, sizeof(double) * ns * norb);
+  ALLOC_OR_FAIL(h->d_onsite32, sizeof(float) * ns * norb);
   ALLOC_OR_FAIL(h->d_U, sizeof(double) * lat->natoms);
   ALLOC_OR_FAIL(h->d_lambda, sizeof(double) * 4);
   const bool need64 = !h->matrix_free && (h->precision == OMEN_F64 || h->precision == OMEN_F32_REFINE64);
@@ -177,6 +193,10 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
   if (need64) ALLOC_OR_FAIL(h->d_blk64, sizeof(double) * ne * nslots);
   if (need32) ALLOC_OR_FAIL(h->d_blk32, sizeof(float) * ne * nslots);
   if (needdf) ALLOC_OR_FAIL(h->d_blkdf, sizeof(float2) * ne * nslots);
+  if (h->matrix_free) {
+    ALLOC_OR_FAIL(h->d_scale64, sizeof(double) * 16 * (size_t)lat->ncells);
+    ALLOC_OR_FAIL(h->d_scale32, sizeof(float) * 16 * (size_t)lat->ncells);
+  }
 
   // parameter tables
   std::vector<double> V(ns * ns * 14), on(ns * norb);
@@ -201,6 +221,9 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
     e = cudaMemcpyAsync(h->d_onsite, on.data(), sizeof(double) * on.size(), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_lambda, p->lambda_so, sizeof(double) * 4, cudaMemcpyHostToDevice, ctx->stream);
+  std::vector<float> on32(on.begin(), on.end());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_onsite32, on32.data(), sizeof(float) * on32.size(), cudaMemcpyHostToDevice, ctx->stream);
   std::vector<float2> ondf(on.size());
   if (e == cudaSuccess && needdf) {
     for (size_t i = 0; i < on.size(); ++i) {
@@ -223,6 +246,12 @@ extern "C" omen_status omen_assemble_H(omen_ctx* ctx, const omen_lattice* lat, c
   }
   if (e == cudaSuccess) {
     b0_table_kernel<<<(unsigned)((ntab + 255) / 256), 256, 0, ctx->stream>>>(d_V, ns, norb, h->d_b0_64, h->d_b0_32);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && h->matrix_free) {
+    const long long n = 16ll * lat->ncells;
+    mf_scale_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 65535), 256, 0, ctx->stream>>>(
+        lat->d_strain, n, p->eta, h->d_scale64, h->d_scale32);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && (need64 || need32 || needdf)) {

@@ -35,20 +35,21 @@ struct HxArgs {
   NeighbourTables nt;
   const T* __restrict__ blk;          // stored blocks (entry-major), or null for matrix-free
   const T* __restrict__ b0;           // [ns*ns*4][norb*norb] blocks at d0 (matrix-free)
-  const double* __restrict__ strain;  // [16*ncells]
+  const T* __restrict__ scale;        // [16*ncells] (d0/d)^eta per bond slot (matrix-free)
   const uint8_t* __restrict__ species;
   const double* __restrict__ onsite;  // [ns][norb]
+  const T* __restrict__ onsite_t;     // the same in T (real matrix-free rows)
   const double* __restrict__ U;       // [natoms]
   const double* __restrict__ lambda;  // [ns]
   const void* x;
   void* y;
   long long nrows;
   double sigma;
-  double eta;
   double2 phase[3];
   int ns;
   int slot_stride;
   int cell0, cell1;                   // cells [cell0, cell1) of this launch (a z-range of planes)
+  int nbid;                           // CTA work items: 8 sites x cell tiles of blockDim.x cells
 };
 
 template <typename T>
@@ -68,15 +69,42 @@ template <typename T, typename C> __device__ __forceinline__ void fma_c(C& acc, 
 
 // RBT: block rows loaded per register batch (0 = the built-in rule below); the CTA width
 // (blockDim.x, a multiple of 32 up to 128) and RBT are the tile shape the tuner chooses.
+// Matrix-free block rows: RB rows of the b0 block (shared memory) into registers, with 16-byte
+// loads where the row offsets allow (FP32 with an even RB and orbital count, FP64 with an even
+// orbital count), else one word at a time.
+template <typename T, int NORB, int RB>
+__device__ __forceinline__ void smem_rows(const T* hb, int r0, T* hr) {
+  constexpr int NE = RB * NORB;
+  if constexpr (sizeof(T) == 4 && NORB % 2 == 0 && RB % 2 == 0) {
+    const float4* h4 = reinterpret_cast<const float4*>(hb + r0 * NORB);
+#pragma unroll
+    for (int e = 0; e < NE / 4; ++e) {
+      const float4 v = h4[e];
+      hr[4 * e] = v.x; hr[4 * e + 1] = v.y; hr[4 * e + 2] = v.z; hr[4 * e + 3] = v.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && NORB % 2 == 0) {
+    const double2* h2 = reinterpret_cast<const double2*>(hb + r0 * NORB);
+#pragma unroll
+    for (int e = 0; e < NE / 2; ++e) {
+      const double2 v = h2[e];
+      hr[2 * e] = v.x; hr[2 * e + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < NE; ++e) hr[e] = hb[r0 * NORB + e];
+  }
+}
+
+// Rows of one work item: site b = bid & 7 (fastest, so CTAs in flight cover all 8 sites of a
+// window of cells and the transposed (B-end) read of a bond block follows its A-end read within
+// L2 reach) and cells [cell0 + (bid >> 3) * blockDim.x, ...) one per thread.
 template <typename T, int NORB, bool CPLX, bool SO, bool MATFREE, int RBT>
-__global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
+__device__ __forceinline__ void hx_item(const HxArgs<T>& a, int bid, const T* __restrict__ tab) {
   using V = typename VecT<T, CPLX>::t;
   constexpr int NS = SO ? 2 : 1;
   const Geo& g = a.g;
-  // site fastest in the block order: CTAs in flight cover all 8 sites of a window of cells,
-  // so the transposed (B-end) read of a bond block follows its A-end read within L2 reach
-  const int b = blockIdx.x & 7;
-  const int cell = a.cell0 + (blockIdx.x >> 3) * blockDim.x + threadIdx.x;
+  const int b = bid & 7;
+  const int cell = a.cell0 + (bid >> 3) * blockDim.x + threadIdx.x;
   if (cell >= a.cell1) return;
   const int N = g.natoms;
   const int atom = b * g.ncells + cell;
@@ -92,7 +120,7 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int o = 0; o < NORB; ++o) {
-        const T d = (T)a.onsite[sp * NORB + o] + u;
+        const T d = a.onsite_t[sp * NORB + o] + u;
         const V xv = x[(size_t)(s * NORB + o) * N + atom];
         if constexpr (CPLX) {
           acc[s][o].x = d * xv.x;
@@ -130,6 +158,10 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
 
   const bool is_a = b < 4;
   const int s = is_a ? b : b - 4;
+  constexpr int RB = RBT > 0 ? RBT
+                             : (MATFREE ? ((sizeof(T) == 4 && NORB % 2 == 0) ? 2 : 1)
+                                        : (sizeof(T) == 8 ? 1 : (NS == 1 ? NORB : (NORB == 10 ? 5 : NORB))));
+  static_assert(NORB % RB == 0, "RB must divide the orbital count");
 #pragma unroll 1
   for (int k = 0; k < 4; ++k) {
     int ox, oy, oz, site2;
@@ -177,9 +209,8 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
     if constexpr (MATFREE) {
       const int sa = is_a ? sp : a.species[atom2];
       const int sb = is_a ? a.species[atom2] : sp;
-      const double e1 = 1.0 + a.strain[slot];
-      scale = (T)(a.eta == 2.0 ? 1.0 / (e1 * e1) : pow(e1, -a.eta));
-      hb = a.b0 + ((size_t)(sa * a.ns + sb) * 4 + k) * (NORB * NORB);
+      scale = a.scale[slot];
+      hb = tab + ((sa * a.ns + sb) * 4 + k) * (NORB * NORB);
       stride = 1;
     } else {
       const size_t ks = is_a ? (size_t)(k * 4 + s) : (size_t)(k * 4 + site2);
@@ -200,13 +231,15 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
     // Rows of the block are loaded RB at a time into registers before their FMAs, so each
     // thread keeps RB*NORB independent loads in flight (memory-level parallelism).  Every
     // accumulator sums its terms in the same order for any RB: the result does not depend on it.
-    constexpr int RB = RBT > 0 ? RBT : ((sizeof(T) == 8 || MATFREE) ? 1 : (NS == 1 ? NORB : (NORB == 10 ? 5 : NORB)));
-    static_assert(NORB % RB == 0, "RB must divide the orbital count");
 #pragma unroll
     for (int r0 = 0; r0 < NORB; r0 += RB) {
       T hr[RB * NORB];
+      if constexpr (MATFREE) {
+        smem_rows<T, NORB, RB>(hb, r0, hr);
+      } else {
 #pragma unroll
-      for (int e = 0; e < RB * NORB; ++e) hr[e] = __ldg(hb + (size_t)(r0 * NORB + e) * stride);
+        for (int e = 0; e < RB * NORB; ++e) hr[e] = __ldg(hb + (size_t)(r0 * NORB + e) * stride);
+      }
       if (is_a) {
 #pragma unroll
         for (int i = 0; i < RB; ++i)
@@ -236,6 +269,169 @@ __global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
   for (int q = 0; q < NS; ++q)
 #pragma unroll
     for (int o = 0; o < NORB; ++o) y[(size_t)(q * NORB + o) * N + atom] = acc[q][o];
+}
+
+// Real matrix-free rows (no spin-orbit, no Bloch phase).  The site class (A or B end of its
+// bonds) is a template parameter, so the row/column order of each block product is fixed at
+// compile time; the four bonds are unrolled; the onsite energies come from a table in T and
+// U - sigma is formed once per atom, so an FP32 product runs no FP64 arithmetic per orbital.
+// Each accumulator sums its terms in the same order as hx_item's (onsite, then k = 0..3).
+// Real FP32 rows with an even orbital count use packed FP32x2 FMAs and a second, row-pair
+// interleaved copy of the table (for the A end) after the row-major one.
+template <typename T, int NORB, bool CPLX>
+__host__ __device__ constexpr bool mf_paired() { return !CPLX && sizeof(T) == 4 && NORB % 2 == 0; }
+
+template <typename T, int NORB, int RB, bool IS_A>
+__device__ __forceinline__ void hx_item_mf_real(const HxArgs<T>& a, int bid, const T* __restrict__ tab) {
+  constexpr bool PAIRED = mf_paired<T, NORB, false>();
+  const int tab_copy = a.ns * a.ns * 4 * NORB * NORB;   // offset of the interleaved copy
+  const Geo& g = a.g;
+  const int b = bid & 7;
+  const int s = IS_A ? b : b - 4;
+  const int cell = a.cell0 + (bid >> 3) * blockDim.x + threadIdx.x;
+  if (cell >= a.cell1) return;
+  const int N = g.natoms;
+  const int atom = b * g.ncells + cell;
+  const int nxy = g.nx * g.ny;
+  const int iz = cell / nxy;
+  const int rem = cell - iz * nxy;
+  const int iy = rem / g.nx;
+  const int ix = rem - iy * g.nx;
+  // faces this cell touches: a bond leaving through one wraps (periodic) or is absent (hard wall)
+  const bool lo[3] = {ix == 0, iy == 0, iz == 0};
+  const bool hi[3] = {ix == g.nx - 1, iy == g.ny - 1, iz == g.nz - 1};
+  const int stride[3] = {1, g.nx, nxy};
+  const int extent[3] = {g.nx * 1, g.ny * g.nx, g.nz * nxy};
+  const T* __restrict__ x = static_cast<const T*>(a.x) + (size_t)blockIdx.z * a.nrows;
+  T* __restrict__ y = static_cast<T*>(a.y) + (size_t)blockIdx.z * a.nrows;
+  const int sp = a.species[atom];
+  const int npair = a.ns * a.ns;
+  T acc[NORB];
+  {
+    const T u = (T)(a.U[atom] - a.sigma);
+    const T* xp = x + atom;
+#pragma unroll
+    for (int o = 0; o < NORB; ++o) acc[o] = (a.onsite_t[sp * NORB + o] + u) * xp[o * N];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int* off = IS_A ? a.nt.a_to_b_off[s][k] : a.nt.b_to_a_off[s][k];
+    const int site2 = IS_A ? a.nt.a_to_b_site[s][k] : a.nt.b_to_a_site[s][k];
+    int cell2 = cell;
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int od = off[d];            // uniform over the CTA: -1 or 0 (A sites), 0 or +1 (B sites)
+      cell2 += od * stride[d];
+      if ((od < 0 && lo[d]) || (od > 0 && hi[d])) {
+        ok = ok && g.periodic[d] != OMEN_HARD_WALL;
+        cell2 -= od * extent[d];
+      }
+    }
+    if (!ok) continue;
+    const int atom2 = site2 * g.ncells + cell2;
+    const int slot = IS_A ? (k * 4 + s) * g.ncells + cell : (k * 4 + site2) * g.ncells + cell2;
+    const int sp2 = a.species[atom2];
+    // table in shared memory ordered [direction][pair][entry]: the (at most ns^2) blocks a warp
+    // reads for one direction lie in distinct banks
+    const T* hb = tab + (k * npair + (IS_A ? sp * a.ns + sp2 : sp2 * a.ns + sp)) * (NORB * NORB);
+    const T sc = a.scale[slot];
+    const T* xp = x + atom2;
+    T xn[NORB];
+#pragma unroll
+    for (int o = 0; o < NORB; ++o) xn[o] = xp[o * N] * sc;
+    if constexpr (PAIRED) {
+      // two accumulators per packed FP32x2 FMA (each lane an ordinary fma: same bits as the
+      // scalar form).  A end: acc[r], acc[r+1] += (h[r][c], h[r+1][c]) x[c] from the row-pair
+      // interleaved copy of the table; B end: acc[c], acc[c+1] += (h[r][c], h[r][c+1]) x[r]
+      // from the row-major copy.
+      const float4* h4 = reinterpret_cast<const float4*>(IS_A ? hb + tab_copy : hb);
+#pragma unroll
+      for (int p = 0; p < NORB / 2; ++p) {
+        float2 hp[NORB];
+#pragma unroll
+        for (int q = 0; q < NORB / 2; ++q) {
+          const float4 v = h4[p * (NORB / 2) + q];
+          hp[2 * q] = make_float2(v.x, v.y);
+          hp[2 * q + 1] = make_float2(v.z, v.w);
+        }
+        if constexpr (IS_A) {
+          float2 acc2 = make_float2(acc[2 * p], acc[2 * p + 1]);
+#pragma unroll
+          for (int c = 0; c < NORB; ++c) acc2 = __ffma2_rn(hp[c], make_float2(xn[c], xn[c]), acc2);
+          acc[2 * p] = acc2.x;
+          acc[2 * p + 1] = acc2.y;
+        } else {
+          // hp holds rows 2p and 2p+1 (row-major: NORB/2 pairs per row)
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int q = 0; q < NORB / 2; ++q) {
+              float2 acc2 = make_float2(acc[2 * q], acc[2 * q + 1]);
+              acc2 = __ffma2_rn(hp[i * (NORB / 2) + q], make_float2(xn[2 * p + i], xn[2 * p + i]), acc2);
+              acc[2 * q] = acc2.x;
+              acc[2 * q + 1] = acc2.y;
+            }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r0 = 0; r0 < NORB; r0 += RB) {
+        T hr[RB * NORB];
+        smem_rows<T, NORB, RB>(hb, r0, hr);
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+#pragma unroll
+          for (int o2 = 0; o2 < NORB; ++o2) {
+            if constexpr (IS_A) acc[r0 + i] = fma(hr[i * NORB + o2], xn[o2], acc[r0 + i]);
+            else acc[o2] = fma(hr[i * NORB + o2], xn[r0 + i], acc[o2]);
+          }
+      }
+    }
+  }
+  T* yp = y + atom;
+#pragma unroll
+  for (int o = 0; o < NORB; ++o) yp[o * N] = acc[o];
+}
+
+// Stored blocks: one work item per CTA.  Matrix-free: the b0 table (ns^2 x 4 directions x
+// norb^2 entries, a few KB) is staged in shared memory once per CTA and the CTAs stride over the
+// work items, so the per-bond block reads are shared-memory broadcasts (a warp touches at most
+// ns^2 distinct blocks) instead of divergent L1 traffic.
+template <typename T, int NORB, bool CPLX, bool SO, bool MATFREE, int RBT>
+__global__ void __launch_bounds__(128) hx_kernel(HxArgs<T> a) {
+  if constexpr (MATFREE) {
+    extern __shared__ __align__(16) unsigned char hx_smem[];
+    T* tab = reinterpret_cast<T*>(hx_smem);
+    constexpr int NE = NORB * NORB;
+    const int npair = a.ns * a.ns;
+    const int n = npair * 4 * NE;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if constexpr (CPLX) {
+        tab[i] = a.b0[i];
+      } else {            // b0 is [pair][k][e]; the real rows read [k][pair][e]
+        const int e = i % NE, pk = i / NE, pair = pk >> 2, k = pk & 3;
+        const int blk = (k * npair + pair) * NE;
+        tab[blk + e] = a.b0[i];
+        if constexpr (mf_paired<T, NORB, CPLX>()) {   // row pair p, column c, row parity q
+          const int r = e / NORB, c = e - r * NORB;
+          tab[n + blk + ((r >> 1) * NORB + c) * 2 + (r & 1)] = a.b0[i];
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (!CPLX) {
+      constexpr int RB = RBT > 0 ? RBT : ((sizeof(T) == 4 && NORB % 2 == 0) ? 2 : 1);
+      for (int bid = blockIdx.x; bid < a.nbid; bid += gridDim.x) {
+        if ((bid & 7) < 4) hx_item_mf_real<T, NORB, RB, true>(a, bid, tab);
+        else hx_item_mf_real<T, NORB, RB, false>(a, bid, tab);
+      }
+    } else {
+      for (int bid = blockIdx.x; bid < a.nbid; bid += gridDim.x) hx_item<T, NORB, CPLX, SO, true, RBT>(a, bid, tab);
+    }
+  } else {
+    hx_item<T, NORB, CPLX, SO, false, RBT>(a, blockIdx.x, nullptr);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -507,19 +703,41 @@ size_t vec_elem_bytes(const omen_ham* h, int precision) {
 }
 
 template <typename T, int NORB, bool CPLX, bool SO, bool MF, int RBT>
-static cudaError_t launch_t(const HxArgs<T>& a, int nvec, int threads, cudaStream_t st) {
-  dim3 grid(((a.cell1 - a.cell0 + threads - 1) / threads) * 8, 1, nvec);
-  hx_kernel<T, NORB, CPLX, SO, MF, RBT><<<grid, threads, 0, st>>>(a);
-  return cudaGetLastError();
+static cudaError_t launch_t(const HxArgs<T>& a0, int nvec, int threads, cudaStream_t st) {
+  HxArgs<T> a = a0;
+  a.nbid = ((a.cell1 - a.cell0 + threads - 1) / threads) * 8;
+  if constexpr (!MF) {
+    dim3 grid(a.nbid, 1, nvec);
+    hx_kernel<T, NORB, CPLX, SO, false, RBT><<<grid, threads, 0, st>>>(a);
+    return cudaGetLastError();
+  } else {
+    // one resident wave of CTAs (per vector), each striding over the work items
+    const size_t smem = (size_t)a.ns * a.ns * 4 * NORB * NORB * sizeof(T) * (mf_paired<T, NORB, CPLX>() ? 2 : 1);
+    auto kern = hx_kernel<T, NORB, CPLX, SO, true, RBT>;
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    const int wave = std::max(1, sms * std::max(1, per_sm));
+    dim3 grid(std::min(a.nbid, wave), 1, nvec);
+    kern<<<grid, threads, smem, st>>>(a);
+    return cudaGetLastError();
+  }
 }
 
 // Register-batch sizes compiled for each variant (0 = the built-in rule): FP32 stored blocks
 // take 1, 2, 5 or NORB rows (NORB only without spin-orbit); FP64 stored 1 or 2; matrix-free
-// only the rule.
+// 1 or 2 (rows dividing the orbital count).
 template <typename T, int NORB, bool SO, bool MF>
 static constexpr bool rb_compiled(int rb) {
   if (rb == 0) return true;
-  if (MF || NORB % rb != 0) return false;
+  if (NORB % rb != 0) return false;
+  if (MF) return rb == 1 || rb == 2;
   if (sizeof(T) == 8) return rb == 1 || rb == 2;
   return rb == 1 || rb == 2 || rb == 5 || (rb == NORB && !SO);
 }
@@ -560,24 +778,25 @@ bool hx_tile_valid(const omen_ham* h, int vec_precision, int threads, int rb) {
 }
 
 template <typename T>
-static cudaError_t launch_prec(const omen_ham* h, const T* blk, const T* b0, const void* x, void* y, int nvec,
-                               double sigma, cudaStream_t st, int cell0, int cell1) {
+static cudaError_t launch_prec(const omen_ham* h, const T* blk, const T* b0, const T* scale, const void* x, void* y,
+                               int nvec, double sigma, cudaStream_t st, int cell0, int cell1) {
   const omen_lattice* L = h->lat;
   HxArgs<T> a;
   a.g = Geo{L->nx, L->ny, L->nz, L->ncells, L->natoms, {L->periodic[0], L->periodic[1], L->periodic[2]}};
   a.nt = host_neighbour_tables();
   a.blk = blk;
   a.b0 = b0;
-  a.strain = L->d_strain;
+  a.scale = scale;
   a.species = L->d_species;
   a.onsite = h->d_onsite;
+  if constexpr (sizeof(T) == 8) a.onsite_t = reinterpret_cast<const T*>(h->d_onsite);
+  else a.onsite_t = reinterpret_cast<const T*>(h->d_onsite32);
   a.U = h->d_U;
   a.lambda = h->d_lambda;
   a.x = x;
   a.y = y;
   a.nrows = h->nrows;
   a.sigma = sigma;
-  a.eta = h->eta;
   for (int d = 0; d < 3; ++d) a.phase[d] = h->phase[d];
   a.ns = h->nspecies;
   a.slot_stride = h->slot_stride;
@@ -598,10 +817,10 @@ static omen_status launch_hx_cells(omen_ctx* ctx, const omen_ham* h, const void*
     e = launch_df(h, x, y, nvec, sigma, st, cell0, cell1);
   } else if (vec_precision == OMEN_F64) {
     if (!h->matrix_free && !h->d_blk64) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP64 blocks");
-    e = launch_prec<double>(h, h->d_blk64, h->d_b0_64, x, y, nvec, sigma, st, cell0, cell1);
+    e = launch_prec<double>(h, h->d_blk64, h->d_b0_64, h->d_scale64, x, y, nvec, sigma, st, cell0, cell1);
   } else {
     if (!h->matrix_free && !h->d_blk32) return set_err(ctx, OMEN_EINVAL, "Hamiltonian has no FP32 blocks");
-    e = launch_prec<float>(h, h->d_blk32, h->d_b0_32, x, y, nvec, sigma, st, cell0, cell1);
+    e = launch_prec<float>(h, h->d_blk32, h->d_b0_32, h->d_scale32, x, y, nvec, sigma, st, cell0, cell1);
   }
   if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "H·X launch failed: %s", cudaGetErrorString(e));
   return OMEN_OK;

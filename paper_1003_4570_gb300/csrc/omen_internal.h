@@ -61,11 +61,15 @@ struct omen_ham {
   double* d_blk64 = nullptr;
   float* d_blk32 = nullptr;
   float2* d_blkdf = nullptr;              // double-float (hi, lo) blocks, same tiled layout
-  // matrix-free table: B0[((sa*ns + sb)*4 + k)*norb*norb + e]
+  // matrix-free table: B0[((sa*ns + sb)*4 + k)*norb*norb + e], and the per-slot bond-length
+  // factor (d0/d)^eta of the structure's strain at assembly ([16*ncells], slot layout)
   double* d_b0_64 = nullptr;
   float* d_b0_32 = nullptr;
+  double* d_scale64 = nullptr;
+  float* d_scale32 = nullptr;
   // onsite energies per species and orbital [ns][norb], potential per atom
   double* d_onsite = nullptr;
+  float* d_onsite32 = nullptr;            // the same in FP32
   float2* d_onsite_df = nullptr;          // the same as double-float pairs (OMEN_F64_DF)
   double* d_U = nullptr;                  // [natoms]
   double lambda_so[4] = {0, 0, 0, 0};
