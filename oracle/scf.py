@@ -6,12 +6,17 @@ until self-consistent.  The paper's outer iteration is Newton–Raphson; this lo
 mixing phi <- phi + mix (phi_out - phi), or Anderson mixing over the last mix_history iterates,
 and stops when max |phi_out - phi| < tol_V, the reading the GPU path follows.  Electron potential energy U = -phi (eV per V).  Only states
 above e_cut (mid-gap) hold electrons; g_s = 2.
+
+poisson="newton": phi_out is the root of the nonlinear Poisson equation with the frozen
+states' predicted charge (oracle/newton.py: Newton–Raphson, Section III-A item 3) instead of
+the linear Poisson solution with the states' charge; the loop, the mixing and the stopping rule
+are the same, and a self-consistent potential is a fixed point of both maps.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import charge, eigs, hamiltonian, lattice, poisson
+from . import charge, eigs, hamiltonian, lattice, newton, poisson
 
 Q_E = poisson.Q_E
 
@@ -46,7 +51,8 @@ def anderson_update(phi, F, dX, dF, beta):
 
 
 def scf(spec, params, grid, donor_rho, n_electrons, kT, kpts, kweights, nev, sigma, e_cut,
-        mix=0.1, tol_V=1e-6, max_iter=300, phi0=None, gs=2.0, mix_history=0):
+        mix=0.1, tol_V=1e-6, max_iter=300, phi0=None, gs=2.0, mix_history=0, poisson_mode="linear",
+        newton_tol=1e-10):
     pos = atom_positions_nm(spec)
     bonds = lattice.find_bonds(spec.nx, spec.ny, spec.nz, spec.periodic)
     phi = np.zeros(grid.shape) if phi0 is None else np.array(phi0, float).reshape(grid.shape)
@@ -73,8 +79,18 @@ def scf(spec, params, grid, donor_rho, n_electrons, kT, kpts, kweights, nev, sig
         for w, V, wk in states:
             occ = np.where(w > e_cut, charge.fermi(w, EF, kT), 0.0)
             n_atom += gs * wk * charge.atom_density(V, occ, spec.natoms)
-        rho = charge.deposit(grid, pos, -Q_E * n_atom) + donor_rho
-        phi_out = poisson.solve_direct(grid, rho)
+        if poisson_mode == "newton":
+            cols, levels_n = [], []
+            for w, V, wk in states:
+                m = w > e_cut
+                if m.any():
+                    cols.append(newton.state_weights(V[:, m], gs * wk, spec.natoms))
+                    levels_n.append(w[m])
+            prob = newton.Problem(grid, pos, np.hstack(cols), np.concatenate(levels_n), EF, kT, phi, donor_rho)
+            phi_out, _ = newton.solve(prob, phi, tol=newton_tol)
+        else:
+            rho = charge.deposit(grid, pos, -Q_E * n_atom) + donor_rho
+            phi_out = poisson.solve_direct(grid, rho)
         dV = np.abs(phi_out - phi).max()
         history.append(dV)
         if dV < tol_V:
