@@ -24,4 +24,6 @@ poisson      3-D finite-difference Poisson (periodic x,y; Dirichlet z) by direct
 charge       Fermi–Dirac filling, Fermi level by bisection, cloud-in-cell deposit and gather.
 effmass      single-band effective-mass Hamiltonian on a uniform grid (explicit CSR).
 vff          Keating valence force field: strain energy, forces, relaxation, bond strains.
+spmv         the plain CSR product of csr_matvec.c over all host cores (timing the oracle's
+             repeated H·X; same sums as scipy's product).
 """

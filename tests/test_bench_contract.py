@@ -48,7 +48,9 @@ def test_reference_arm_prints_the_contract_line():
                 "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
-    assert line["config"]["atoms"] == 1_000_000 and line["config"]["bonds"] == 1_970_150
+    # the config names the slab the reference arm times (50 x 50 x 4 cells of the 1M-atom recipe)
+    assert line["config"]["atoms"] == 80_000 and line["config"]["rows"] == 800_000
+    assert "50x50x4" in line["config"]["workload"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
