@@ -95,8 +95,17 @@ omen_status omen_set_graph_capture(omen_ctx* ctx, int enable);
  * Ritz values of working accuracy (Simon, Math. Comp. 42 (1984) 115; the paper's Lanczos
  * solver, Section III-A item 1, does not say how it orthogonalises).  It saves the update only
  * while no Ritz pair has converged; it costs one extra norm per step.  The first step after a
- * start or restart always takes two full passes.  EINVAL for another value. */
-enum { OMEN_REORTH_FULL = 0, OMEN_REORTH_SEMI = 1 };
+ * start or restart always takes two full passes.  OMEN_REORTH_PARTIAL (FP64 vectors, real or
+ * complex; FP32 and double-float vectors keep the full pass: an FP32 basis driven past its
+ * rounding floor loses orthogonality faster than the estimates follow) skips the projection as
+ * well: it estimates the overlaps
+ * of each new vector with the basis from the projected matrix by Simon's recurrence
+ * (omega_{j+1} from omega_j, omega_{j-1}, the columns of T and a rounding term; the estimate
+ * recurrence as in Larsen's PROPACK) and runs the full pass, for that vector and the next, only
+ * when an estimate exceeds the square root of the unit roundoff.  A step then reads the basis
+ * only when a pass runs.  Every result is still checked by FP64 residuals.  EINVAL for another
+ * value. */
+enum { OMEN_REORTH_FULL = 0, OMEN_REORTH_SEMI = 1, OMEN_REORTH_PARTIAL = 2 };
 omen_status omen_set_reorthogonalization(omen_ctx* ctx, int policy);
 
 /* Missed-copy check of single-vector solves for the lowest eigenvalues (default on).  A
@@ -439,6 +448,57 @@ omen_status omen_poisson(omen_ctx* ctx, const omen_grid* grid, const double* rho
 omen_status omen_poisson_static(const omen_grid* grid, const double* rho_dev, double* phi_dev,
                                 const omen_cg_opts* opts, omen_solve_info* info, void* cuda_stream);
 
+/* Newton–Raphson nonlinear Poisson (paper Section III-A item 3: the converged potential of the
+ * Poisson solver is obtained iteratively by Newton–Raphson).  The eigenstates computed in the
+ * potential phi_in are frozen; the electrons respond to a change of potential by a local shift of
+ * the levels (the predictor of Trellakis et al., J. Appl. Phys. 81, 7880 (1997)):
+ *   n_i(phi) = sum_n W_ni f((E_n - u_i - E_F)/kT),  u_i = phi(r_i) - phi_in(r_i)
+ * (potential at the atoms by trilinear interpolation, as omen_gather), and
+ *   -div(eps0 eps_r grad phi) = rho_D - q * deposit(n(phi))
+ * (cloud-in-cell deposit as omen_deposit) is solved by Newton–Raphson with the exact Jacobian,
+ * each step a conjugate-gradient solve in one cooperative launch. */
+typedef struct {
+  int nstates;
+  const double* E_host;      /* [nstates] levels (eV) in the potential phi_in */
+  const double* W_dev;       /* [nstates][natoms] electrons each state puts on each atom when full
+                                (spin and k weight included; 0 for states that hold none), e.g.
+                                from omen_state_weights */
+  double E_F;                /* eV */
+  double kT;                 /* eV, > 0 */
+  const double* phi_in_dev;  /* grid potential the states were computed in (V) */
+} omen_frozen_states;
+
+typedef struct {
+  double tol_V;              /* stop when the largest change of a Newton step is below tol_V */
+  int max_iter;              /* Newton steps */
+  omen_cg_opts cg;           /* each step's CG on the Jacobian (relative residual, iterations) */
+} omen_newton_opts;
+
+typedef struct {
+  int iterations;            /* Newton steps taken */
+  int converged;
+  double last_step_V;        /* max |change| of the last step */
+  long long cg_iterations;   /* CG iterations over all steps */
+  double seconds;
+} omen_newton_info;
+
+/* Solve the nonlinear Poisson equation above on grid for the structure lat.  rho_d_dev: fixed
+ * (donor) charge density on the interior unknowns (C/m^3); phi_dev: start in (e.g. phi_in),
+ * root out.  Allocates its work (maps and vectors, about 24 words per atom and 5 per unknown)
+ * on ctx's stream; synchronous.  EINVAL for bad arguments, ENOCONV when a CG solve or the
+ * Newton iteration hits its limit (phi_dev holds the last iterate), ENUMERIC on a non-finite
+ * step. */
+omen_status omen_poisson_newton(omen_ctx* ctx, const omen_lattice* lat, const omen_grid* grid,
+                                const omen_frozen_states* states, const double* rho_d_dev, double* phi_dev,
+                                const omen_newton_opts* opts, omen_newton_info* info);
+
+/* W_dev[n][i] = weight_host[n] * sum_o |psi_n(o*natoms + i)|^2 for nstates FP64 (double or
+ * complex128) vectors psi_dev [nstates][nrows] of a tight-binding Hamiltonian: the W of
+ * omen_frozen_states (weight = spin degeneracy times k weight, 0 for states that hold no
+ * electrons).  EUNSUPPORTED for an effective-mass Hamiltonian. */
+omen_status omen_state_weights(omen_ctx* ctx, const omen_ham* ham, const void* psi_dev, int nstates,
+                               const double* weight_host, double* W_dev);
+
 /* n_atom_dev[i] += weight * sum_n occ_host[n] * sum_o |psi_n(o*natoms + i)|^2 for nstates FP64
  * (double or complex128) vectors psi_dev [nstates][nrows] of ham (paper: charge from the
  * filled states, Section III-A item 2). */
@@ -482,6 +542,10 @@ typedef struct {
   double tol_V;              /* stop when max |phi_out - phi| < tol_V */
   int max_iter;
   omen_cg_opts cg;
+  int poisson_newton;        /* 0: phi_out solves the linear Poisson equation with the states'
+                                charge; 1: phi_out is the root of the nonlinear Poisson equation
+                                with the frozen states' predicted charge (omen_poisson_newton,
+                                steps to min(1e-9, tol_V/100) V, CG options as above) */
 } omen_scf_desc;
 
 typedef struct {
@@ -496,7 +560,8 @@ typedef struct {
 
 /* Self-consistent Schrödinger–Poisson loop (paper Section III-A): potential -> onsite
  * U = -phi at the atoms -> eigenstates per k -> Fermi level by neutrality -> electron charge
- * -> Poisson -> mixing (linear or Anderson), until max |phi_out - phi| < tol_V.  phi_dev: grid potential, start
+ * -> Poisson (linear, or Newton–Raphson with the frozen-state predictor) -> mixing (linear or
+ * Anderson), until max |phi_out - phi| < tol_V.  phi_dev: grid potential, start
  * value in (zeros = zero-field start), converged potential out.  ENOCONV at max_iter;
  * ENUMERIC if the highest computed state of some k is occupied above 1e-12 (nev too small). */
 omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* desc, double* phi_dev, omen_scf_info* info);

@@ -1,5 +1,5 @@
-// Finite-difference Poisson solver (paper Section III-A item 3: "finite difference method"
-// with an iterative linear solver; Aztec there, conjugate gradients here).
+// Finite-difference Poisson solver (paper Section III-A item 3: a finite-difference Poisson
+// equation and an iterative linear solver; Aztec there, conjugate gradients here).
 //
 // -div(eps0 eps_r grad phi) = rho on a uniform grid: 7-point stencil, periodic along x and y,
 // phi = 0 on the z = 0 and z = Lz planes.  The operator is symmetric positive definite, so
@@ -16,74 +16,7 @@
 
 namespace cgr = cooperative_groups;
 
-static constexpr double kEps0 = 8.8541878128e-12;  // F/m
-
-struct PGrid {
-  int nx, ny, nzi;           // nzi = nz - 1 interior planes
-  double cx, cy, cz;         // 1/h^2 (1/m^2)
-  long long n;
-};
-
-__device__ __forceinline__ double stencil(const double* __restrict__ v, const PGrid& g, long long idx) {
-  const int i = (int)(idx % g.nx);
-  const int j = (int)((idx / g.nx) % g.ny);
-  const int k = (int)(idx / ((long long)g.nx * g.ny));
-  const long long plane = (long long)g.nx * g.ny;
-  const double c = v[idx];
-  const int ip = (i + 1 == g.nx) ? 0 : i + 1, im = (i == 0) ? g.nx - 1 : i - 1;
-  const int jp = (j + 1 == g.ny) ? 0 : j + 1, jm = (j == 0) ? g.ny - 1 : j - 1;
-  const long long row = idx - i - (long long)j * g.nx;
-  double s = g.cx * (2.0 * c - v[row + (long long)j * g.nx + ip] - v[row + (long long)j * g.nx + im]);
-  s += g.cy * (2.0 * c - v[row + (long long)jp * g.nx + i] - v[row + (long long)jm * g.nx + i]);
-  const double up = (k + 1 < g.nzi) ? v[idx + plane] : 0.0;
-  const double dn = (k > 0) ? v[idx - plane] : 0.0;
-  s += g.cz * (2.0 * c - up - dn);
-  return s;
-}
-
-// The same stencil with the cell coordinates given (no divisions per element).
-__device__ __forceinline__ double stencil_at(const double* __restrict__ v, const PGrid& g, int i, int j, int k,
-                                            long long idx) {
-  const long long plane = (long long)g.nx * g.ny;
-  const double c = v[idx];
-  const int ip = (i + 1 == g.nx) ? 0 : i + 1, im = (i == 0) ? g.nx - 1 : i - 1;
-  const int jp = (j + 1 == g.ny) ? 0 : j + 1, jm = (j == 0) ? g.ny - 1 : j - 1;
-  const long long row = idx - i;
-  double s = g.cx * (2.0 * c - v[row + ip] - v[row + im]);
-  s += g.cy * (2.0 * c - v[row + (long long)(jp - j) * g.nx + i] - v[row + (long long)(jm - j) * g.nx + i]);
-  const double up = (k + 1 < g.nzi) ? v[idx + plane] : 0.0;
-  const double dn = (k > 0) ? v[idx - plane] : 0.0;
-  s += g.cz * (2.0 * c - up - dn);
-  return s;
-}
-
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
-  return t;  // valid in thread 0
-}
-
-// every block sums the partials of all blocks in index order (same result everywhere)
-__device__ __forceinline__ double grid_total(const double* __restrict__ part, double* sh) {
-  double t = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += part[b];
-  // ordered: reduce within the block deterministically
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = t;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
-  __syncthreads();
-  return s;
-}
+#include "fd.cuh"
 
 struct CGOut {
   int iterations;

@@ -133,7 +133,7 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
   }
   const long long nrows = hams[0]->nrows;
   const size_t elem = hams[0]->is_complex ? 16 : 8;
-  DevVec phi_atom, U, n_atom, q, rho, phi_out, part, psi, v0, Fcur, Fprev, Xprev, dXh, dFh, gpart, gam;
+  DevVec phi_atom, U, n_atom, q, rho, phi_out, part, psi, v0, Fcur, Fprev, Xprev, dXh, dFh, gpart, gam, Wst, zero_rho;
   const int H = std::max(0, std::min(8, d->mix_history));
   const int nblk = 256;
   if (!phi_atom.alloc(sizeof(double) * N) || !U.alloc(sizeof(double) * N) || !n_atom.alloc(sizeof(double) * N) ||
@@ -145,6 +145,13 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
       !gpart.alloc(sizeof(double) * 81 * 256) || !gam.alloc(sizeof(double) * 8)) {
     free_hams();
     return set_err(ctx, OMEN_ENOMEM, "SCF work buffers");
+  }
+  if (d->poisson_newton) {
+    if (!Wst.alloc(sizeof(double) * (size_t)N * d->nev * d->nk) || (!d->donor_rho_dev && !zero_rho.alloc(sizeof(double) * ng))) {
+      free_hams();
+      return set_err(ctx, OMEN_ENOMEM, "SCF Newton buffers");
+    }
+    if (!d->donor_rho_dev) OMEN_CUDA(ctx, cudaMemsetAsync(zero_rho.p, 0, sizeof(double) * ng, ctx->stream));
   }
   const unsigned ga = (unsigned)std::min(4096, (N + 255) / 256);
   const unsigned gg = (unsigned)std::min<long long>(nblk, (ng + 255) / 256);
@@ -212,6 +219,24 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
       }
     }
     if (st != OMEN_OK) break;
+    if (d->poisson_newton) {
+      // the root of the nonlinear Poisson equation with the frozen states' predicted charge
+      for (int k = 0; k < d->nk && st == OMEN_OK; ++k) {
+        std::vector<double> wk(d->nev);
+        for (int n = 0; n < d->nev; ++n) wk[n] = evals[(size_t)k * d->nev + n] > d->e_cut ? gs * d->kw_host[k] : 0.0;
+        st = omen_state_weights(ctx, hams[k], static_cast<char*>(psi.p) + elem * nrows * (size_t)d->nev * k, d->nev,
+                                wk.data(), Wst.d() + (size_t)N * d->nev * k);
+      }
+      if (st != OMEN_OK) break;
+      OMEN_CUDA(ctx, cudaMemcpyAsync(phi_out.p, phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, ctx->stream));
+      omen_frozen_states fs{d->nev * d->nk, evals.data(), Wst.d(), EF, d->kT, phi};
+      omen_newton_opts no{std::min(1e-9, 0.01 * d->tol_V), 50, d->cg};
+      omen_newton_info ni{};
+      auto tp = std::chrono::steady_clock::now();
+      st = omen_poisson_newton(ctx, L, G, &fs, d->donor_rho_dev ? d->donor_rho_dev : zero_rho.d(), phi_out.d(), &no, &ni);
+      inf->poisson_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - tp).count();
+      if (st != OMEN_OK) break;
+    } else {
     // electrons per atom
     OMEN_CUDA(ctx, cudaMemsetAsync(n_atom.p, 0, sizeof(double) * N, ctx->stream));
     for (int k = 0; k < d->nk && st == OMEN_OK; ++k) {
@@ -236,6 +261,7 @@ extern "C" omen_status omen_scf(omen_ctx* ctx, const omen_scf_desc* d, double* p
     st = omen_poisson(ctx, G, rho.d(), phi_out.d(), &d->cg, &si);
     inf->poisson_seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - tp).count();
     if (st != OMEN_OK) break;
+    }
     maxdiff_kernel<<<gg, 256, 0, ctx->stream>>>(phi_out.d(), phi, ng, part.d());
     std::vector<double> hp(gg);
     OMEN_CUDA(ctx, cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * gg, cudaMemcpyDeviceToHost, ctx->stream));

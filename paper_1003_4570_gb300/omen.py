@@ -89,7 +89,24 @@ class SCFDesc(C.Structure):
                 ("k_host", C.c_void_p), ("kw_host", C.c_void_p), ("nev", C.c_int), ("sigma", C.c_double),
                 ("e_cut", C.c_double), ("eig_tol", C.c_double), ("eig_block", C.c_int), ("eig_basis", C.c_int),
                 ("eig_max_iter", C.c_int), ("mix", C.c_double), ("mix_history", C.c_int), ("tol_V", C.c_double),
-                ("max_iter", C.c_int), ("cg", CGOpts)]
+                ("max_iter", C.c_int), ("cg", CGOpts), ("poisson_newton", C.c_int)]
+
+
+class FrozenStates(C.Structure):
+    _fields_ = [("nstates", C.c_int), ("E_host", C.c_void_p), ("W_dev", C.c_void_p), ("E_F", C.c_double),
+                ("kT", C.c_double), ("phi_in_dev", C.c_void_p)]
+
+
+class NewtonOpts(C.Structure):
+    _fields_ = [("tol_V", C.c_double), ("max_iter", C.c_int), ("cg", CGOpts)]
+
+
+class NewtonInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("last_step_V", C.c_double),
+                ("cg_iterations", C.c_longlong), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class SCFInfo(C.Structure):
@@ -175,6 +192,9 @@ def lib():
             "omen_gather": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
             "omen_fermi_level": (i, [vp, vp, i, d, d, C.POINTER(d)]),
             "omen_scf": (i, [vp, C.POINTER(SCFDesc), vp, C.POINTER(SCFInfo)]),
+            "omen_poisson_newton": (i, [vp, vp, C.POINTER(Grid), C.POINTER(FrozenStates), vp, vp, C.POINTER(NewtonOpts),
+                                        C.POINTER(NewtonInfo)]),
+            "omen_state_weights": (i, [vp, vp, vp, i, vp, vp]),
             "omen_mlp_create": (i, [vp, C.POINTER(MLPDesc), vp, C.POINTER(vp)]),
             "omen_mlp_free": (None, [vp]),
             "omen_mlp_param_count": (ll, [vp]),
@@ -259,7 +279,7 @@ def omen_create(device=0, stream=None) -> Context:
     return Context(h)
 
 
-OMEN_REORTH_FULL, OMEN_REORTH_SEMI = 0, 1
+OMEN_REORTH_FULL, OMEN_REORTH_SEMI, OMEN_REORTH_PARTIAL = 0, 1, 2
 
 
 def omen_set_reorthogonalization(ctx: Context, policy) -> None:
@@ -517,7 +537,7 @@ def omen_fermi_level(E, level_weight, n_target, kT):
 def omen_scf(ctx: Context, lat: Lattice, params, grid, phi_dev, donor_rho_dev, n_electrons, kT, kpts, kweights,
              nev, sigma, e_cut, precision=OMEN_F64, eig_tol=1e-9, eig_block=1, eig_basis=None, eig_max_iter=20000,
              mix=0.1, tol_V=1e-6, max_iter=300, cg_rtol=1e-13, cg_max_iter=100000, raise_on_noconv=True,
-             mix_history=0):
+             mix_history=0, poisson_newton=False):
     """Self-consistent loop in place on phi_dev.  Returns (info dict, status)."""
     tp = tb_params_struct(params)
     g = grid_struct(grid)
@@ -528,9 +548,34 @@ def omen_scf(ctx: Context, lat: Lattice, params, grid, phi_dev, donor_rho_dev, n
     d = SCFDesc(lat.handle, C.addressof(tp), int(precision), C.addressof(g), _ptr(donor_rho_dev), float(n_electrons),
                 float(kT), len(kw), k.ctypes.data, kw.ctypes.data, int(nev), float(sigma), float(e_cut), float(eig_tol),
                 int(eig_block), int(eig_basis), int(eig_max_iter), float(mix), int(mix_history), float(tol_V),
-                int(max_iter), CGOpts(float(cg_rtol), int(cg_max_iter)))
+                int(max_iter), CGOpts(float(cg_rtol), int(cg_max_iter)), int(bool(poisson_newton)))
     info = SCFInfo()
     s = lib().omen_scf(ctx.handle, C.byref(d), _ptr(phi_dev), C.byref(info))
+    if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
+        ctx.check(s)
+    return info.as_dict(), s
+
+
+def omen_state_weights(ctx: Context, ham: Hamiltonian, psi_dev, nstates, weights, W_dev) -> None:
+    """W_dev[n][atom] = weights[n] * sum_orb |psi_n|^2 (FP64 eigenvectors of a tight-binding H)."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    natoms, _ = ham.lattice.counts()
+    _need(psi_dev, int(nstates) * ham.nrows * ham.evec_bytes, "psi_dev")
+    _need(W_dev, int(nstates) * natoms * 8, "W_dev")
+    ctx.check(lib().omen_state_weights(ctx.handle, ham.handle, _ptr(psi_dev), int(nstates), w.ctypes.data, _ptr(W_dev)))
+
+
+def omen_poisson_newton(ctx: Context, lat: Lattice, grid, E, W_dev, E_F, kT, phi_in_dev, rho_d_dev, phi_dev,
+                        tol_V=1e-10, max_iter=50, cg_rtol=1e-12, cg_max_iter=100000, raise_on_noconv=True):
+    """Root of the nonlinear Poisson equation with the frozen states' predicted charge, in place
+    on phi_dev.  Returns (info dict, status)."""
+    g = grid_struct(grid)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    fs = FrozenStates(len(E), E.ctypes.data if len(E) else None, _ptr(W_dev), float(E_F), float(kT), _ptr(phi_in_dev))
+    o = NewtonOpts(float(tol_V), int(max_iter), CGOpts(float(cg_rtol), int(cg_max_iter)))
+    info = NewtonInfo()
+    s = lib().omen_poisson_newton(ctx.handle, lat.handle, C.byref(g), C.byref(fs), _ptr(rho_d_dev), _ptr(phi_dev),
+                                  C.byref(o), C.byref(info))
     if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
         ctx.check(s)
     return info.as_dict(), s

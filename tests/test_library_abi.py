@@ -54,7 +54,8 @@ STRUCTS = {
     "TuneResult": "omen_tune_result", "SolveInfo": "omen_solve_info", "SCFDesc": "omen_scf_desc",
     "SCFInfo": "omen_scf_info", "EffMassDesc": "omen_effmass_desc", "MLPDesc": "omen_mlp_desc",
     "KbatchItem": "omen_kbatch_item", "VFFParams": "omen_vff_params", "VFFOpts": "omen_vff_opts",
-    "VFFInfo": "omen_vff_info",
+    "VFFInfo": "omen_vff_info", "FrozenStates": "omen_frozen_states", "NewtonOpts": "omen_newton_opts",
+    "NewtonInfo": "omen_newton_info",
 }
 
 
