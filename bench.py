@@ -246,10 +246,12 @@ def measure_variants(ctx, omen, lat, p, natoms, nbonds, reps=50):
 
 def measure_lanczos(ctx, omen, ham, iters=500, basis=64):
     """The paper's benchmark unit (Section II-B): wall time of 500 Lanczos iterations, with the
-    default full Gram–Schmidt update at every step and with the semi-orthogonal policy."""
+    default full Gram–Schmidt update at every step, with the semi-orthogonal policy (overlaps
+    measured every step) and with partial reorthogonalisation (overlaps estimated)."""
     import torch
     out = {}
-    for name, pol in (("full_update", omen.OMEN_REORTH_FULL), ("semi_orthogonal", omen.OMEN_REORTH_SEMI)):
+    for name, pol in (("full_update", omen.OMEN_REORTH_FULL), ("semi_orthogonal", omen.OMEN_REORTH_SEMI),
+                      ("partial_reorthogonalization", omen.OMEN_REORTH_PARTIAL)):
         omen.omen_set_reorthogonalization(ctx, pol)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -554,6 +556,61 @@ def measure_kbatch(ctx, omen, nxy=4, nz=80, nk=32, nev=8, seed=7):
     return out
 
 
+def c5_kpoints(L):
+    """The 4 x 4 Monkhorst-Pack mesh of the lateral zone, halved by time reversal (H(-k) is the
+    complex conjugate of H(k)): 8 wave vectors (1/nm), weight 1/8 each."""
+    ks = [(i / 8 * 2 * np.pi / L, j / 8 * 2 * np.pi / L, 0.0) for i in (1, 3) for j in (1, 3, -1, -3)]
+    return np.array(ks), np.full(len(ks), 1.0 / len(ks))
+
+
+def launch_hx_shapes(ctx, omen, cells):
+    """Profiling aid: one FP64 stored H·X launch per compiled launch shape (CTA width 32, 64, 96,
+    128 x block rows per batch 1, 2), in that order, on the alloy recipe at cells^3, so that one
+    ncu capture of the 8 launches gives each shape's DRAM traffic per bond."""
+    import torch
+    spec, p = synth.config_sige_alloy(cells, seed=2)
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p)
+    x = torch.rand(ham.nrows, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    shapes = [(t, rb) for t in (32, 64, 96, 128) for rb in (1, 2)]
+    for t, rb in shapes:
+        omen.omen_hx_set_tile(ctx, ham, omen.OMEN_F64, t, rb)
+        omen.omen_hx(ctx, ham, x, y)
+    torch.cuda.synchronize()
+    return {"cells": cells, "bonds": lat.counts()[1], "shapes_in_launch_order": shapes}
+
+
+def measure_c5_solve_cost(ctx, omen, nev=32, seed=5):
+    """One zero-field eigen-solve of the 4x4x80-cell delta layer (10,240 atoms, 102,400 complex
+    rows) at one wave vector of the 4x4 mesh: the 32 states nearest sigma = E_c - 0.4 E_g by
+    folded-spectrum Lanczos (single vector and block 4), to the 1e-6 eV bound of the first SCF
+    iteration.  One SCF iteration of the configured workload needs this for 8 wave vectors."""
+    import torch
+    spec, p, _ = synth.delta_layer(4, 80, seed=seed)
+    L = 4 * spec.a_nm
+    ks, _ = c5_kpoints(L)
+    eg = synth.GAPPED_SI_EC - synth.GAPPED_SI_EV
+    sigma = synth.GAPPED_SI_EC - 0.4 * eg
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, k=tuple(ks[0]))
+    out = {"workload": "delta-doped Si 4x4x80 cells (10,240 atoms, 102,400 complex rows), k = (1/8, 1/8) of the "
+                       f"4x4 mesh, {nev} states nearest sigma, zero field", "runs": []}
+    for block, basis in ((1, 96), (4, 96), (4, 256), (1, 384)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, info, st = omen.omen_eigs(ctx, ham, nev, omen.OMEN_NEAREST, sigma=sigma, tol=1e-6, block=block, basis=basis,
+                                      max_iter=400000, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        out["runs"].append({"block": block, "basis": basis, "seconds": time.perf_counter() - t0,
+                            "steps": info["iterations"], "converged": info["converged"],
+                            "bound": info["max_error_bound"], "levels_eV": [float(min(ev)), float(max(ev))]})
+        print(json.dumps(out["runs"][-1]), flush=True)
+    best = min(r["seconds"] for r in out["runs"] if r["converged"])
+    out["per_scf_iteration_seconds_8k"] = 8 * best
+    return out
+
+
 def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
     """SCF iterations and wall time from the zero-field start and from the learned start.
 
@@ -839,10 +896,12 @@ def main():
                     "smaller only for profiling captures)")
     ap.add_argument("--scf-full", action="store_true",
                     help="one-off: warm-start network trained on 200 SCF solutions, 20 held-out profiles (minutes)")
+    ap.add_argument("--scf-study", default="", metavar="NZ,NTRAIN,NTEST",
+                    help="one-off: warm-start study on a 1x1xNZ-cell slab (NTRAIN training, NTEST held-out profiles)")
     ap.add_argument("--kbatch-full", action="store_true",
                     help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
     ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube", "so-eigs",
-                                                   "so-all", "effmass", "m2-ladder"],
+                                                   "so-all", "effmass", "m2-ladder", "c5-solve", "hx-shapes"],
                     help="profiling aid: run one side measurement alone and print its JSON")
     ap.add_argument("--tile", default="", metavar="THREADS,RB",
                     help="fix the H·X launch shape instead of tuning it (e.g. 64,2; profiling aid)")
@@ -861,6 +920,14 @@ def main():
         ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
         print(json.dumps({"scf_full": measure_scf(ctx, omen, n_train=200, n_test=20, train_steps=2000)}))
         return
+    if args.scf_study:
+        import torch
+        from paper_1003_4570_gb300 import omen
+        ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+        nz, ntr, nte = (int(v) for v in args.scf_study.split(","))
+        print(json.dumps({"scf_study": measure_scf(ctx, omen, nzc=nz, n_train=ntr, n_test=nte,
+                                                   train_steps=max(400, 10 * ntr))}))
+        return
     if args.kbatch_full:
         import torch
         from paper_1003_4570_gb300 import omen
@@ -877,9 +944,12 @@ def main():
             which = "so_f32_refine64" if args.only == "so-eigs" else "so-all"
             print(json.dumps({args.only: measure_eigs_1m(ctx, omen, lat, p, only=which)}))
             return
+        if args.only == "hx-shapes":
+            print(json.dumps({"hx_shapes": launch_hx_shapes(ctx, omen, args.cells)}))
+            return
         fn = {"kbatch": measure_kbatch, "hx-kbatch": measure_hx_kbatch, "scf": measure_scf,
               "small-si": measure_small_si, "cube": measure_cube_500, "effmass": measure_effmass,
-              "m2-ladder": measure_m2_ladder}[args.only]
+              "m2-ladder": measure_m2_ladder, "c5-solve": measure_c5_solve_cost}[args.only]
         print(json.dumps({args.only: fn(ctx, omen)}))
         return
     if args.lanczos_only:

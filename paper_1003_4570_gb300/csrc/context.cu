@@ -39,7 +39,8 @@ extern "C" void omen_destroy(omen_ctx* c) {
 
 extern "C" omen_status omen_set_reorthogonalization(omen_ctx* c, int policy) {
   if (!c) return OMEN_EINVAL;
-  if (policy != OMEN_REORTH_FULL && policy != OMEN_REORTH_SEMI) return set_err(c, OMEN_EINVAL, "unknown policy %d", policy);
+  if (policy != OMEN_REORTH_FULL && policy != OMEN_REORTH_SEMI && policy != OMEN_REORTH_PARTIAL)
+    return set_err(c, OMEN_EINVAL, "unknown policy %d", policy);
   c->reorth = policy;
   return OMEN_OK;
 }

@@ -691,6 +691,109 @@ __global__ void normalize_df_kernel(const float2* __restrict__ W, float2* __rest
   }
 }
 
+// Partial reorthogonalisation (Simon, Math. Comp. 42 (1984) 115; the estimate recurrence as in
+// Larsen's PROPACK): om holds estimates omega_i[k] of the overlaps v_i . v_k of the two newest
+// basis vectors (vector i in row i & 1 of om, ldT entries each; om[2 ldT] a running estimate of
+// ||A||).  With A v_k = sum_l T[l, k] v_l for every earlier basis vector (the columns of the
+// projected matrix, thick-restart arrowhead included), the new vector
+// beta' v_{j+1} = A v_j - alpha_j v_j - beta_j v_{j-1} has
+//   beta' omega_{j+1}[k] = sum_l T[l, k] omega_j[l] - alpha_j omega_j[k] - beta_j omega_{j-1}[k]
+// plus a rounding term eps1 ||A|| (added with the sign of the estimate).  The overlaps with v_j
+// and v_{j-1} are removed exactly by the three-term step.  When the largest estimate exceeds
+// delta (the square root of the unit roundoff) the full Gram–Schmidt pass runs for this vector
+// and the next one, and the estimates restart at eps1.  gate[0]: this step's pass; gate[1]: the
+// pass of the next step is forced.
+template <bool C>
+__global__ void omega_kernel(const double2* __restrict__ T, int ldT, int j, const double2* __restrict__ nrm2,
+                             double* __restrict__ om, int* __restrict__ gate, double eps1, double delta) {
+  // estimates are complex for complex vectors: omega_i[k] = v_k^H v_i, and v_k^H A v_j =
+  // sum_l conj(T[l, k]) omega_j[l] since A is Hermitian
+  constexpr int S = C ? 2 : 1;                          // doubles per estimate
+  double* wj = om + (size_t)(j & 1) * S * ldT;          // omega_j
+  double* wn = om + (size_t)((j + 1) & 1) * S * ldT;    // omega_{j-1} in, omega_{j+1} out
+  const double bn = sqrt(fmax(nrm2->x, 0.0));
+  const double aj = T[j + (size_t)j * ldT].x;
+  const double bj = j > 0 ? T[j + (size_t)(j - 1) * ldT].x : 0.0;
+  __shared__ double red[32];
+  __shared__ int run_s;
+  const double anorm = fmax(om[2 * S * ldT], fabs(aj) + fabs(bj) + bn);
+  const double ib = 1.0 / fmax(bn, 1e-300);
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < j - 1; k += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int l = 0; l <= j; ++l) {
+      const double2 t = T[l + (size_t)k * ldT];
+      if constexpr (C) {
+        const double wr = wj[2 * l], wi = wj[2 * l + 1];
+        sr += t.x * wr + t.y * wi;          // conj(t) * w
+        si += t.x * wi - t.y * wr;
+      } else {
+        sr += t.x * wj[l];
+      }
+    }
+    if constexpr (C) {
+      double vr = sr - aj * wj[2 * k] - bj * wn[2 * k];
+      double vi = si - aj * wj[2 * k + 1] - bj * wn[2 * k + 1];
+      const double a = hypot(vr, vi);
+      const double g = a > 0.0 ? (a + eps1 * anorm) / a : 0.0;
+      vr = a > 0.0 ? vr * g : eps1 * anorm;
+      vi = a > 0.0 ? vi * g : 0.0;
+      wn[2 * k] = vr * ib;
+      wn[2 * k + 1] = vi * ib;
+      mx = fmax(mx, hypot(vr, vi) * ib);
+    } else {
+      double v = sr - aj * wj[k] - bj * wn[k];
+      v = (v + copysign(eps1 * anorm, v)) * ib;
+      wn[k] = v;
+      mx = fmax(mx, fabs(v));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    const int forced = gate[1];
+    const int run = (m > delta || !(m == m) || forced) ? 1 : 0;
+    gate[0] = run;
+    gate[1] = (run && !forced) ? 1 : 0;
+    run_s = run;
+    om[2 * S * ldT] = anorm;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k <= j; k += blockDim.x)
+    if (run_s || k >= j - 1) {
+      wn[S * k] = eps1;
+      if (C) wn[S * k + 1] = 0.0;
+    }
+  if (threadIdx.x == 0) {
+    wn[S * (j + 1)] = 1.0;
+    if (C) wn[S * (j + 1) + 1] = 0.0;
+  }
+}
+
+// After full passes: vectors i1 - 1 and i1 orthogonal to all earlier ones (estimates eps1), and
+// the next step's pass forced (a restart's kept vectors are only semi-orthogonal among themselves).
+template <bool C>
+__global__ void omega_reset_kernel(double* __restrict__ om, int ldT, int i1, double eps1, int* __restrict__ gate) {
+  constexpr int S = C ? 2 : 1;
+  double* a = om + (size_t)(i1 & 1) * S * ldT;
+  double* b = om + (size_t)((i1 - 1) & 1) * S * ldT;
+  for (int k = threadIdx.x; k < ldT; k += blockDim.x) {
+    a[S * k] = (k == i1) ? 1.0 : eps1;
+    if (C) a[S * k + 1] = 0.0;
+    if (i1 >= 1) {
+      b[S * k] = (k == i1 - 1) ? 1.0 : eps1;
+      if (C) b[S * k + 1] = 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    gate[0] = 1;
+    gate[1] = 1;
+  }
+}
+
 // Device-side reduction of the partials into out (na x nb, column-major) and, optionally,
 // into columns col0.. of the projected matrix T (ldT x ldT, column-major).
 __global__ void reduce_dev_kernel(const double2* __restrict__ P, int nchunks, int na, int nb, double2* __restrict__ out,
@@ -1279,6 +1382,32 @@ struct KrylovOps {
     OMEN_CHECK_LAUNCH(ctx);
     return OMEN_OK;
   }
+  // Partial reorthogonalisation: the full pass h = V^H w (added into T column js), w -= V h for
+  // one real vector, every kernel skipped unless gate[0] (set by omega_kernel) is nonzero.
+  omen_status pass_gated(const void* Vb, int na, void* W, double2* h_dev, double2* Tm, int ldT, int js, const int* gate) {
+    const int ig1 = dots_ig_for(na, dots1_ig(cplx));
+    const int rows = (int)dot_rows(na, ig1);
+    const long long nchunks = (n + rows - 1) / rows;
+    omen_status s1 = ensure_partial((size_t)nchunks * na);
+    if (s1 != OMEN_OK) return s1;
+    dim3 grid((na + ig1 - 1) / ig1, (unsigned)nchunks);
+    const size_t shm1 = (size_t)na * sizeof(double2);
+    const unsigned grid1 = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+#define PASSG(Tt, Cc)                                                                                            \
+  do {                                                                                                           \
+    launch_dots1<Tt, Cc>(ig1, grid, ctx->stream, Vb, n, na, W, n, rows, d_partial, 0, 0, 0, nullptr, nullptr, gate); \
+    reduce_dev_kernel<<<na, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, 1, h_dev, Tm, ldT, js, 0, 0, 0, gate); \
+    smem_limit(combine1_kernel<Tt, Cc>, shm1);                                                                   \
+    combine1_kernel<Tt, Cc><<<grid1, 256, shm1, ctx->stream>>>(Vb, n, na, h_dev, W, n, -1.0, 1.0, 0, 0, 0, nullptr, \
+                                                              nullptr, gate);                                   \
+  } while (0)
+    if (prec == OMEN_F64) { if (cplx) PASSG(double, true); else PASSG(double, false); }
+    else { if (cplx) PASSG(float, true); else PASSG(float, false); }
+#undef PASSG
+    OMEN_CHECK_LAUNCH(ctx);
+    return OMEN_OK;
+  }
+
   // the next gated pass (parity) is applied unconditionally (after a restart's full passes)
   omen_status force_next_pass(int parity) {
     OMEN_CUDA(ctx, cudaMemsetAsync(ctx->d_status + 2 + (parity ^ 1), 1, sizeof(int), ctx->stream));
@@ -1960,6 +2089,24 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   // One step on the device: W = A v_js, orthogonalise W against v_0..v_{nb-1} (T column js),
   // v_nb = W / ||W|| (T[nb, js] = ||W||).  No host synchronisation.
   const bool semi = ctx->reorth == OMEN_REORTH_SEMI && op.prec != OMEN_F64_DF;
+  // partial reorthogonalisation by overlap estimates (real FP64 / FP32 vectors)
+  // (FP64 vectors only: in FP32 a basis run past its rounding floor, as the FP32 phase of a
+  // refined solve is, loses orthogonality faster than the estimates follow)
+  const bool pro = ctx->reorth == OMEN_REORTH_PARTIAL && op.prec == OMEN_F64;
+  const double unit = op.prec == OMEN_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+  const double eps1 = 0.5 * unit * std::sqrt((double)op.n);
+  const double delta = std::sqrt(unit);
+  int* pgate = ctx->d_status + 6;
+  DevBuf Om;
+  if (pro) {
+    const size_t omb = sizeof(double) * (4 * (size_t)ldT + 1);   // complex estimates, two vectors
+    if (cudaMalloc(&Om.p, omb) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(ctx, OMEN_ENOMEM, "overlap estimates");
+    }
+    OMEN_CUDA(ctx, cudaMemsetAsync(Om.p, 0, omb, ctx->stream));
+  }
+  double* om = static_cast<double*>(Om.p);
   auto enqueue_step = [&](int js, int nb, bool fr) -> omen_status {
     long long unused = 0;
     omen_status s2 = op.apply(op.col(V, js), W, tmp, 1, folded, o->sigma, unused);
@@ -1971,6 +2118,25 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
         if (s2 == OMEN_OK) s2 = op.combine_dev(V, nb, dh, 1, W, -1.0, 1.0);
       }
       if (s2 == OMEN_OK && semi) s2 = op.force_next_pass((js + 1) & 1);
+      if (s2 == OMEN_OK && pro) {
+        if (op.cplx) omega_reset_kernel<true><<<1, 256, 0, ctx->stream>>>(om, ldT, nb, eps1, pgate);
+        else omega_reset_kernel<false><<<1, 256, 0, ctx->stream>>>(om, ldT, nb, eps1, pgate);
+        OMEN_CHECK_LAUNCH(ctx);
+      }
+    } else if (pro) {
+      // three-term step, then the full pass only when the overlap estimates call for it
+      s2 = op.dots_dev(op.col(V, js), 1, W, 1, dh, dT + js, ldT, js);
+      if (s2 == OMEN_OK) s2 = op.combine_dev(op.col(V, js), 1, dh, 1, W, -1.0, 1.0);
+      if (s2 == OMEN_OK) s2 = op.combine_dev(op.col(V, js - 1), 1, dT + js + (size_t)(js - 1) * ldT, 1, W, -1.0, 1.0);
+      if (s2 != OMEN_OK) return s2;
+      OMEN_CUDA(ctx, cudaMemcpyAsync(dT + (js - 1) + (size_t)js * ldT, dT + js + (size_t)(js - 1) * ldT,
+                                     sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+      s2 = op.dots_dev(W, 1, W, 1, dn, nullptr, 0, 0);
+      if (s2 != OMEN_OK) return s2;
+      if (op.cplx) omega_kernel<true><<<1, 256, 0, ctx->stream>>>(dT, ldT, js, dn, om, pgate, eps1, delta);
+      else omega_kernel<false><<<1, 256, 0, ctx->stream>>>(dT, ldT, js, dn, om, pgate, eps1, delta);
+      OMEN_CHECK_LAUNCH(ctx);
+      s2 = op.pass_gated(V, nb, W, dh, dT, ldT, js, pgate);
     } else {
       // three-term step against v_j (alpha) and v_{j-1} (beta, already in T), then one full
       // pass that removes what rounding left along every basis vector (under the

@@ -224,3 +224,61 @@ def test_folded_nearest_finds_every_copy_of_a_degenerate_level(ctx):
                                   basis=48, max_iter=60000)
     assert info["converged"] == 1, info
     np.testing.assert_allclose(ev, ref, atol=1e-9, rtol=0)
+
+
+def test_folded_nearest_sigma_set_5cubed_alloy(ctx):
+    """The 16 eigenvalues nearest a mid-spectrum shift of the 1M-atom recipe at 5^3 cells (1,000
+    atoms, 10,000 rows, hard walls, 2% strain, sp3d5s*): the folded-spectrum solve returns the
+    same set as a dense solve, each value within 1e-9 eV.  The shift follows the recipe (centre
+    of the spectrum plus the seeded offset, rounded to 1 meV)."""
+    from paper_1003_4570_gb300 import omen
+    spec, p = synth.config_sige_alloy(5, seed=2)
+    H = hamiltonian.assemble(spec, p)
+    w = np.linalg.eigvalsh(H.toarray())
+    sigma = round(0.5 * (w[0] + w[-1]) + synth.sigma_offset_fraction(2) * (w[-1] - w[0]), 3)
+    d = np.sort(np.abs(w - sigma))
+    assert d[16] - d[15] > 1e-6                 # the set of 16 is unique at this tolerance
+    ref = eigs.nearest(w, sigma, 16)
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p)
+    ev, info, _ = omen.omen_eigs(ctx, ham, 16, which=omen.OMEN_NEAREST, sigma=sigma, tol=1e-9, block=1, basis=64,
+                                 max_iter=400000)
+    assert info["converged"] == 1, info
+    np.testing.assert_allclose(np.sort(ev), ref, atol=1e-9, rtol=0)
+
+
+@pytest.mark.parametrize("which,prec,bloch", [("lowest", 0, False), ("nearest", 0, False), ("nearest", 0, True),
+                                              ("lowest", 0, True), ("nearest", 2, False)])
+def test_partial_reorthogonalization_matches_full_and_dense(ctx, which, prec, bloch):
+    """Skipping the Gram–Schmidt pass while the estimated overlaps stay below the square root of
+    the unit roundoff keeps the eigenvalues at the dense solution's (FP64 real and complex: 1e-9
+    eV), through several thick restarts; a refined FP32 solve (which keeps its full passes) is
+    unaffected (1e-8 eV)."""
+    from paper_1003_4570_gb300 import omen
+    spec = synth.lattice_spec(2, 3, 3, (2, 2, 1) if bloch else (0, 0, 1), seed=47, alloy_fraction=0.3,
+                              strain_amp=0.02)
+    p = synth.draw_tb_params(47, 10, 2)
+    kv = (0.4, -0.7, 0.0) if bloch else None
+    H = hamiltonian.assemble(spec, p, kvec=kv)
+    w = np.linalg.eigvalsh(H.toarray())
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=prec, k=kv)
+    tol = {0: 1e-9, 1: 1e-5, 2: 1e-8}[prec]
+    kw = dict(tol=0.5 * tol if prec == 1 else tol, block=1, basis=40, max_iter=40000)
+    if which == "nearest":
+        sigma = round(0.5 * (w[0] + w[-1]) + 0.2, 3)
+        kw.update(which=omen.OMEN_NEAREST, sigma=sigma)
+        ref = eigs.nearest(w, sigma, 6)
+    else:
+        ref = w[:6]
+    res = {}
+    try:
+        for pol in (omen.OMEN_REORTH_FULL, omen.OMEN_REORTH_PARTIAL):
+            omen.omen_set_reorthogonalization(ctx, pol)
+            res[pol] = omen.omen_eigs(ctx, ham, 6, **kw)
+    finally:
+        omen.omen_set_reorthogonalization(ctx, omen.OMEN_REORTH_FULL)
+    for pol, (ev, info, st) in res.items():
+        assert info["converged"] == 1, (pol, info)
+        np.testing.assert_allclose(np.sort(ev), ref, atol=tol, rtol=0)
+    assert res[omen.OMEN_REORTH_PARTIAL][1]["restarts"] >= 1
