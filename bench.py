@@ -37,9 +37,13 @@ SAMPLE_NZ = 4          # CPU sample: 50 x 50 x 4 cells of the same recipe
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 figure is in the measured-peaks file)
 
 
-# DRAM bytes per FP64 H·X launch on the 1M-atom alloy, by launch shape (CTA width, block rows
-# per register batch), from the ncu launch lists summarised in profiles/hx_kernel_sige_alloy.md
-HX_F64_TRAFFIC = {(128, 1): 2.547e9, (64, 2): 1.920e9, (32, 2): 1.915e9}
+# DRAM bytes (read + write) per bond of one FP64 stored H·X launch, by launch shape (CTA width,
+# block rows per register batch): ncu capture of every shape on the 30^3-cell case of the alloy
+# recipe (profiles/hx_kernel_f64_shapes_sige_alloy.md), scaled to a launch by its bonds
+HX_F64_TRAFFIC_PER_BOND = {(32, 1): 1203.0, (32, 2): 922.4, (64, 1): 1190.2, (64, 2): 917.9, (96, 1): 1160.4,
+                           (96, 2): 924.9, (128, 1): 1151.1, (128, 2): 917.2}
+HX_F64_TRAFFIC_SOURCE = ("profiles/hx_kernel_f64_shapes_sige_alloy.md: ncu dram__bytes of each launch shape "
+                         "at 30^3 cells, per bond x this launch's bonds")
 
 
 def measured_peaks():
@@ -271,6 +275,8 @@ def measure_eigs_1m(ctx, omen, lat, p, nev=16, only=None):
     import torch
     out = {}
     variants = [("f64", False, omen.OMEN_F64, 1e-9), ("f64_double_float", False, omen.OMEN_F64_DF, 1e-9),
+                ("f64_partial_reorth", False, omen.OMEN_F64, 1e-9),
+                ("f64_double_float_partial_reorth", False, omen.OMEN_F64_DF, 1e-9),
                 ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)]
     if only == "so-all":
         # the spin-orbit precision comparison: raw complex64, complex64 + FP64 refinement, and
@@ -282,11 +288,14 @@ def measure_eigs_1m(ctx, omen, lat, p, nev=16, only=None):
         if only and only != "so-all" and name != only:
             continue
         ham = omen.omen_assemble_H(ctx, lat, p, spin_orbit=so, precision=prec)
+        if name.endswith("partial_reorth"):
+            omen.omen_set_reorthogonalization(ctx, omen.OMEN_REORTH_PARTIAL)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev, info, st = omen.omen_eigs(ctx, ham, nev, omen.OMEN_LOWEST, tol=tol, block=1 if not so else 2,
                                       basis=96, max_iter=6000, raise_on_noconv=False)
         torch.cuda.synchronize()
+        omen.omen_set_reorthogonalization(ctx, omen.OMEN_REORTH_FULL)
         out[name] = {"seconds": time.perf_counter() - t0, "converged": info["converged"], "tol_eV": tol,
                      "iterations": info["iterations"], "hx_count": info["hx_count"],
                      "max_error_bound": info["max_error_bound"], "max_residual_raw": info["max_residual_raw"],
@@ -824,12 +833,14 @@ def run_gpu(args, rank, world, local_rank):
     if prec == omen.OMEN_F64:
         fl = flops_per_hx(nbonds, natoms)
         achieved_tf = fl / (launch_ms / 1e3) / 1e12
-        # DRAM bytes per launch of this kernel at this workload, from the ncu launch list in
-        # profiles/hx_kernel_sige_alloy.md (null for other workloads)
+        # DRAM bytes per launch of this kernel for the chosen shape: per-bond traffic from the
+        # committed ncu capture of every shape, times this launch's bonds (not measured in this run)
         shape = (tile["threads"], tile["rows_per_batch"] or 1) if tile else None
-        traffic = HX_F64_TRAFFIC.get(shape) if (args.cells == N_CELLS and not args.matrix_free) else None
+        per_bond = HX_F64_TRAFFIC_PER_BOND.get(shape) if not args.matrix_free else None
+        traffic = per_bond * nbonds if per_bond else None
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_source": HX_F64_TRAFFIC_SOURCE if traffic else None,
                 "kernel": "hx_kernel<double,10,real,stored>", "hbm_achieved_gbs": achieved_gbs,
                 "hbm_frac_of_measured": achieved_gbs / hbm, "peak_source": "recipe nominal FP64"}
     else:

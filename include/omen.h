@@ -96,9 +96,9 @@ omen_status omen_set_graph_capture(omen_ctx* ctx, int enable);
  * solver, Section III-A item 1, does not say how it orthogonalises).  It saves the update only
  * while no Ritz pair has converged; it costs one extra norm per step.  The first step after a
  * start or restart always takes two full passes.  OMEN_REORTH_PARTIAL (FP64 vectors, real or
- * complex; FP32 and double-float vectors keep the full pass: an FP32 basis driven past its
- * rounding floor loses orthogonality faster than the estimates follow) skips the projection as
- * well: it estimates the overlaps
+ * complex, and double-float vectors; FP32 vectors keep the full pass: an FP32 basis driven past
+ * its rounding floor loses orthogonality faster than the estimates follow) skips the projection
+ * as well: it estimates the overlaps
  * of each new vector with the basis from the projected matrix by Simon's recurrence
  * (omega_{j+1} from omega_j, omega_{j-1}, the columns of T and a rounding term; the estimate
  * recurrence as in Larsen's PROPACK) and runs the full pass, for that vector and the next, only
@@ -607,6 +607,14 @@ omen_status omen_mlp_targets(omen_ctx* ctx, const omen_mlp* mlp, const omen_grid
  * (0 V on the grounded planes), the same on every lateral point: phi_dev [(nz-1)*ny*nx]. */
 omen_status omen_mlp_warm_start(omen_ctx* ctx, omen_mlp* mlp, const omen_grid* grid, const double* donor_rho_dev,
                                 double* phi_dev);
+
+/* omen_scf from the network's start (omen_mlp_warm_start on d->donor_rho_dev), with the
+ * zero-field start as the fallback: if that loop returns ENOCONV or ENUMERIC, phi_dev is reset to
+ * zero and omen_scf runs again.  *fallback (may be NULL) = 1 when the result comes from the
+ * zero-field run; info then counts both runs' time and products, and its iterations those of the
+ * zero-field run.  d->donor_rho_dev is required. */
+omen_status omen_scf_learned(omen_ctx* ctx, const omen_scf_desc* d, omen_mlp* mlp, double* phi_dev,
+                             omen_scf_info* info, int* fallback);
 
 #ifdef __cplusplus
 }

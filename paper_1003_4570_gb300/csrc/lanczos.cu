@@ -590,7 +590,9 @@ __global__ void dots_cols_df_kernel(const float2* __restrict__ A, const float2* 
 template <int NB, int IG>
 __global__ void __launch_bounds__(256) dots_df_kernel(const float2* __restrict__ A, long long lda, int na,
                                                       const float2* __restrict__ B, long long ldb, int nb, long long n,
-                                                      int rows_per_cta, double2* __restrict__ P) {
+                                                      int rows_per_cta, double2* __restrict__ P,
+                                                      const int* __restrict__ gate = nullptr) {
+  if (gate && !*gate) return;   // a pass the overlap estimates skip
   const int i0 = blockIdx.x * IG;
   const int ni = min(IG, na - i0);
   const long long r0 = (long long)blockIdx.y * rows_per_cta;
@@ -637,7 +639,9 @@ __global__ void __launch_bounds__(256) dots_df_kernel(const float2* __restrict__
 template <int NB>
 __global__ void __launch_bounds__(256) combine_df_kernel(const float2* __restrict__ A, long long lda, int na,
                                                          const double2* __restrict__ M, int nb, float2* __restrict__ Y,
-                                                         long long ldy, long long n, double alpha, double beta) {
+                                                         long long ldy, long long n, double alpha, double beta,
+                                                         const int* __restrict__ gate = nullptr) {
+  if (gate && !*gate) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* Ms = reinterpret_cast<float2*>(smem_raw);
   for (int t = threadIdx.x; t < na * nb; t += blockDim.x) Ms[t] = df_from_double(alpha * M[t].x);
@@ -1385,6 +1389,27 @@ struct KrylovOps {
   // Partial reorthogonalisation: the full pass h = V^H w (added into T column js), w -= V h for
   // one real vector, every kernel skipped unless gate[0] (set by omega_kernel) is nonzero.
   omen_status pass_gated(const void* Vb, int na, void* W, double2* h_dev, double2* Tm, int ldT, int js, const int* gate) {
+    if (prec == OMEN_F64_DF) {
+      const int ig = dots_ig_for(na, 16);
+      const int rows = (int)dot_rows(na, ig);
+      const long long nchunks = (n + rows - 1) / rows;
+      omen_status s1 = ensure_partial((size_t)nchunks * na);
+      if (s1 != OMEN_OK) return s1;
+      dim3 grid((na + ig - 1) / ig, (unsigned)nchunks);
+      const float2* Af = static_cast<const float2*>(Vb);
+      const float2* Bf = static_cast<const float2*>(W);
+#define DDFG(IGc) dots_df_kernel<1, IGc><<<grid, 256, 0, ctx->stream>>>(Af, n, na, Bf, n, 1, n, rows, d_partial, gate)
+      if (ig == 1) DDFG(1); else if (ig == 2) DDFG(2); else if (ig == 4) DDFG(4); else if (ig == 8) DDFG(8); else DDFG(16);
+#undef DDFG
+      reduce_dev_kernel<<<na, 256, 0, ctx->stream>>>(d_partial, (int)nchunks, na, 1, h_dev, Tm, ldT, js, 0, 0, 0, gate);
+      const unsigned gridc = (unsigned)std::min<long long>((n + 255) / 256, (long long)sm_count * 8);
+      const size_t shm = (size_t)na * sizeof(float2);
+      smem_limit(combine_df_kernel<1>, shm);
+      combine_df_kernel<1><<<gridc, 256, shm, ctx->stream>>>(Af, n, na, h_dev, 1, static_cast<float2*>(W), n, n, -1.0, 1.0,
+                                                            gate);
+      OMEN_CHECK_LAUNCH(ctx);
+      return OMEN_OK;
+    }
     const int ig1 = dots_ig_for(na, dots1_ig(cplx));
     const int rows = (int)dot_rows(na, ig1);
     const long long nchunks = (n + rows - 1) / rows;
@@ -2090,10 +2115,11 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   // v_nb = W / ||W|| (T[nb, js] = ||W||).  No host synchronisation.
   const bool semi = ctx->reorth == OMEN_REORTH_SEMI && op.prec != OMEN_F64_DF;
   // partial reorthogonalisation by overlap estimates (real FP64 / FP32 vectors)
-  // (FP64 vectors only: in FP32 a basis run past its rounding floor, as the FP32 phase of a
-  // refined solve is, loses orthogonality faster than the estimates follow)
-  const bool pro = ctx->reorth == OMEN_REORTH_PARTIAL && op.prec == OMEN_F64;
-  const double unit = op.prec == OMEN_F64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+  // (FP64 and double-float vectors only: in FP32 a basis run past its rounding floor, as the FP32
+  // phase of a refined solve is, loses orthogonality faster than the estimates follow)
+  const bool pro = ctx->reorth == OMEN_REORTH_PARTIAL && (op.prec == OMEN_F64 || op.prec == OMEN_F64_DF);
+  // unit roundoff: FP64 2^-53; double-float pairs carry about 48 bits, taken as 2^-46
+  const double unit = op.prec == OMEN_F64 ? 1.1102230246251565e-16 : 1.4210854715202004e-14;
   const double eps1 = 0.5 * unit * std::sqrt((double)op.n);
   const double delta = std::sqrt(unit);
   int* pgate = ctx->d_status + 6;
@@ -2505,11 +2531,14 @@ extern "C" omen_status omen_eigs(omen_ctx* ctx, const omen_ham* ham, const omen_
   if (s == OMEN_OK) s = rayleigh_residuals(op, Xb.p, HXb.p, Rb.p, kout, rr.lam, rr.res);
   if (s != OMEN_OK) { op.release(); return s; }
   inf->hx_count += kout;
-  // the nev wanted among the kout: lowest, or nearest sigma (Ritz vectors are ordered by
-  // theta of A, which for the folded operator is (lambda - sigma)^2)
+  // the nev wanted among the kout: lowest, or nearest sigma.  For the folded operator the key is
+  // the square root of its Rayleigh quotient, ||(H - sigma) x||^2 = r^2 + (lambda - sigma)^2 (r the
+  // H residual, orthogonal to x): an unconverged extra vector that mixes levels on both sides of
+  // sigma has lambda near sigma but a large r, and must not displace a converged pair.
   std::vector<double> key(kout);
   for (int i = 0; i < kout; ++i)
-    key[i] = (o->which == OMEN_NEAREST) ? std::fabs(rr.lam[i] - o->sigma) : (o->which == OMEN_HIGHEST ? -rr.lam[i] : rr.lam[i]);
+    key[i] = (o->which == OMEN_NEAREST) ? std::hypot(rr.lam[i] - o->sigma, rr.res[i])
+                                        : (o->which == OMEN_HIGHEST ? -rr.lam[i] : rr.lam[i]);
   s = sort_columns(op, Xb.p, kout, key, &rr.lam, &rr.res);
   if (s != OMEN_OK) { op.release(); return s; }
   error_bounds(rr.lam, rr.lam, rr.res, rr.bound);

@@ -466,3 +466,32 @@ extern "C" omen_status omen_mlp_warm_start(omen_ctx* ctx, omen_mlp* m, const ome
   if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "warm start: %s", cudaGetErrorString(e));
   return OMEN_OK;
 }
+
+// The learned start with the zero-field start as fallback and judge: the network's potential
+// starts omen_scf; if that loop fails (iteration limit, or a start so far off that the states it
+// produces cannot hold the electrons), phi is reset to zero field and the loop runs again from
+// there.  info covers the run that produced phi; *fallback tells which start that was.
+extern "C" omen_status omen_scf_learned(omen_ctx* ctx, const omen_scf_desc* d, omen_mlp* m, double* phi,
+                                        omen_scf_info* info, int* fallback) {
+  if (!ctx || !d || !m || !phi || !d->grid || !d->donor_rho_dev) return set_err(ctx, OMEN_EINVAL, "null argument");
+  if (fallback) *fallback = 0;
+  omen_status s = omen_mlp_warm_start(ctx, m, d->grid, d->donor_rho_dev, phi);
+  if (s != OMEN_OK) return s;
+  omen_scf_info first{};
+  s = omen_scf(ctx, d, phi, &first);
+  if (s == OMEN_OK || (s != OMEN_ENOCONV && s != OMEN_ENUMERIC)) {
+    if (info) *info = first;
+    return s;
+  }
+  const long long ng = (long long)d->grid->nx * d->grid->ny * (d->grid->nz - 1);
+  OMEN_CUDA(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * ng, ctx->stream));
+  if (fallback) *fallback = 1;
+  omen_scf_info second{};
+  s = omen_scf(ctx, d, phi, &second);
+  second.seconds += first.seconds;          // the failed learned run is part of the cost
+  second.eig_seconds += first.eig_seconds;
+  second.poisson_seconds += first.poisson_seconds;
+  second.hx_count += first.hx_count;
+  if (info) *info = second;
+  return s;
+}

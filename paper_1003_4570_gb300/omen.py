@@ -192,6 +192,7 @@ def lib():
             "omen_gather": (i, [vp, vp, C.POINTER(Grid), vp, vp]),
             "omen_fermi_level": (i, [vp, vp, i, d, d, C.POINTER(d)]),
             "omen_scf": (i, [vp, C.POINTER(SCFDesc), vp, C.POINTER(SCFInfo)]),
+            "omen_scf_learned": (i, [vp, C.POINTER(SCFDesc), vp, vp, C.POINTER(SCFInfo), C.POINTER(i)]),
             "omen_poisson_newton": (i, [vp, vp, C.POINTER(Grid), C.POINTER(FrozenStates), vp, vp, C.POINTER(NewtonOpts),
                                         C.POINTER(NewtonInfo)]),
             "omen_state_weights": (i, [vp, vp, vp, i, vp, vp]),
@@ -579,6 +580,37 @@ def omen_poisson_newton(ctx: Context, lat: Lattice, grid, E, W_dev, E_F, kT, phi
     if s != OMEN_OK and not (s == OMEN_ENOCONV and not raise_on_noconv):
         ctx.check(s)
     return info.as_dict(), s
+
+
+def _scf_desc(lat, params, grid, donor_rho_dev, n_electrons, kT, kpts, kweights, nev, sigma, e_cut, precision,
+              eig_tol, eig_block, eig_basis, eig_max_iter, mix, tol_V, max_iter, cg_rtol, cg_max_iter, mix_history,
+              poisson_newton):
+    tp = tb_params_struct(params)
+    g = grid_struct(grid)
+    k = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 3)
+    kw = np.ascontiguousarray(kweights, dtype=np.float64)
+    if eig_basis is None:
+        eig_basis = max(4 * eig_block, ((2 * nev + 2 * eig_block + eig_block - 1) // eig_block) * eig_block)
+    d = SCFDesc(lat.handle, C.addressof(tp), int(precision), C.addressof(g), _ptr(donor_rho_dev), float(n_electrons),
+                float(kT), len(kw), k.ctypes.data, kw.ctypes.data, int(nev), float(sigma), float(e_cut), float(eig_tol),
+                int(eig_block), int(eig_basis), int(eig_max_iter), float(mix), int(mix_history), float(tol_V),
+                int(max_iter), CGOpts(float(cg_rtol), int(cg_max_iter)), int(bool(poisson_newton)))
+    return d, (tp, g, k, kw)
+
+
+def omen_scf_learned(ctx: Context, mlp, lat: Lattice, params, grid, phi_dev, donor_rho_dev, n_electrons, kT, kpts,
+                     kweights, nev, sigma, e_cut, precision=OMEN_F64, eig_tol=1e-9, eig_block=1, eig_basis=None,
+                     eig_max_iter=20000, mix=0.1, tol_V=1e-6, max_iter=300, cg_rtol=1e-13, cg_max_iter=100000,
+                     mix_history=0, poisson_newton=False):
+    """omen_scf from the network's start, falling back to zero field.  Returns (info, status, fallback)."""
+    d, keep = _scf_desc(lat, params, grid, donor_rho_dev, n_electrons, kT, kpts, kweights, nev, sigma, e_cut,
+                        precision, eig_tol, eig_block, eig_basis, eig_max_iter, mix, tol_V, max_iter, cg_rtol,
+                        cg_max_iter, mix_history, poisson_newton)
+    info = SCFInfo()
+    fb = C.c_int()
+    s = lib().omen_scf_learned(ctx.handle, C.byref(d), mlp.handle, _ptr(phi_dev), C.byref(info), C.byref(fb))
+    ctx.check(s)
+    return info.as_dict(), s, bool(fb.value)
 
 
 def omen_tune_hx(ctx: Context, ham: Hamiltonian, vec_precision=None, nvec=1, reps=10) -> dict:
