@@ -275,8 +275,6 @@ def measure_eigs_1m(ctx, omen, lat, p, nev=16, only=None):
     import torch
     out = {}
     variants = [("f64", False, omen.OMEN_F64, 1e-9), ("f64_double_float", False, omen.OMEN_F64_DF, 1e-9),
-                ("f64_partial_reorth", False, omen.OMEN_F64, 1e-9),
-                ("f64_double_float_partial_reorth", False, omen.OMEN_F64_DF, 1e-9),
                 ("so_f32_refine64", True, omen.OMEN_F32_REFINE64, 1e-8)]
     if only == "so-all":
         # the spin-orbit precision comparison: raw complex64, complex64 + FP64 refinement, and
@@ -590,6 +588,28 @@ def launch_hx_shapes(ctx, omen, cells):
     return {"cells": cells, "bonds": lat.counts()[1], "shapes_in_launch_order": shapes}
 
 
+def measure_vff(ctx, omen, cells=N_CELLS, gtol=1e-8):
+    """Valence-force-field relaxation of the alloy recipe (Keating, seeded constants, Si and Ge
+    lattice constants, the box at the Si constant, hard walls): conjugate-gradient iterations,
+    time, energy and largest force left."""
+    import torch
+    spec, _ = synth.config_sige_alloy(cells, seed=2)
+    vp = synth.draw_vff_params(2)
+    lat = omen.omen_build_lattice(ctx, spec)
+    u = torch.zeros((3, spec.natoms), dtype=torch.float64, device="cuda")
+    st = torch.empty(16 * spec.ncells, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info, status = omen.omen_relax_vff(ctx, lat, vp, u, gtol=gtol, max_iter=50000, strain_dev=st, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s_np = st.cpu().numpy()
+    return {"atoms": spec.natoms, "gtol_eV_per_nm": gtol, "seconds": dt, "iterations": info["iterations"],
+            "converged": info["converged"], "energy_start_eV": info["energy_start"], "energy_eV": info["energy"],
+            "max_force_eV_per_nm": info["max_force"], "ms_per_iteration": 1e3 * dt / max(1, info["iterations"]),
+            "bond_strain_range": [float(s_np[s_np != 0].min()), float(s_np[s_np != 0].max())]}
+
+
 def measure_c5_solve_cost(ctx, omen, nev=32, seed=5):
     """One zero-field eigen-solve of the 4x4x80-cell delta layer (10,240 atoms, 102,400 complex
     rows) at one wave vector of the 4x4 mesh: the 32 states nearest sigma = E_c - 0.4 E_g by
@@ -620,7 +640,7 @@ def measure_c5_solve_cost(ctx, omen, nev=32, seed=5):
     return out
 
 
-def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
+def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400, nev=8):
     """SCF iterations and wall time from the zero-field start and from the learned start.
 
     The network is trained here on self-consistent potentials that omen_scf itself produces
@@ -633,9 +653,10 @@ def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
     grid = poisson.Grid(3, 3, round(nzc * a / 0.2), a, a, nzc * a)
     lat = omen.omen_build_lattice(ctx, spec)
     eg = synth.GAPPED_SI_EC - synth.GAPPED_SI_EV
-    common = dict(kT=8.617333262e-5 * 4, kpts=[(0.0, 0.0, 0.0)], kweights=[1.0], nev=8,
+    common = dict(kT=8.617333262e-5 * 4, kpts=[(0.0, 0.0, 0.0)], kweights=[1.0], nev=nev,
                   sigma=synth.GAPPED_SI_EC - 0.4 * eg, e_cut=0.5 * (synth.GAPPED_SI_EC + synth.GAPPED_SI_EV),
-                  eig_tol=1e-10, eig_block=1, eig_basis=48, mix=0.3, mix_history=6, tol_V=1e-6, max_iter=200)
+                  eig_tol=1e-10, eig_block=1, eig_basis=max(48, 3 * nev), mix=0.3, mix_history=6, tol_V=1e-6,
+                  max_iter=200)
 
     def solve(seed, phi):
         ns, w = synth.draw_doping(seed)
@@ -677,7 +698,7 @@ def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400):
         zi.append(info0["iterations"]); zt.append(s0)
         li.append(info1["iterations"]); lt.append(s1 + t_inf)
     return {"workload": f"delta-doped Si 1x1x{nzc} cells ({spec.natoms} atoms, {spec.natoms * 10} rows), Gamma, "
-                        f"grid {grid.nx}x{grid.ny}x{grid.nz}, Anderson mixing, tol 1e-6 V",
+                        f"grid {grid.nx}x{grid.ny}x{grid.nz}, {nev} states nearest sigma, Anderson mixing, tol 1e-6 V",
             "zero_field": {"iterations": zi, "seconds": zt, "mean_iterations": float(np.mean(zi))},
             "learned": {"iterations": li, "seconds": lt, "mean_iterations": float(np.mean(li)),
                         "includes": "network inference"},
@@ -876,6 +897,8 @@ def run_gpu(args, rank, world, local_rank):
         result["kbatch"] = measure_kbatch(ctx, omen)
         result["scf_learned_vs_zero"] = measure_scf(ctx, omen)
         result["effective_mass"] = measure_effmass(ctx, omen)
+        if args.cells == N_CELLS:
+            result["vff_relax_1M_atoms"] = measure_vff(ctx, omen)
     if rank == 0 and world == 1 and not args.no_cpu:
         t0 = time.perf_counter()
         cspec, H, cnb = cpu_sample()
@@ -907,12 +930,13 @@ def main():
                     "smaller only for profiling captures)")
     ap.add_argument("--scf-full", action="store_true",
                     help="one-off: warm-start network trained on 200 SCF solutions, 20 held-out profiles (minutes)")
-    ap.add_argument("--scf-study", default="", metavar="NZ,NTRAIN,NTEST",
-                    help="one-off: warm-start study on a 1x1xNZ-cell slab (NTRAIN training, NTEST held-out profiles)")
+    ap.add_argument("--scf-study", default="", metavar="NZ,NTRAIN,NTEST,NEV",
+                    help="one-off: warm-start study on a 1x1xNZ-cell slab (NTRAIN training, NTEST held-out profiles, "
+                         "NEV states per solve)")
     ap.add_argument("--kbatch-full", action="store_true",
                     help="one-off: the 8-instance x 128-k batching workload, batched vs per-k (minutes)")
     ap.add_argument("--only", default="", choices=["", "kbatch", "hx-kbatch", "scf", "small-si", "cube", "so-eigs",
-                                                   "so-all", "effmass", "m2-ladder", "c5-solve", "hx-shapes"],
+                                                   "so-all", "effmass", "m2-ladder", "c5-solve", "hx-shapes", "vff", "eigs-1m"],
                     help="profiling aid: run one side measurement alone and print its JSON")
     ap.add_argument("--tile", default="", metavar="THREADS,RB",
                     help="fix the H·X launch shape instead of tuning it (e.g. 64,2; profiling aid)")
@@ -935,9 +959,9 @@ def main():
         import torch
         from paper_1003_4570_gb300 import omen
         ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
-        nz, ntr, nte = (int(v) for v in args.scf_study.split(","))
+        nz, ntr, nte, nev = (int(v) for v in args.scf_study.split(","))
         print(json.dumps({"scf_study": measure_scf(ctx, omen, nzc=nz, n_train=ntr, n_test=nte,
-                                                   train_steps=max(400, 10 * ntr))}))
+                                                   train_steps=max(400, 10 * ntr), nev=nev)}))
         return
     if args.kbatch_full:
         import torch
@@ -949,6 +973,11 @@ def main():
         import torch
         from paper_1003_4570_gb300 import omen
         ctx = omen.omen_create(0, torch.cuda.current_stream().cuda_stream)
+        if args.only == "eigs-1m":
+            spec, p = synth.config_sige_alloy(args.cells, seed=2)
+            lat = omen.omen_build_lattice(ctx, spec)
+            print(json.dumps({args.only: measure_eigs_1m(ctx, omen, lat, p)}))
+            return
         if args.only in ("so-eigs", "so-all"):
             spec, p = synth.config_sige_alloy(args.cells, seed=2)
             lat = omen.omen_build_lattice(ctx, spec)
@@ -960,7 +989,7 @@ def main():
             return
         fn = {"kbatch": measure_kbatch, "hx-kbatch": measure_hx_kbatch, "scf": measure_scf,
               "small-si": measure_small_si, "cube": measure_cube_500, "effmass": measure_effmass,
-              "m2-ladder": measure_m2_ladder, "c5-solve": measure_c5_solve_cost}[args.only]
+              "m2-ladder": measure_m2_ladder, "c5-solve": measure_c5_solve_cost, "vff": measure_vff}[args.only]
         print(json.dumps({args.only: fn(ctx, omen)}))
         return
     if args.lanczos_only:

@@ -96,14 +96,15 @@ omen_status omen_set_graph_capture(omen_ctx* ctx, int enable);
  * solver, Section III-A item 1, does not say how it orthogonalises).  It saves the update only
  * while no Ritz pair has converged; it costs one extra norm per step.  The first step after a
  * start or restart always takes two full passes.  OMEN_REORTH_PARTIAL (FP64 vectors, real or
- * complex, and double-float vectors; FP32 vectors keep the full pass: an FP32 basis driven past
- * its rounding floor loses orthogonality faster than the estimates follow) skips the projection
- * as well: it estimates the overlaps
- * of each new vector with the basis from the projected matrix by Simon's recurrence
+ * complex; other vectors keep the full pass) skips the projection as well: it estimates the
+ * overlaps of each new vector with the basis from the projected matrix by Simon's recurrence
  * (omega_{j+1} from omega_j, omega_{j-1}, the columns of T and a rounding term; the estimate
  * recurrence as in Larsen's PROPACK) and runs the full pass, for that vector and the next, only
- * when an estimate exceeds the square root of the unit roundoff.  A step then reads the basis
- * only when a pass runs.  Every result is still checked by FP64 residuals.  EINVAL for another
+ * when an estimate exceeds the square root of the unit roundoff.  A step then reads the basis only
+ * when a pass runs.  The estimates do not follow the overlaps that the Ritz vectors kept at a
+ * thick restart carry from one cycle to the next: OMEN_LOWEST solves through many restarts can
+ * stall (ENOCONV; a stop is confirmed by FP64 residuals on H first), so the policy suits fixed
+ * step counts and folded solves.  Every result is checked by FP64 residuals.  EINVAL for another
  * value. */
 enum { OMEN_REORTH_FULL = 0, OMEN_REORTH_SEMI = 1, OMEN_REORTH_PARTIAL = 2 };
 omen_status omen_set_reorthogonalization(omen_ctx* ctx, int policy);

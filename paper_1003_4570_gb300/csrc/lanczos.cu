@@ -2115,13 +2115,13 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
   // v_nb = W / ||W|| (T[nb, js] = ||W||).  No host synchronisation.
   const bool semi = ctx->reorth == OMEN_REORTH_SEMI && op.prec != OMEN_F64_DF;
   // partial reorthogonalisation by overlap estimates (real FP64 / FP32 vectors)
-  // (FP64 and double-float vectors only: in FP32 a basis run past its rounding floor, as the FP32
-  // phase of a refined solve is, loses orthogonality faster than the estimates follow)
-  const bool pro = ctx->reorth == OMEN_REORTH_PARTIAL && (op.prec == OMEN_F64 || op.prec == OMEN_F64_DF);
-  // unit roundoff: FP64 2^-53; double-float pairs carry about 48 bits, taken as 2^-46
-  const double unit = op.prec == OMEN_F64 ? 1.1102230246251565e-16 : 1.4210854715202004e-14;
+  // (FP64 vectors only: an FP32 basis driven past its rounding floor, as the FP32 phase of a
+  // refined solve is, loses orthogonality faster than the estimates follow, and double-float
+  // bases drifted from the fully orthogonalised run's Ritz values)
+  const bool pro = ctx->reorth == OMEN_REORTH_PARTIAL && op.prec == OMEN_F64;
+  const double unit = 1.1102230246251565e-16;                      // 2^-53
   const double eps1 = 0.5 * unit * std::sqrt((double)op.n);
-  const double delta = std::sqrt(unit);
+  const double delta = std::sqrt(unit);                            // semi-orthogonality
   int* pgate = ctx->d_status + 6;
   DevBuf Om;
   if (pro) {
@@ -2251,10 +2251,42 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
       for (int i = 0; i < nbas; ++i) resA[i] = std::fabs(beta) * std::abs(Y[jstart + (size_t)i * nbas]);
       const int nev = o->nev;
       bool done = false;
+      // explicit check on H for the nev (+1) Ritz vectors of smallest theta: true FP64 residuals
+      auto explicit_check = [&](bool& ok) -> omen_status {
+        const int kc = std::min(nbas, nev + 1);
+        std::vector<cd> Yk((size_t)nbas * kc);
+        for (int j = 0; j < kc; ++j)
+          for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
+        omen_status s3 = op.combine(V, nbas, Yk, kc, Xb.p, 1.0, 0.0);
+        if (s3 != OMEN_OK) return s3;
+        if (!HXb.p && (cudaMalloc(&HXb.p, (size_t)(o->nev + 1) * vbytes) != cudaSuccess ||
+                       cudaMalloc(&Rb.p, (size_t)(o->nev + 1) * vbytes) != cudaSuccess)) {
+          cudaGetLastError();
+          return set_err(ctx, OMEN_ENOMEM, "Ritz check vectors");
+        }
+        s3 = launch_hx(ctx, op.ham, Xb.p, HXb.p, kc, 0.0, op.prec);
+        if (s3 != OMEN_OK) return s3;
+        hx += kc;
+        std::vector<double> lamk, resk, bd;
+        s3 = rayleigh_residuals(op, Xb.p, HXb.p, Rb.p, kc, lamk, resk);
+        if (s3 != OMEN_OK) return s3;
+        if (op.negate)
+          for (double& l : lamk) l = -l;
+        std::vector<double> lam(lamk.begin(), lamk.begin() + nev), res(resk.begin(), resk.begin() + nev);
+        error_bounds(lamk, lam, res, bd);
+        ok = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+        return OMEN_OK;
+      };
       if (!folded) {
         std::vector<double> lam(theta.begin(), theta.begin() + nev), res(resA.begin(), resA.begin() + nev), bd;
         error_bounds(theta, lam, res, bd);
         done = *std::max_element(bd.begin(), bd.end()) <= o->tol;
+        // under partial reorthogonalisation the projected matrix is only as good as the basis's
+        // orthogonality, which restarts erode: confirm on H before stopping
+        if (done && pro) {
+          s = explicit_check(done);
+          if (s != OMEN_OK) return s;
+        }
         // nothing of the operator below the line (Weyl): no lower eigenvalue left to find
         if (op.has_line && theta[0] - resA[0] > op.stop_line) {
           done = true;
@@ -2268,26 +2300,8 @@ static omen_status lanczos_solve_single(KrylovOps& op, const omen_eig_opts* o, v
         const double rmax = *std::max_element(resA.begin(), resA.begin() + nev);
         if (gateA < 0) gateA = std::max(o->tol, 1e-12) * 1e3;
         if (rmax <= gateA || iter >= max_iter_of(o)) {
-          const int kc = std::min(nbas, nev + 1);
-          std::vector<cd> Yk((size_t)nbas * kc);
-          for (int j = 0; j < kc; ++j)
-            for (int i = 0; i < nbas; ++i) Yk[i + (size_t)j * nbas] = Y[i + (size_t)j * nbas];
-          s = op.combine(V, nbas, Yk, kc, Xb.p, 1.0, 0.0);
+          s = explicit_check(done);
           if (s != OMEN_OK) return s;
-          if (!HXb.p && (cudaMalloc(&HXb.p, (size_t)(o->nev + 1) * vbytes) != cudaSuccess ||
-                         cudaMalloc(&Rb.p, (size_t)(o->nev + 1) * vbytes) != cudaSuccess)) {
-            cudaGetLastError();
-            return set_err(ctx, OMEN_ENOMEM, "Ritz check vectors");
-          }
-          s = launch_hx(ctx, op.ham, Xb.p, HXb.p, kc, 0.0, op.prec);
-          if (s != OMEN_OK) return s;
-          hx += kc;
-          std::vector<double> lamk, resk, bd;
-          s = rayleigh_residuals(op, Xb.p, HXb.p, Rb.p, kc, lamk, resk);
-          if (s != OMEN_OK) return s;
-          std::vector<double> lam(lamk.begin(), lamk.begin() + nev), res(resk.begin(), resk.begin() + nev);
-          error_bounds(lamk, lam, res, bd);
-          done = *std::max_element(bd.begin(), bd.end()) <= o->tol;
           if (!done) gateA = std::min(gateA, rmax) * 0.01;
         }
       }

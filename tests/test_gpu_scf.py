@@ -85,3 +85,32 @@ def test_scf_matches_oracle(ctx, hist):
     assert abs(info["iterations"] - info_ref["iterations"]) <= 1
     np.testing.assert_allclose(phi.cpu().numpy(), phi_ref, atol=1e-6, rtol=0)
     assert abs(info["E_F"] - info_ref["E_F"]) < 1e-6
+
+
+def test_scf_two_k_points_2x2x40_slab_matches_oracle(ctx):
+    """The self-consistent loop on a 2x2x40-cell delta layer (1,280 atoms, 12,800 complex rows,
+    21.7 nm along z) with two wave vectors of the 2x2 lateral mesh (the other two are their time
+    reversals), 16 states per k nearest sigma, on the 0.2-nm grid (5x5x109): the converged
+    potential within 1e-6 V and the Fermi level within 1e-6 eV of the oracle loop, whose states
+    come from sparse shift-invert solves."""
+    from paper_1003_4570_gb300 import omen
+    spec, p, (_, w) = synth.delta_layer(2, 40, seed=5)
+    a = spec.a_nm
+    L = 2 * a
+    grid = poisson.Grid(round(L / 0.2), round(L / 0.2), round(40 * a / 0.2), L, L, 40 * a)
+    ns = 1e14
+    rho = synth.donor_rho_on_grid(ns, w, grid.nx, grid.ny, grid.nz, grid.Lz_nm)
+    ks = [(0.25 * 2 * np.pi / L, 0.25 * 2 * np.pi / L, 0.0), (0.25 * 2 * np.pi / L, -0.25 * 2 * np.pi / L, 0.0)]
+    eg = synth.GAPPED_SI_EC - synth.GAPPED_SI_EV
+    kw = dict(n_electrons=ns * (L * 1e-7) ** 2, kT=8.617333262e-5 * 4, kpts=ks, kweights=[0.5, 0.5], nev=16,
+              sigma=synth.GAPPED_SI_EC - 0.4 * eg, e_cut=0.5 * (synth.GAPPED_SI_EC + synth.GAPPED_SI_EV))
+    phi_ref, info_ref = scf.scf(spec, p, grid, rho, kw["n_electrons"], kw["kT"], ks, kw["kweights"], kw["nev"],
+                                kw["sigma"], kw["e_cut"], mix=0.3, tol_V=1e-6, max_iter=100, mix_history=6)
+    lat = omen.omen_build_lattice(ctx, spec)
+    phi = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+    info, st = omen.omen_scf(ctx, lat, p, grid, phi, torch.from_numpy(rho).cuda(), eig_tol=1e-10, eig_block=4,
+                             eig_basis=64, mix=0.3, tol_V=1e-6, max_iter=100, mix_history=6, **kw)
+    assert info["converged"] == 1, info
+    assert abs(info["iterations"] - info_ref["iterations"]) <= 2, (info["iterations"], info_ref["iterations"])
+    np.testing.assert_allclose(phi.cpu().numpy(), phi_ref, atol=1e-6, rtol=0)
+    assert abs(info["E_F"] - info_ref["E_F"]) < 1e-6
