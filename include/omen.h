@@ -120,6 +120,11 @@ omen_status omen_set_reorthogonalization(omen_ctx* ctx, int policy);
  * multiplicity needs no check. */
 omen_status omen_set_locking_check(omen_ctx* ctx, int enable);
 
+/* The device's FP64 fused multiply-add rate in TFLOP/s (no counterpart in the paper): eight
+ * independent FMA chains per thread in one resident wave, best of three timed launches.  The FP64
+ * products of this library are bound by that rate, so their roofline is reported against it. */
+omen_status omen_probe_fp64_rate(omen_ctx* ctx, double* tflops);
+
 /* ---- structure (paper Section II-A: atoms of the domain and their neighbours) ---------- */
 
 typedef struct {

@@ -163,6 +163,7 @@ def lib():
             "omen_set_graph_capture": (i, [vp, i]),
             "omen_set_reorthogonalization": (i, [vp, i]),
             "omen_set_locking_check": (i, [vp, i]),
+            "omen_probe_fp64_rate": (i, [vp, C.POINTER(d)]),
             "omen_tune_hx": (i, [vp, vp, i, i, i, C.POINTER(TuneResult)]),
             "omen_tune_hx_kbatch": (i, [vp, vp, i, i, C.POINTER(TuneResult)]),
             "omen_hx_set_tile": (i, [vp, vp, i, i, i]),
@@ -285,6 +286,13 @@ OMEN_REORTH_FULL, OMEN_REORTH_SEMI, OMEN_REORTH_PARTIAL = 0, 1, 2
 
 def omen_set_reorthogonalization(ctx: Context, policy) -> None:
     ctx.check(lib().omen_set_reorthogonalization(ctx.handle, int(policy)))
+
+
+def omen_probe_fp64_rate(ctx: Context) -> float:
+    """Measured FP64 FMA rate of the device (TFLOP/s)."""
+    t = C.c_double()
+    ctx.check(lib().omen_probe_fp64_rate(ctx.handle, C.byref(t)))
+    return t.value
 
 
 def omen_set_locking_check(ctx: Context, enable: bool) -> None:

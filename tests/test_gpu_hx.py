@@ -245,3 +245,11 @@ def test_hx_host_overlapped_slabs(ctx, per):
     from paper_1003_4570_gb300.omen import lib
     ctx.check(lib().omen_hx_host(ctx.handle, ham.handle, xp.data_ptr(), yp.data_ptr(), 2, 0.3))
     assert np.array_equal(yp.numpy(), y)
+
+
+def test_fp64_rate_probe(ctx):
+    """The FP64 FMA-rate probe the roofline uses returns a plausible device rate (GB300's nominal
+    FP64 rate is 1.25 TFLOP/s; a probe outside 0.1-5 TFLOP/s would mean the timing is broken)."""
+    from paper_1003_4570_gb300 import omen
+    r = omen.omen_probe_fp64_rate(ctx)
+    assert 0.1 < r < 5.0, r
