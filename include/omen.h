@@ -412,8 +412,12 @@ typedef struct {
  * phi = 0 V on the planes z = 0 and z = Lz. */
 
 typedef struct {
-  double rtol;               /* stop when ||r|| <= rtol ||b|| */
+  double rtol;               /* stop when ||r|| <= rtol ||b|| (b - A x in FP64 in both forms) */
   int max_iter;
+  int precision;             /* OMEN_F64: FP64 iterations.  OMEN_F32_REFINE64: FP32 iterations
+                                whose residual is replaced by the FP64 one b - A x after every
+                                10x drop (reliable updates); x, the stopping test and the answer
+                                stay FP64.  Zero-initialised options give OMEN_F64. */
 } omen_cg_opts;
 
 typedef struct {
@@ -424,10 +428,11 @@ typedef struct {
 } omen_solve_info;
 
 /* Solve -div(eps0 eps_r grad phi) = rho (7-point finite differences, periodic x and y,
- * phi = 0 at both z ends) by conjugate gradients in FP64, all iterations in one cooperative
- * launch (paper: finite-difference Poisson solver, Section III-A item 3).
- * rho_dev: C/m^3; phi_dev: V, initial guess in, solution out.  ENOCONV at max_iter; EINVAL for
- * a grid of 2^31 or more unknowns. */
+ * phi = 0 at both z ends) by conjugate gradients, all iterations in one cooperative launch
+ * (paper: finite-difference Poisson solver, Section III-A item 3), in FP64 or with FP32
+ * iterations and FP64 residual replacement (opts->precision).
+ * rho_dev: C/m^3; phi_dev: V, initial guess in, solution out (rho = 0 gives phi = 0).
+ * ENOCONV at max_iter; EINVAL for a grid of 2^31 or more unknowns or another precision. */
 omen_status omen_poisson(omen_ctx* ctx, const omen_grid* grid, const double* rho_dev, double* phi_dev,
                          const omen_cg_opts* opts, omen_solve_info* info);
 
@@ -443,7 +448,8 @@ omen_status omen_poisson(omen_ctx* ctx, const omen_grid* grid, const double* rho
  *    across a cudaDeviceReset would be stale); the first call on a device loads the library's
  *    device code there, so make that first call before any stream capture.
  *  - Grids with more than OMEN_POISSON_STATIC_MAX_UNKNOWNS interior unknowns
- *    (nx*ny*(nz-1)) are rejected with OMEN_EINVAL; other argument errors also return
+ *    (nx*ny*(nz-1)) are rejected with OMEN_EINVAL, and so is opts->precision other than
+ *    OMEN_F64 (the iterations here are FP64); other argument errors also return
  *    OMEN_EINVAL, CUDA failures OMEN_ECUDA, hitting max_iter OMEN_ENOCONV.  No message
  *    is recorded (there is no context).
  *  - All calls share the one array, which keeps the last call's contents; every word is
@@ -477,7 +483,8 @@ typedef struct {
 typedef struct {
   double tol_V;              /* stop when the largest change of a Newton step is below tol_V */
   int max_iter;              /* Newton steps */
-  omen_cg_opts cg;           /* each step's CG on the Jacobian (relative residual, iterations) */
+  omen_cg_opts cg;           /* each step's CG on the Jacobian (relative residual, iterations;
+                                the precision field is not used: these iterations are FP64) */
 } omen_newton_opts;
 
 typedef struct {

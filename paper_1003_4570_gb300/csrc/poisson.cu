@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(256) cg_kernel(PGrid g, const double* __restri
   double rr = grid_total(part0, sh);
   const double bb = grid_total(part2, sh);
   const double stop = rtol * rtol * bb;
+  if (bb == 0.0)   // b = 0: the solution is x = 0 whatever the initial guess
+    for (long long i = t0; i < n; i += stride) x[i] = 0.0;
   int it = 0;
   while (rr > stop && it < max_iter && bb > 0.0) {
     double lpq = 0.0;
@@ -111,12 +113,329 @@ __global__ void __launch_bounds__(256) cg_kernel(PGrid g, const double* __restri
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Mixed-precision CG: the iterations in FP32, the residual replaced by the true FP64
+// residual b - A x whenever the FP32 recurrence residual has fallen by a factor kDelta since
+// the last replacement ("reliable updates", van der Vorst & Ye, SIAM J. Sci. Comput. 22, 1716
+// (2000)).  The search direction is kept across a replacement, so the Krylov recurrence goes
+// on and the iteration count stays near the FP64 one, while each iteration moves FP32 words
+// on the FP32 pipe.  The FP32 system is scaled to unit size: A^ = A / c_max and
+// r^ = r * s with s = 1 / rms(r), so the FP32 sums of squares stay far from overflow for any
+// grid spacing; the correction d^ it accumulates maps back as d = d^ / (c_max s).  The
+// solution x and the stopping test ||b - A x|| <= rtol ||b|| stay in FP64.
+struct PGrid32 {
+  int nx, ny, nzi;
+  float cx, cy, cz;          // 1/h^2 divided by the largest of the three
+};
+
+__device__ __forceinline__ float stencil32_at(const float* __restrict__ v, const PGrid32& g, int i, int j, int k,
+                                              long long idx) {
+  const long long plane = (long long)g.nx * g.ny;
+  const float c = v[idx];
+  const int ip = (i + 1 == g.nx) ? 0 : i + 1, im = (i == 0) ? g.nx - 1 : i - 1;
+  const long long row = idx - i;
+  const long long rn = (j + 1 == g.ny) ? row - (long long)(g.ny - 1) * g.nx : row + g.nx;
+  const long long rs = (j == 0) ? row + (long long)(g.ny - 1) * g.nx : row - g.nx;
+  float s = g.cx * (2.f * c - v[row + ip] - v[row + im]);
+  s += g.cy * (2.f * c - v[rn + i] - v[rs + i]);
+  const float up = (k + 1 < g.nzi) ? v[idx + plane] : 0.f;
+  const float dn = (k > 0) ? v[idx - plane] : 0.f;
+  s += g.cz * (2.f * c - up - dn);
+  return s;
+}
+
+// Visit every interior unknown with its coordinates: rows of x over the CTAs and a row's
+// points over the threads when rows are wide, otherwise points over all threads with the
+// coordinates by 32-bit division (n < 2^31).
+template <class F>
+__device__ __forceinline__ void for_each_point(const PGrid& g, F&& f) {
+  if (g.nx >= 64) {
+    const long long nrow = (long long)g.ny * g.nzi;
+    for (long long rw = blockIdx.x; rw < nrow; rw += gridDim.x) {
+      const int j = (int)(rw % g.ny), k = (int)(rw / g.ny);
+      const long long base = rw * g.nx;
+      for (int i = threadIdx.x; i < g.nx; i += blockDim.x) f(i, j, k, base + i);
+    }
+  } else {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.n; idx += stride) {
+      const unsigned u = (unsigned)idx;
+      const int i = (int)(u % (unsigned)g.nx), j = (int)((u / (unsigned)g.nx) % (unsigned)g.ny);
+      const int k = (int)(u / ((unsigned)g.nx * (unsigned)g.ny));
+      f(i, j, k, idx);
+    }
+  }
+}
+
+static constexpr double kReliableDelta = 0.1;   // replace the residual after a 10x drop
+
+// The FP32 passes on grids with rows of 32 points or more: a warp takes a row (its
+// coordinates once), 32 consecutive points per chunk, and issues the loads of kChunks chunks
+// before their arithmetic, so each thread keeps several independent loads in flight.
+static constexpr int kChunks = 2;
+
+struct Nb7 {
+  float c, xp, xm, yp, ym, zp, zm;
+};
+
+struct RowGeo {
+  long long row, rn, rs, plane;   // first index of this row, of the rows at j+1 and j-1; plane size
+  bool up, dn;                    // neighbours at k+1 and k-1 are unknowns (else phi = 0)
+};
+
+__device__ __forceinline__ RowGeo row_geo(const PGrid32& g, long long rw) {
+  RowGeo r;
+  const int j = (int)(rw % g.ny), k = (int)(rw / g.ny);
+  r.row = rw * g.nx;
+  r.rn = (j + 1 == g.ny) ? r.row - (long long)(g.ny - 1) * g.nx : r.row + g.nx;
+  r.rs = (j == 0) ? r.row + (long long)(g.ny - 1) * g.nx : r.row - g.nx;
+  r.plane = (long long)g.nx * g.ny;
+  r.up = k + 1 < g.nzi;
+  r.dn = k > 0;
+  return r;
+}
+
+__device__ __forceinline__ void load_nb(const float* __restrict__ v, const PGrid32& g, const RowGeo& rg, int i,
+                                        bool ok, Nb7& o) {
+  o = Nb7{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (ok) {
+    const int ip = (i + 1 == g.nx) ? 0 : i + 1, im = (i == 0) ? g.nx - 1 : i - 1;
+    o.c = v[rg.row + i];
+    o.xp = v[rg.row + ip];
+    o.xm = v[rg.row + im];
+    o.yp = v[rg.rn + i];
+    o.ym = v[rg.rs + i];
+    if (rg.up) o.zp = v[rg.row + i + rg.plane];
+    if (rg.dn) o.zm = v[rg.row + i - rg.plane];
+  }
+}
+
+__device__ __forceinline__ float apply_nb(const PGrid32& g, const Nb7& o) {
+  float s = g.cx * (2.f * o.c - o.xp - o.xm);
+  s += g.cy * (2.f * o.c - o.yp - o.ym);
+  s += g.cz * (2.f * o.c - o.zp - o.zm);
+  return s;
+}
+
+// <p, A^ p> over this thread's points (rows of 32 points or more)
+__device__ __forceinline__ float pass_pq_rows(const PGrid32& g, const float* __restrict__ p) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long nrow = (long long)g.ny * g.nzi;
+  const int nch = (g.nx + 31) >> 5;
+  float acc = 0.f;
+  for (long long rw = gw; rw < nrow; rw += nw) {
+    const RowGeo rg = row_geo(g, rw);
+    for (int c0 = 0; c0 < nch; c0 += kChunks) {
+      Nb7 nb[kChunks];
+#pragma unroll
+      for (int u = 0; u < kChunks; ++u) {
+        const int i = (c0 + u) * 32 + lane;
+        load_nb(p, g, rg, i, c0 + u < nch && i < g.nx, nb[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kChunks; ++u) acc += nb[u].c * apply_nb(g, nb[u]);
+    }
+  }
+  return acc;
+}
+
+// d += alpha p, r -= alpha A^ p; returns the sum of the new r^2 over this thread's points
+__device__ __forceinline__ float pass_update_rows(const PGrid32& g, const float* __restrict__ p,
+                                                  float* __restrict__ d, float* __restrict__ r, float alpha) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long nrow = (long long)g.ny * g.nzi;
+  const int nch = (g.nx + 31) >> 5;
+  float acc = 0.f;
+  for (long long rw = gw; rw < nrow; rw += nw) {
+    const RowGeo rg = row_geo(g, rw);
+    for (int c0 = 0; c0 < nch; c0 += kChunks) {
+      Nb7 nb[kChunks];
+      float dv[kChunks], rv[kChunks];
+#pragma unroll
+      for (int u = 0; u < kChunks; ++u) {
+        const int i = (c0 + u) * 32 + lane;
+        const bool ok = c0 + u < nch && i < g.nx;
+        load_nb(p, g, rg, i, ok, nb[u]);
+        dv[u] = ok ? d[rg.row + i] : 0.f;
+        rv[u] = ok ? r[rg.row + i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kChunks; ++u) {
+        const int i = (c0 + u) * 32 + lane;
+        if (c0 + u < nch && i < g.nx) {
+          d[rg.row + i] = dv[u] + alpha * nb[u].c;
+          const float ri = rv[u] - alpha * apply_nb(g, nb[u]);
+          r[rg.row + i] = ri;
+          acc += ri * ri;
+        }
+      }
+    }
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(256, 4) cg_mixed_kernel(PGrid g, PGrid32 g32, double cmax,
+                                                       const double* __restrict__ rho, double scale,
+                                                       double* __restrict__ x, float* __restrict__ r,
+                                                       float* __restrict__ p, float* __restrict__ d,
+                                                       double* __restrict__ part, double rtol, int max_iter,
+                                                       CGOut* __restrict__ out) {
+  cgr::grid_group grid = cgr::this_grid();
+  __shared__ double sh[32];
+  const long long n = g.n;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double* part0 = part;
+  double* part1 = part + gridDim.x;
+  double* part2 = part + 2 * gridDim.x;
+  // true residual in FP64 (and ||b||^2 on the first call)
+  auto true_residual = [&](bool with_b, double* bb_out) -> double {
+    double lrr = 0.0, lbb = 0.0;
+    for_each_point(g, [&](int i, int j, int k, long long idx) {
+      const double b = scale * rho[idx];
+      const double ri = b - stencil_at(x, g, i, j, k, idx);
+      lrr += ri * ri;
+      lbb += b * b;
+    });
+    double v = block_sum(lrr, sh);
+    if (threadIdx.x == 0) part0[blockIdx.x] = v;
+    if (with_b) {
+      v = block_sum(lbb, sh);
+      if (threadIdx.x == 0) part2[blockIdx.x] = v;
+    }
+    grid.sync();
+    if (with_b) *bb_out = grid_total(part2, sh);
+    return grid_total(part0, sh);
+  };
+  // r^ = (b - A x) * s in FP32; returns ||r^||^2 (grid-wide)
+  auto load_residual = [&](double s, bool init) -> double {
+    float lr = 0.f;
+    for_each_point(g, [&](int i, int j, int k, long long idx) {
+      const double ri = scale * rho[idx] - stencil_at(x, g, i, j, k, idx);
+      const float rs = (float)(ri * s);
+      r[idx] = rs;
+      if (init) {
+        p[idx] = rs;
+        d[idx] = 0.f;
+      }
+      lr += rs * rs;
+    });
+    const double v = block_sum((double)lr, sh);
+    if (threadIdx.x == 0) part1[blockIdx.x] = v;
+    grid.sync();
+    return grid_total(part1, sh);
+  };
+  double bb = 0.0;
+  double rr64 = true_residual(true, &bb);
+  const double stop = rtol * rtol * bb;
+  int it = 0;
+  bool conv = !(rr64 > stop);
+  if (bb == 0.0) {
+    // b = 0: the solution is x = 0 whatever the initial guess
+    for (long long i = t0; i < n; i += stride) x[i] = 0.0;
+    rr64 = 0.0;
+    conv = true;
+  }
+  if (!conv && it < max_iter) {
+    double s = 1.0 / sqrt(rr64 / (double)n);
+    double rr = load_residual(s, true);
+    double rmax = rr;
+    const double delta2 = kReliableDelta * kReliableDelta;
+    for (;;) {
+      // q = A^ p, <p, q>
+      float lpq = 0.f;
+      if (g.nx >= 32)
+        lpq = pass_pq_rows(g32, p);
+      else
+        for_each_point(g, [&](int i, int j, int k, long long idx) { lpq += p[idx] * stencil32_at(p, g32, i, j, k, idx); });
+      double v = block_sum((double)lpq, sh);
+      if (threadIdx.x == 0) part0[blockIdx.x] = v;
+      grid.sync();
+      const float alpha = (float)(rr / grid_total(part0, sh));
+      // d += alpha p, r -= alpha A^ p (the product recomputed rather than stored)
+      float lr = 0.f;
+      if (g.nx >= 32) {
+        lr = pass_update_rows(g32, p, d, r, alpha);
+      } else {
+        for_each_point(g, [&](int i, int j, int k, long long idx) {
+          const float pi = p[idx];
+          const float qi = stencil32_at(p, g32, i, j, k, idx);
+          d[idx] += alpha * pi;
+          const float ri = r[idx] - alpha * qi;
+          r[idx] = ri;
+          lr += ri * ri;
+        });
+      }
+      v = block_sum((double)lr, sh);
+      if (threadIdx.x == 0) part1[blockIdx.x] = v;
+      grid.sync();
+      double rn = grid_total(part1, sh);
+      ++it;
+      double beta_scale = 1.0;
+      if (rn < delta2 * rmax || rn <= stop * s * s || it >= max_iter) {
+        // fold the FP32 correction into x and replace the residual by the FP64 one
+        const double back = 1.0 / (cmax * s);
+        for (long long i = t0; i < n; i += stride) {
+          x[i] += back * (double)d[i];
+          d[i] = 0.f;
+        }
+        grid.sync();
+        rr64 = true_residual(false, nullptr);
+        if (!(rr64 > stop)) {
+          conv = true;
+          break;
+        }
+        if (it >= max_iter) break;
+        const double s_new = 1.0 / sqrt(rr64 / (double)n);
+        const double ratio = s_new / s;
+        rn = load_residual(s_new, false);
+        // p is still in the old units: rescale it inside the update below, and the old
+        // <r, r> with it
+        rr *= ratio * ratio;
+        beta_scale = ratio;
+        s = s_new;
+        rmax = rn;
+      }
+      const float beta = (float)(rn / rr * beta_scale);
+      rr = rn;
+      // p = r + beta p, four elements per thread in flight
+      for (long long i0 = t0; i0 < n; i0 += 4 * stride) {
+        float rv[4], pv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long i = i0 + u * stride;
+          rv[u] = i < n ? r[i] : 0.f;
+          pv[u] = i < n ? p[i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long i = i0 + u * stride;
+          if (i < n) p[i] = rv[u] + beta * pv[u];
+        }
+      }
+      grid.sync();
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out->iterations = it;
+    out->converged = conv;
+    out->rel = bb > 0.0 ? sqrt(rr64 / bb) : 0.0;
+  }
+}
+
 extern "C" omen_status omen_poisson(omen_ctx* ctx, const omen_grid* gr, const double* rho, double* phi,
                                     const omen_cg_opts* o, omen_solve_info* info) {
   if (!ctx || !gr || !rho || !phi || !o) return set_err(ctx, OMEN_EINVAL, "null argument");
   if (gr->nx < 1 || gr->ny < 1 || gr->nz < 2) return set_err(ctx, OMEN_EINVAL, "grid needs nx, ny >= 1 and nz >= 2");
   if (!(gr->Lx_nm > 0 && gr->Ly_nm > 0 && gr->Lz_nm > 0 && gr->eps_r > 0)) return set_err(ctx, OMEN_EINVAL, "grid lengths and eps_r must be > 0");
   if (!(o->rtol > 0) || o->max_iter < 1) return set_err(ctx, OMEN_EINVAL, "cg options");
+  if (o->precision != OMEN_F64 && o->precision != OMEN_F32_REFINE64)
+    return set_err(ctx, OMEN_EINVAL, "cg precision must be OMEN_F64 or OMEN_F32_REFINE64");
+  const bool mixed = o->precision == OMEN_F32_REFINE64;
   OMEN_CUDA(ctx, cudaSetDevice(ctx->device));
   auto t0 = std::chrono::steady_clock::now();
   PGrid g;
@@ -132,26 +451,40 @@ extern "C" omen_status omen_poisson(omen_ctx* ctx, const omen_grid* gr, const do
   if (g.n >= (1ll << 31)) return set_err(ctx, OMEN_EINVAL, "grid larger than 2^31 unknowns");
   int dev_sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  OMEN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, 256, 0));
+  const void* kern = mixed ? (const void*)cg_mixed_kernel : (const void*)cg_kernel;
+  OMEN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
   long long want = (g.n + 255) / 256;
   int blocks = (int)std::min<long long>(want, (long long)dev_sms * std::max(1, per_sm));
   blocks = std::max(blocks, 1);
-  double* buf = nullptr;
-  const size_t vec = (size_t)g.n * sizeof(double);
+  // three work vectors (FP64, or FP32 for the mixed form), three partial-sum rows, the result
+  const size_t elem = mixed ? sizeof(float) : sizeof(double);
+  const size_t vec = ((size_t)g.n * elem + 255) / 256 * 256;
+  char* buf = nullptr;
   if (cudaMallocAsync(&buf, 3 * vec + 3 * blocks * sizeof(double) + sizeof(CGOut) + 64, ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     return set_err(ctx, OMEN_ENOMEM, "CG work vectors");
   }
-  double* r = buf;
-  double* p = r + g.n;
-  double* q = p + g.n;
-  double* part = q + g.n;
+  double* part = reinterpret_cast<double*>(buf + 3 * vec);
   CGOut* out = reinterpret_cast<CGOut*>(part + 3 * blocks);
   double scale = 1.0 / (kEps0 * gr->eps_r);
   double rtol = o->rtol;
   int max_iter = o->max_iter;
-  void* args[] = {&g, &rho, &scale, &phi, &r, &p, &q, &part, &rtol, &max_iter, &out};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)cg_kernel, dim3(blocks), dim3(256), args, 0, ctx->stream);
+  cudaError_t e;
+  if (mixed) {
+    const double cmax = std::max(g.cx, std::max(g.cy, g.cz));
+    PGrid32 g32{g.nx, g.ny, g.nzi, (float)(g.cx / cmax), (float)(g.cy / cmax), (float)(g.cz / cmax)};
+    float* r = reinterpret_cast<float*>(buf);
+    float* p = reinterpret_cast<float*>(buf + vec);
+    float* d = reinterpret_cast<float*>(buf + 2 * vec);
+    void* args[] = {&g, &g32, (void*)&cmax, &rho, &scale, &phi, &r, &p, &d, &part, &rtol, &max_iter, &out};
+    e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(256), args, 0, ctx->stream);
+  } else {
+    double* r = reinterpret_cast<double*>(buf);
+    double* p = reinterpret_cast<double*>(buf + vec);
+    double* q = reinterpret_cast<double*>(buf + 2 * vec);
+    void* args[] = {&g, &rho, &scale, &phi, &r, &p, &q, &part, &rtol, &max_iter, &out};
+    e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(256), args, 0, ctx->stream);
+  }
   CGOut ho{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&ho, out, sizeof(CGOut), cudaMemcpyDeviceToHost, ctx->stream);
   cudaFreeAsync(buf, ctx->stream);
@@ -202,7 +535,7 @@ extern "C" omen_status omen_poisson_static(const omen_grid* gr, const double* rh
   if (!gr || !rho || !phi || !o) return OMEN_EINVAL;
   if (gr->nx < 1 || gr->ny < 1 || gr->nz < 2) return OMEN_EINVAL;
   if (!(gr->Lx_nm > 0 && gr->Ly_nm > 0 && gr->Lz_nm > 0 && gr->eps_r > 0)) return OMEN_EINVAL;
-  if (!(o->rtol > 0) || o->max_iter < 1) return OMEN_EINVAL;
+  if (!(o->rtol > 0) || o->max_iter < 1 || o->precision != OMEN_F64) return OMEN_EINVAL;
   const long long n = (long long)gr->nx * gr->ny * (gr->nz - 1);
   if (n > kStaticMaxUnknowns) return OMEN_EINVAL;   // grid larger than the static work area
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);

@@ -65,7 +65,7 @@ class Grid(C.Structure):
 
 
 class CGOpts(C.Structure):
-    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int)]
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int)]
 
 
 class TuneResult(C.Structure):
@@ -507,10 +507,11 @@ def grid_struct(g) -> Grid:
     return Grid(int(g.nx), int(g.ny), int(g.nz), float(g.Lx_nm), float(g.Ly_nm), float(g.Lz_nm), float(g.eps_r))
 
 
-def omen_poisson(ctx: Context, grid, rho_dev, phi_dev, rtol=1e-12, max_iter=100000):
-    """CG solve in place on phi_dev (initial guess in).  Returns the solve info dict."""
+def omen_poisson(ctx: Context, grid, rho_dev, phi_dev, rtol=1e-12, max_iter=100000, precision=OMEN_F64):
+    """CG solve in place on phi_dev (initial guess in).  precision OMEN_F64, or OMEN_F32_REFINE64
+    for FP32 iterations with FP64 residual replacement.  Returns the solve info dict."""
     g = grid_struct(grid)
-    o = CGOpts(float(rtol), int(max_iter))
+    o = CGOpts(float(rtol), int(max_iter), int(precision))
     info = SolveInfo()
     ctx.check(lib().omen_poisson(ctx.handle, C.byref(g), _ptr(rho_dev), _ptr(phi_dev), C.byref(o), C.byref(info)))
     return info.as_dict()

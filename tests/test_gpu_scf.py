@@ -2,8 +2,9 @@
 
 The self-consistent loop is compared with linear and with Anderson mixing.
 
-Poisson CG against the oracle's sparse direct solve (1e-10 of max |phi|, including the
-11 x 11 x 217 grid of the 4x4x80-cell delta layer); cloud-in-cell deposit and gather
+Poisson CG, in FP64 and with FP32 iterations and FP64 residual replacement, against the
+oracle's sparse direct solve (1e-10 of max |phi|, including the 11 x 11 x 217 grid of the
+4x4x80-cell delta layer); zero charge gives zero potential; cloud-in-cell deposit and gather
 (1e-12 relative); electrons per atom from eigenvectors; Fermi level; and the full
 self-consistent loop against the oracle loop (converged potentials within 1e-6 V).
 """
@@ -35,6 +36,46 @@ def test_poisson_cg_matches_direct(ctx, dims):
     info = omen.omen_poisson(ctx, g, torch.from_numpy(rho).cuda(), phi, rtol=1e-13)
     assert info["converged"] == 1
     np.testing.assert_allclose(phi.cpu().numpy(), ref, atol=1e-10 * np.abs(ref).max(), rtol=0)
+
+
+@pytest.mark.parametrize("dims", [(11, 11, 217, 2.1724, 2.1724, 43.448), (5, 3, 40, 1.0, 0.7, 8.0), (1, 1, 9, 0.5, 0.5, 3.0),
+                                  (96, 6, 25, 9.6, 0.6, 2.5), (70, 1, 33, 7.0, 0.1, 3.3)])
+def test_poisson_mixed_precision_cg_matches_direct(ctx, dims):
+    """FP32 iterations with FP64 residual replacement reach the same FP64 answer; rows of 64
+    points or more take the row-per-CTA path, narrower grids the flat one."""
+    from paper_1003_4570_gb300 import omen
+    g = poisson.Grid(*dims)
+    rho = np.random.default_rng(5).normal(size=g.shape) * 1e6
+    ref = poisson.solve_direct(g, rho)
+    phi = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    info = omen.omen_poisson(ctx, g, torch.from_numpy(rho).cuda(), phi, rtol=1e-13, precision=omen.OMEN_F32_REFINE64)
+    assert info["converged"] == 1 and info["rel_residual"] <= 1e-13
+    np.testing.assert_allclose(phi.cpu().numpy(), ref, atol=1e-10 * np.abs(ref).max(), rtol=0)
+    # the FP32 recurrence keeps the FP64 iteration count within a small factor
+    phi64 = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    info64 = omen.omen_poisson(ctx, g, torch.from_numpy(rho).cuda(), phi64, rtol=1e-13)
+    assert info["iterations"] <= 1.5 * info64["iterations"] + 5
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_poisson_zero_charge_gives_zero_potential(ctx, mixed):
+    from paper_1003_4570_gb300 import omen
+    g = poisson.Grid(5, 3, 40, 1.0, 0.7, 8.0)
+    phi = torch.rand(g.shape, dtype=torch.float64, device="cuda") + 0.5
+    rho = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    info = omen.omen_poisson(ctx, g, rho, phi, precision=omen.OMEN_F32_REFINE64 if mixed else omen.OMEN_F64)
+    assert info["converged"] == 1
+    assert torch.count_nonzero(phi).item() == 0
+
+
+def test_poisson_precision_checked(ctx):
+    from paper_1003_4570_gb300 import omen
+    g = poisson.Grid(5, 3, 40, 1.0, 0.7, 8.0)
+    phi = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    rho = torch.ones(g.shape, dtype=torch.float64, device="cuda")
+    for bad in (omen.OMEN_F32, omen.OMEN_F64_DF, 7):
+        with pytest.raises(omen.OmenError, match="EINVAL"):
+            omen.omen_poisson(ctx, g, rho, phi, precision=bad)
 
 
 def test_deposit_gather_density_fermi(ctx):
