@@ -400,7 +400,8 @@ def measure_charge_poisson(ctx, omen, lat, ham, spec, nstates=16, ng=256):
                                "ms_per_iteration": tm / info["iterations"] * 1e3,
                                "GB_per_s": 7 * 4 * nu * info["iterations"] / tm / 1e9,
                                "rel_residual": info["rel_residual"], "speedup_vs_fp64": tp / tm,
-                               "max_abs_diff_vs_fp64_V": float((phi32 - phi).abs().max())}
+                               "max_abs_diff_vs_fp64_V": float((phi32 - phi).abs().max()),
+                               "max_abs_phi_V": float(phi.abs().max())}
     del phi32
     phi_atom = torch.empty(spec.natoms, dtype=torch.float64, device="cuda")
     t = timed(lambda: omen.omen_gather(ctx, lat, grid, phi, phi_atom))
@@ -996,6 +997,8 @@ def main():
                                                    "so-all", "effmass", "m2-ladder", "c5-solve", "hx-shapes", "vff", "eigs-1m",
                                                    "fp64-rate", "charge-poisson"],
                     help="profiling aid: run one side measurement alone and print its JSON")
+    ap.add_argument("--poisson-grid", type=int, default=256, metavar="NG",
+                    help="points per side of the Poisson grid of --only charge-poisson (profiling aid)")
     ap.add_argument("--tile", default="", metavar="THREADS,RB",
                     help="fix the H·X launch shape instead of tuning it (e.g. 64,2; profiling aid)")
     ap.add_argument("--lanczos-only", type=int, default=0, metavar="ITERS",
@@ -1046,7 +1049,7 @@ def main():
             spec, p = synth.config_sige_alloy(args.cells, seed=2)
             lat = omen.omen_build_lattice(ctx, spec)
             ham = omen.omen_assemble_H(ctx, lat, p)
-            print(json.dumps({"charge_poisson": measure_charge_poisson(ctx, omen, lat, ham, spec)}))
+            print(json.dumps({"charge_poisson": measure_charge_poisson(ctx, omen, lat, ham, spec, ng=args.poisson_grid)}))
             return
         if args.only == "hx-shapes":
             print(json.dumps({"hx_shapes": launch_hx_shapes(ctx, omen, args.cells)}))

@@ -59,18 +59,34 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
-// every block sums the partials of all blocks in index order (same result everywhere)
-__device__ __forceinline__ double grid_total(const double* __restrict__ part, double* sh) {
-  double t = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += part[b];
-  // ordered: reduce within the block deterministically
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+// The sum of a float per thread over the block: warp sums in FP32, then FP64 across warps
+// (valid in thread 0).  For the FP32 passes, whose per-thread sums are FP32 already; it keeps
+// the reduction off GB300's narrow FP64 pipe.
+__device__ __forceinline__ double block_sum_f(float v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0) sh[w] = t;
+  if (lane == 0) sh[w] = (double)v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  return t;  // valid in thread 0
+}
+
+// Every block sums the partials of all blocks in the same fixed order (the same result
+// everywhere): warp 0 adds them and broadcasts the total through shared memory, so the FP64
+// additions are one warp's, not the whole block's.
+__device__ __forceinline__ double grid_total(const double* __restrict__ part, double* sh) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) t += part[b];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[0] = t;
+  }
+  __syncthreads();
+  const double s = sh[0];
   __syncthreads();
   return s;
 }

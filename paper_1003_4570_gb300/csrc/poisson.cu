@@ -122,7 +122,10 @@ __global__ void __launch_bounds__(256) cg_kernel(PGrid g, const double* __restri
 // on the FP32 pipe.  The FP32 system is scaled to unit size: A^ = A / c_max and
 // r^ = r * s with s = 1 / rms(r), so the FP32 sums of squares stay far from overflow for any
 // grid spacing; the correction d^ it accumulates maps back as d = d^ / (c_max s).  The
-// solution x and the stopping test ||b - A x|| <= rtol ||b|| stay in FP64.
+// solution x and the stopping test ||b - A x|| <= rtol ||b|| stay in FP64.  The FP32
+// recurrence loses the superlinear end of FP64 CG: to 1e-8 on a 256^3 grid it takes 1.15x the
+// FP64 iterations, on the 11 x 11 x 217 grid of a delta layer about 1.4x, and to 1e-13 there
+// 1.9x.
 struct PGrid32 {
   int nx, ny, nzi;
   float cx, cy, cz;          // 1/h^2 divided by the largest of the three
@@ -140,6 +143,24 @@ __device__ __forceinline__ float stencil32_at(const float* __restrict__ v, const
   s += g.cy * (2.f * c - v[rn + i] - v[rs + i]);
   const float up = (k + 1 < g.nzi) ? v[idx + plane] : 0.f;
   const float dn = (k > 0) ? v[idx - plane] : 0.f;
+  s += g.cz * (2.f * c - up - dn);
+  return s;
+}
+
+// The 7-point stencil of r + beta p_old (the same values as stencil32_at of the stored p)
+__device__ __forceinline__ float stencil32_dir_at(const float* __restrict__ r, const float* __restrict__ po, float beta,
+                                                  const PGrid32& g, int i, int j, int k, long long idx) {
+  const long long plane = (long long)g.nx * g.ny;
+  auto val = [&](long long q) { return r[q] + beta * po[q]; };
+  const float c = val(idx);
+  const int ip = (i + 1 == g.nx) ? 0 : i + 1, im = (i == 0) ? g.nx - 1 : i - 1;
+  const long long row = idx - i;
+  const long long rn = (j + 1 == g.ny) ? row - (long long)(g.ny - 1) * g.nx : row + g.nx;
+  const long long rs = (j == 0) ? row + (long long)(g.ny - 1) * g.nx : row - g.nx;
+  float s = g.cx * (2.f * c - val(row + ip) - val(row + im));
+  s += g.cy * (2.f * c - val(rn + i) - val(rs + i));
+  const float up = (k + 1 < g.nzi) ? val(idx + plane) : 0.f;
+  const float dn = (k > 0) ? val(idx - plane) : 0.f;
   s += g.cz * (2.f * c - up - dn);
   return s;
 }
@@ -173,40 +194,42 @@ static constexpr double kReliableDelta = 0.1;   // replace the residual after a 
 // coordinates once), 32 consecutive points per chunk, and issues the loads of kChunks chunks
 // before their arithmetic, so each thread keeps several independent loads in flight.
 static constexpr int kChunks = 2;
+static constexpr int kDirChunks = 1;   // the direction pass loads r and p_old: as many loads
 
 struct Nb7 {
   float c, xp, xm, yp, ym, zp, zm;
 };
 
-struct RowGeo {
-  long long row, rn, rs, plane;   // first index of this row, of the rows at j+1 and j-1; plane size
-  bool up, dn;                    // neighbours at k+1 and k-1 are unknowns (else phi = 0)
+// Row base pointers of one row of the grid (32-bit offsets within a row: n < 2^31).
+template <typename P>
+struct RowPtr {
+  P c, n, s, u, d;   // this row; the rows at j+1 and j-1 (periodic); at k+1 and k-1 (or null)
 };
 
-__device__ __forceinline__ RowGeo row_geo(const PGrid32& g, long long rw) {
-  RowGeo r;
-  const int j = (int)(rw % g.ny), k = (int)(rw / g.ny);
-  r.row = rw * g.nx;
-  r.rn = (j + 1 == g.ny) ? r.row - (long long)(g.ny - 1) * g.nx : r.row + g.nx;
-  r.rs = (j == 0) ? r.row + (long long)(g.ny - 1) * g.nx : r.row - g.nx;
-  r.plane = (long long)g.nx * g.ny;
-  r.up = k + 1 < g.nzi;
-  r.dn = k > 0;
+template <typename P>
+__device__ __forceinline__ RowPtr<P> row_ptr(P v, const PGrid32& g, int rw) {
+  RowPtr<P> r;
+  const int j = rw % g.ny, k = rw / g.ny;
+  const int plane = g.nx * g.ny;
+  r.c = v + (long long)rw * g.nx;
+  r.n = (j + 1 == g.ny) ? r.c - (g.ny - 1) * g.nx : r.c + g.nx;
+  r.s = (j == 0) ? r.c + (g.ny - 1) * g.nx : r.c - g.nx;
+  r.u = (k + 1 < g.nzi) ? r.c + plane : nullptr;
+  r.d = (k > 0) ? r.c - plane : nullptr;
   return r;
 }
 
-__device__ __forceinline__ void load_nb(const float* __restrict__ v, const PGrid32& g, const RowGeo& rg, int i,
-                                        bool ok, Nb7& o) {
+__device__ __forceinline__ void load_nb(const RowPtr<const float*>& rp, const PGrid32& g, int i, bool ok, Nb7& o) {
   o = Nb7{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (ok) {
     const int ip = (i + 1 == g.nx) ? 0 : i + 1, im = (i == 0) ? g.nx - 1 : i - 1;
-    o.c = v[rg.row + i];
-    o.xp = v[rg.row + ip];
-    o.xm = v[rg.row + im];
-    o.yp = v[rg.rn + i];
-    o.ym = v[rg.rs + i];
-    if (rg.up) o.zp = v[rg.row + i + rg.plane];
-    if (rg.dn) o.zm = v[rg.row + i - rg.plane];
+    o.c = rp.c[i];
+    o.xp = rp.c[ip];
+    o.xm = rp.c[im];
+    o.yp = rp.n[i];
+    o.ym = rp.s[i];
+    if (rp.u) o.zp = rp.u[i];
+    if (rp.d) o.zm = rp.d[i];
   }
 }
 
@@ -217,25 +240,49 @@ __device__ __forceinline__ float apply_nb(const PGrid32& g, const Nb7& o) {
   return s;
 }
 
-// <p, A^ p> over this thread's points (rows of 32 points or more)
-__device__ __forceinline__ float pass_pq_rows(const PGrid32& g, const float* __restrict__ p) {
+// The new direction p = r + beta p_old at a point and at its six neighbours
+__device__ __forceinline__ void combine_nb(const Nb7& r, const Nb7& po, float beta, Nb7& o) {
+  o.c = r.c + beta * po.c;
+  o.xp = r.xp + beta * po.xp;
+  o.xm = r.xm + beta * po.xm;
+  o.yp = r.yp + beta * po.yp;
+  o.ym = r.ym + beta * po.ym;
+  o.zp = r.zp + beta * po.zp;
+  o.zm = r.zm + beta * po.zm;
+}
+
+// p = r + beta p_old into pn (each point written by its own thread; the neighbours' values are
+// formed again from r and p_old, so no barrier is needed between the update and the product),
+// and <p, A^ p> over this thread's points (rows of 32 points or more)
+__device__ __forceinline__ float pass_dir_pq_rows(const PGrid32& g, const float* __restrict__ r,
+                                                  const float* __restrict__ po, float* __restrict__ pn,
+                                                  float beta) {
   const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long nrow = (long long)g.ny * g.nzi;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nrow = g.ny * g.nzi;
   const int nch = (g.nx + 31) >> 5;
   float acc = 0.f;
-  for (long long rw = gw; rw < nrow; rw += nw) {
-    const RowGeo rg = row_geo(g, rw);
-    for (int c0 = 0; c0 < nch; c0 += kChunks) {
-      Nb7 nb[kChunks];
+  for (int rw = gw; rw < nrow; rw += nw) {
+    const RowPtr<const float*> rr = row_ptr(r, g, rw);
+    const RowPtr<const float*> rp = row_ptr(po, g, rw);
+    float* __restrict__ pr = pn + (long long)rw * g.nx;
+    for (int c0 = 0; c0 < nch; c0 += kDirChunks) {
+      Nb7 nr[kDirChunks], np[kDirChunks];
 #pragma unroll
-      for (int u = 0; u < kChunks; ++u) {
+      for (int u = 0; u < kDirChunks; ++u) {
         const int i = (c0 + u) * 32 + lane;
-        load_nb(p, g, rg, i, c0 + u < nch && i < g.nx, nb[u]);
+        load_nb(rr, g, i, i < g.nx, nr[u]);
+        load_nb(rp, g, i, i < g.nx, np[u]);
       }
 #pragma unroll
-      for (int u = 0; u < kChunks; ++u) acc += nb[u].c * apply_nb(g, nb[u]);
+      for (int u = 0; u < kDirChunks; ++u) {
+        const int i = (c0 + u) * 32 + lane;
+        Nb7 nb;
+        combine_nb(nr[u], np[u], beta, nb);
+        if (i < g.nx) pr[i] = nb.c;
+        acc += nb.c * apply_nb(g, nb);
+      }
     }
   }
   return acc;
@@ -245,31 +292,33 @@ __device__ __forceinline__ float pass_pq_rows(const PGrid32& g, const float* __r
 __device__ __forceinline__ float pass_update_rows(const PGrid32& g, const float* __restrict__ p,
                                                   float* __restrict__ d, float* __restrict__ r, float alpha) {
   const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long nrow = (long long)g.ny * g.nzi;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nrow = g.ny * g.nzi;
   const int nch = (g.nx + 31) >> 5;
   float acc = 0.f;
-  for (long long rw = gw; rw < nrow; rw += nw) {
-    const RowGeo rg = row_geo(g, rw);
+  for (int rw = gw; rw < nrow; rw += nw) {
+    const RowPtr<const float*> rp = row_ptr(p, g, rw);
+    float* __restrict__ dr = d + (long long)rw * g.nx;
+    float* __restrict__ rr = r + (long long)rw * g.nx;
     for (int c0 = 0; c0 < nch; c0 += kChunks) {
       Nb7 nb[kChunks];
       float dv[kChunks], rv[kChunks];
 #pragma unroll
       for (int u = 0; u < kChunks; ++u) {
         const int i = (c0 + u) * 32 + lane;
-        const bool ok = c0 + u < nch && i < g.nx;
-        load_nb(p, g, rg, i, ok, nb[u]);
-        dv[u] = ok ? d[rg.row + i] : 0.f;
-        rv[u] = ok ? r[rg.row + i] : 0.f;
+        const bool ok = i < g.nx;
+        load_nb(rp, g, i, ok, nb[u]);
+        dv[u] = ok ? dr[i] : 0.f;
+        rv[u] = ok ? rr[i] : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < kChunks; ++u) {
         const int i = (c0 + u) * 32 + lane;
-        if (c0 + u < nch && i < g.nx) {
-          d[rg.row + i] = dv[u] + alpha * nb[u].c;
+        if (i < g.nx) {
+          dr[i] = dv[u] + alpha * nb[u].c;
           const float ri = rv[u] - alpha * apply_nb(g, nb[u]);
-          r[rg.row + i] = ri;
+          rr[i] = ri;
           acc += ri * ri;
         }
       }
@@ -281,7 +330,7 @@ __device__ __forceinline__ float pass_update_rows(const PGrid32& g, const float*
 __global__ void __launch_bounds__(256, 4) cg_mixed_kernel(PGrid g, PGrid32 g32, double cmax,
                                                        const double* __restrict__ rho, double scale,
                                                        double* __restrict__ x, float* __restrict__ r,
-                                                       float* __restrict__ p, float* __restrict__ d,
+                                                       float* p, float* q, float* __restrict__ d,
                                                        double* __restrict__ part, double rtol, int max_iter,
                                                        CGOut* __restrict__ out) {
   cgr::grid_group grid = cgr::this_grid();
@@ -319,12 +368,12 @@ __global__ void __launch_bounds__(256, 4) cg_mixed_kernel(PGrid g, PGrid32 g32, 
       const float rs = (float)(ri * s);
       r[idx] = rs;
       if (init) {
-        p[idx] = rs;
+        p[idx] = 0.f;   // the first direction is r itself (beta = 0 below)
         d[idx] = 0.f;
       }
       lr += rs * rs;
     });
-    const double v = block_sum((double)lr, sh);
+    const double v = block_sum_f(lr, sh);
     if (threadIdx.x == 0) part1[blockIdx.x] = v;
     grid.sync();
     return grid_total(part1, sh);
@@ -345,32 +394,43 @@ __global__ void __launch_bounds__(256, 4) cg_mixed_kernel(PGrid g, PGrid32 g32, 
     double rr = load_residual(s, true);
     double rmax = rr;
     const double delta2 = kReliableDelta * kReliableDelta;
+    // the direction lives in two buffers: each iteration forms p = r + beta p_old from the old
+    // one into the other, so the update needs no barrier of its own
+    float* po = p;
+    float* pn = q;
+    float beta = 0.f;
     for (;;) {
-      // q = A^ p, <p, q>
+      // p = r + beta p_old, <p, A^ p>
       float lpq = 0.f;
-      if (g.nx >= 32)
-        lpq = pass_pq_rows(g32, p);
-      else
-        for_each_point(g, [&](int i, int j, int k, long long idx) { lpq += p[idx] * stencil32_at(p, g32, i, j, k, idx); });
-      double v = block_sum((double)lpq, sh);
+      if (g.nx >= 32) {
+        lpq = pass_dir_pq_rows(g32, r, po, pn, beta);
+      } else {
+        for_each_point(g, [&](int i, int j, int k, long long idx) {
+          const float pc = r[idx] + beta * po[idx];
+          pn[idx] = pc;
+          lpq += pc * stencil32_dir_at(r, po, beta, g32, i, j, k, idx);
+        });
+      }
+      const float* pd = pn;   // this iteration's direction
+      double v = block_sum_f(lpq, sh);
       if (threadIdx.x == 0) part0[blockIdx.x] = v;
       grid.sync();
       const float alpha = (float)(rr / grid_total(part0, sh));
       // d += alpha p, r -= alpha A^ p (the product recomputed rather than stored)
       float lr = 0.f;
       if (g.nx >= 32) {
-        lr = pass_update_rows(g32, p, d, r, alpha);
+        lr = pass_update_rows(g32, pd, d, r, alpha);
       } else {
         for_each_point(g, [&](int i, int j, int k, long long idx) {
-          const float pi = p[idx];
-          const float qi = stencil32_at(p, g32, i, j, k, idx);
+          const float pi = pd[idx];
+          const float qi = stencil32_at(pd, g32, i, j, k, idx);
           d[idx] += alpha * pi;
           const float ri = r[idx] - alpha * qi;
           r[idx] = ri;
           lr += ri * ri;
         });
       }
-      v = block_sum((double)lr, sh);
+      v = block_sum_f(lr, sh);
       if (threadIdx.x == 0) part1[blockIdx.x] = v;
       grid.sync();
       double rn = grid_total(part1, sh);
@@ -400,24 +460,11 @@ __global__ void __launch_bounds__(256, 4) cg_mixed_kernel(PGrid g, PGrid32 g32, 
         s = s_new;
         rmax = rn;
       }
-      const float beta = (float)(rn / rr * beta_scale);
+      beta = (float)(rn / rr * beta_scale);
       rr = rn;
-      // p = r + beta p, four elements per thread in flight
-      for (long long i0 = t0; i0 < n; i0 += 4 * stride) {
-        float rv[4], pv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const long long i = i0 + u * stride;
-          rv[u] = i < n ? r[i] : 0.f;
-          pv[u] = i < n ? p[i] : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const long long i = i0 + u * stride;
-          if (i < n) p[i] = rv[u] + beta * pv[u];
-        }
-      }
-      grid.sync();
+      float* t = po;
+      po = pn;
+      pn = t;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -452,19 +499,22 @@ extern "C" omen_status omen_poisson(omen_ctx* ctx, const omen_grid* gr, const do
   int dev_sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ctx->device);
   const void* kern = mixed ? (const void*)cg_mixed_kernel : (const void*)cg_kernel;
-  OMEN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
-  long long want = (g.n + 255) / 256;
-  int blocks = (int)std::min<long long>(want, (long long)dev_sms * std::max(1, per_sm));
+  const int threads = 256;
+  OMEN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+  if (per_sm < 1) return set_err(ctx, OMEN_ECUDA, "Poisson CG kernel does not fit on an SM");
+  long long want = (g.n + threads - 1) / threads;
+  int blocks = (int)std::min<long long>(want, (long long)dev_sms * per_sm);
   blocks = std::max(blocks, 1);
-  // three work vectors (FP64, or FP32 for the mixed form), three partial-sum rows, the result
+  // work vectors (three FP64, or four FP32 for the mixed form), three partial-sum rows, the result
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
+  const int nvec = mixed ? 4 : 3;
   const size_t vec = ((size_t)g.n * elem + 255) / 256 * 256;
   char* buf = nullptr;
-  if (cudaMallocAsync(&buf, 3 * vec + 3 * blocks * sizeof(double) + sizeof(CGOut) + 64, ctx->stream) != cudaSuccess) {
+  if (cudaMallocAsync(&buf, nvec * vec + 3 * blocks * sizeof(double) + sizeof(CGOut) + 64, ctx->stream) != cudaSuccess) {
     cudaGetLastError();
     return set_err(ctx, OMEN_ENOMEM, "CG work vectors");
   }
-  double* part = reinterpret_cast<double*>(buf + 3 * vec);
+  double* part = reinterpret_cast<double*>(buf + nvec * vec);
   CGOut* out = reinterpret_cast<CGOut*>(part + 3 * blocks);
   double scale = 1.0 / (kEps0 * gr->eps_r);
   double rtol = o->rtol;
@@ -475,9 +525,10 @@ extern "C" omen_status omen_poisson(omen_ctx* ctx, const omen_grid* gr, const do
     PGrid32 g32{g.nx, g.ny, g.nzi, (float)(g.cx / cmax), (float)(g.cy / cmax), (float)(g.cz / cmax)};
     float* r = reinterpret_cast<float*>(buf);
     float* p = reinterpret_cast<float*>(buf + vec);
-    float* d = reinterpret_cast<float*>(buf + 2 * vec);
-    void* args[] = {&g, &g32, (void*)&cmax, &rho, &scale, &phi, &r, &p, &d, &part, &rtol, &max_iter, &out};
-    e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(256), args, 0, ctx->stream);
+    float* q = reinterpret_cast<float*>(buf + 2 * vec);
+    float* d = reinterpret_cast<float*>(buf + 3 * vec);
+    void* args[] = {&g, &g32, (void*)&cmax, &rho, &scale, &phi, &r, &p, &q, &d, &part, &rtol, &max_iter, &out};
+    e = cudaLaunchCooperativeKernel(kern, dim3(blocks), dim3(threads), args, 0, ctx->stream);
   } else {
     double* r = reinterpret_cast<double*>(buf);
     double* p = reinterpret_cast<double*>(buf + vec);
