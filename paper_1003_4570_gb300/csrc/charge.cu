@@ -3,33 +3,91 @@
 // together under charge neutrality).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "omen_internal.h"
 #include "sk_device.cuh"
 #include "vec.cuh"
 #include "cic.cuh"
+#include "df.cuh"
 
 // n_atom[i] += w * sum_n occ[n] * sum_o |psi_n[o*N + i]|^2
-template <bool C>
-__global__ void density_kernel(const void* __restrict__ psiv, long long nrows, int natoms, int nb, int nstates,
-                               const double* __restrict__ occ, double w, double* __restrict__ n_atom) {
+//
+// The squares are summed on the FP32 pipe in double-float arithmetic (GB300's FP64 rate would
+// otherwise bound the kernel, one FP64 FMA per 8-byte amplitude).  Each FP64 amplitude v is
+// split, scaled by 2^32 (exact), into FP32 parts with integer operations only: hi keeps the
+// sign, the exponent and the leading 24 significant bits, lo is the rest rounded to FP32 (48
+// significant bits in all).  v^2 2^64 is then hi^2 (the FP32 product plus its exact FMA error)
+// + 2 hi lo + lo^2, the terms added with TwoSum into an FP32 pair (about 1e-14 relative).  The
+// scaling keeps amplitudes in [2^-83, 2^32) clear of FP32 underflow and overflow; smaller ones
+// (contributing below 2^-166) count as zero, and so do occupations below 2^-126.
+template <int kSplitShift>
+__device__ __forceinline__ float2 split_fp64(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  const int e = (int)((hi32 >> 20) & 0x7FFu);   // biased FP64 exponent
+  // FP32 exponent of hi: e - 1023 + 127 + shift
+  const int eh = e - 896 + kSplitShift;
+  if (eh <= 0) return make_float2(0.f, 0.f);     // |v| < 2^-158, or zero
+  const unsigned sign = hi32 & 0x80000000u;
+  const unsigned top23 = ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
+  const float hi = __uint_as_float(sign | ((unsigned)eh << 23) | top23);
+  // the remaining 29 bits: rem * 2^(e - 1075 + shift)
+  const unsigned rem = lo32 & 0x1FFFFFFFu;
+  const int el = e - 948 + kSplitShift;
+  const float scale = el > 0 ? __uint_as_float((unsigned)el << 23) : 0.f;
+  const float lo = __fmul_rn(__uint2float_rn(rem), scale);
+  return make_float2(hi, sign ? -lo : lo);
+}
+
+__device__ __forceinline__ void df_add_square(float& S, float& Cc, double v) {
+  const float2 h = split_fp64<32>(v);
+  const float p = __fmul_rn(h.x, h.x);
+  float e = __fmaf_rn(h.x, h.x, -p);
+  e = __fmaf_rn(__fmul_rn(2.f, h.x), h.y, e);
+  e = __fmaf_rn(h.y, h.y, e);
+  const float s = __fadd_rn(S, p);
+  const float bb = __fsub_rn(s, S);
+  const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  Cc = __fadd_rn(Cc, __fadd_rn(t, e));
+  S = s;
+}
+
+template <bool C, int NB>
+__global__ void __launch_bounds__(256) density_kernel(const void* __restrict__ psiv, long long nrows, int natoms,
+                                                      int nb_rt, int nstates, const double* __restrict__ occ,
+                                                      double w, double* __restrict__ n_atom) {
   using E = Elem<double, C>;
   const typename E::V* psi = static_cast<const typename E::V*>(psiv);
+  const int nb = NB > 0 ? NB : nb_rt;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < natoms; i += gridDim.x * blockDim.x) {
-    double acc = 0.0;
+    float AS = 0.f, AC = 0.f;   // sum over states of occ * (state's sum of squares)
     for (int s = 0; s < nstates; ++s) {
       const double f = occ[s];
       if (f == 0.0) continue;
-      double a = 0.0;
-      for (int o = 0; o < nb; ++o) {
-        const typename E::V v = psi[(size_t)s * nrows + (size_t)o * natoms + i];
-        const double re = E::re(v), im = E::im(v);
-        a += re * re + im * im;
+      const typename E::V* ps = psi + (size_t)s * nrows + i;
+      float S = 0.f, Cc = 0.f;
+      if constexpr (NB > 0) {
+        typename E::V v[NB];
+#pragma unroll
+        for (int o = 0; o < NB; ++o) v[o] = ps[(size_t)o * natoms];
+#pragma unroll
+        for (int o = 0; o < NB; ++o) {
+          df_add_square(S, Cc, E::re(v[o]));
+          if constexpr (C) df_add_square(S, Cc, E::im(v[o]));
+        }
+      } else {
+        for (int o = 0; o < nb; ++o) {
+          const typename E::V v = ps[(size_t)o * natoms];
+          df_add_square(S, Cc, E::re(v));
+          if constexpr (C) df_add_square(S, Cc, E::im(v));
+        }
       }
-      acc += f * a;
+      df_mac(AS, AC, df_norm(S, Cc), split_fp64<0>(f));
     }
-    n_atom[i] += w * acc;
+    // the squares carry the factor 2^64 of the split
+    n_atom[i] += w * (((double)AS + (double)AC) * 0x1p-64);
   }
 }
 
@@ -80,9 +138,33 @@ extern "C" omen_status omen_density_accum(omen_ctx* ctx, const omen_ham* h, cons
   }
   OMEN_CUDA(ctx, cudaMemcpyAsync(d_occ, occ_host, sizeof(double) * nstates, cudaMemcpyHostToDevice, ctx->stream));
   const int N = (int)(h->nrows / h->nb);   // atoms, or grid points of an effective-mass Hamiltonian
-  const unsigned grid = (unsigned)std::min(1024, (N + 255) / 256);
-  if (h->is_complex) density_kernel<true><<<grid, 256, 0, ctx->stream>>>(psi, h->nrows, N, h->nb, nstates, d_occ, w, n_atom);
-  else density_kernel<false><<<grid, 256, 0, ctx->stream>>>(psi, h->nrows, N, h->nb, nstates, d_occ, w, n_atom);
+  // one thread per atom, the grid a whole number of waves of 152-SM-sized blocks
+  const unsigned grid = (unsigned)std::max(1, std::min((N + 255) / 256, 152 * 8));
+  auto launch = [&](auto cplx, auto nbc) {
+    constexpr bool Cx = decltype(cplx)::value;
+    constexpr int NB = decltype(nbc)::value;
+    density_kernel<Cx, NB><<<grid, 256, 0, ctx->stream>>>(psi, h->nrows, N, h->nb, nstates, d_occ, w, n_atom);
+  };
+  using T_ = std::true_type;
+  using F_ = std::false_type;
+  using I1 = std::integral_constant<int, 1>;
+  using I5 = std::integral_constant<int, 5>;
+  using I10 = std::integral_constant<int, 10>;
+  using I20 = std::integral_constant<int, 20>;
+  using I0 = std::integral_constant<int, 0>;
+  if (h->is_complex) {
+    if (h->nb == 1) launch(T_{}, I1{});
+    else if (h->nb == 5) launch(T_{}, I5{});
+    else if (h->nb == 10) launch(T_{}, I10{});
+    else if (h->nb == 20) launch(T_{}, I20{});
+    else launch(T_{}, I0{});
+  } else {
+    if (h->nb == 1) launch(F_{}, I1{});
+    else if (h->nb == 5) launch(F_{}, I5{});
+    else if (h->nb == 10) launch(F_{}, I10{});
+    else if (h->nb == 20) launch(F_{}, I20{});
+    else launch(F_{}, I0{});
+  }
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(d_occ, ctx->stream);
   if (e != cudaSuccess) return set_err(ctx, OMEN_ECUDA, "density: %s", cudaGetErrorString(e));

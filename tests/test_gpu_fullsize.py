@@ -7,7 +7,11 @@ search over the whole structure, and the GPU products are compared on those rows
   max |y| over the sample), FP32 stored and matrix-free (2e-6);
 * the same alloy with spin-orbit, complex64 (20M rows, 2e-6);
 * the 4x4x80-cell delta-doped Si slab with its donor-sheet potential, k-batched complex64
-  products at 3 wave vectors (2e-6).
+  products at 3 wave vectors (2e-6);
+* the 8 lowest FP64 eigenpairs of the 1M-atom alloy, and 4 spin-orbit pairs from complex64
+  Lanczos with FP64 refinement: H x = lambda x on the oracle's rows (the sample plus the 64
+  atoms where each localised state is largest) to the solver's residual norm, and orthonormal
+  vectors.
 """
 import numpy as np
 import pytest
@@ -99,3 +103,62 @@ def test_delta_layer_kbatch_sampled_rows(ctx):
     for q, kv in enumerate(ks):
         rows, ref = hamiltonian.hx_rows(spec, p, x[q].astype(complex), atoms, bonds=bonds, U_atom=U, kvec=kv)
         np.testing.assert_allclose(y[q][rows], ref, atol=2e-6 * np.abs(ref).max(), rtol=0)
+
+
+def test_alloy_1m_atoms_lowest_eigenpairs_are_eigenpairs_of_the_oracle_rows(ctx, alloy):
+    """Eigen parity at 1M atoms, where no dense solve exists: the 8 lowest FP64 eigenpairs the
+    solver returns satisfy H x = lambda x on the sampled rows of the oracle's own Hamiltonian
+    (every residual component within the solver's residual norm), and are orthonormal."""
+    from paper_1003_4570_gb300 import omen
+    spec, p, bonds, atoms = alloy
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p)
+    n, nev = ham.nrows, 8
+    V = torch.empty(nev * n, dtype=torch.float64, device="cuda")
+    ev, info, _ = omen.omen_eigs(ctx, ham, nev, omen.OMEN_LOWEST, tol=1e-9, block=1, basis=64, max_iter=6000,
+                                 evecs_dev=V)
+    assert info["converged"] == 1 and np.all(np.diff(ev) >= 0)
+    Vm = V.view(nev, n)
+    G = (Vm @ Vm.T).cpu().numpy()
+    assert np.abs(G - np.eye(nev)).max() < 1e-10
+    X = Vm.cpu().numpy()
+    bound = info["max_residual"]
+    assert bound < 1e-3
+    for i in range(nev):
+        # the band-edge states of the random alloy are localised: check the rows where this
+        # state lives (its 64 largest atoms) as well as the fixed sample
+        w = (X[i].reshape(-1, spec.natoms) ** 2).sum(axis=0)
+        where = np.unique(np.concatenate([atoms, np.argsort(w)[-64:]]))
+        rows, ref = sampled_rows(spec, p, bonds, where, X[i])
+        r = ref - ev[i] * X[i][rows]
+        # each component of H x - lambda x is bounded by its norm
+        assert np.abs(r).max() <= 1.01 * bound + 1e-13, (i, np.abs(r).max(), bound)
+        # the bound is well below the size of the rows checked (the check is not on zeros)
+        assert np.abs(ref).max() > 10 * (1.01 * bound + 1e-13)
+
+
+def test_alloy_spin_orbit_1m_atoms_refined_eigenpairs_against_oracle_rows(ctx, alloy):
+    """The same check for the precision form at 20M complex rows: complex64 Lanczos with the
+    FP64 Rayleigh-Ritz refinement returns FP64 eigenvectors whose sampled residuals against the
+    oracle's spin-orbit rows stay within the refined residual norm."""
+    from paper_1003_4570_gb300 import omen
+    spec, p, bonds, atoms = alloy
+    lat = omen.omen_build_lattice(ctx, spec)
+    ham = omen.omen_assemble_H(ctx, lat, p, precision=omen.OMEN_F32_REFINE64, spin_orbit=True)
+    n, nev = ham.nrows, 4
+    V = torch.empty(nev * n, dtype=torch.complex128, device="cuda")
+    ev, info, _ = omen.omen_eigs(ctx, ham, nev, omen.OMEN_LOWEST, tol=1e-8, block=2, basis=64, max_iter=6000,
+                                 evecs_dev=V)
+    assert info["converged"] == 1
+    Vm = V.view(nev, n)
+    G = (Vm.conj() @ Vm.T).cpu().numpy()
+    assert np.abs(G - np.eye(nev)).max() < 1e-10
+    X = Vm.cpu().numpy()
+    bound = info["max_residual"]
+    for i in range(nev):
+        w = (np.abs(X[i].reshape(-1, spec.natoms)) ** 2).sum(axis=0)
+        where = np.unique(np.concatenate([atoms, np.argsort(w)[-64:]]))
+        rows, ref = sampled_rows(spec, p, bonds, where, X[i], spin_orbit=True)
+        r = ref - ev[i] * X[i][rows]
+        assert np.abs(r).max() <= 1.01 * bound + 1e-13, (i, np.abs(r).max(), bound)
+        assert np.abs(ref).max() > 10 * (1.01 * bound + 1e-13)

@@ -82,6 +82,41 @@ def test_poisson_precision_checked(ctx):
             omen.omen_poisson(ctx, g, rho, phi, precision=bad)
 
 
+@pytest.mark.parametrize("case", ["sp3s_real", "sp3d5s_real", "sp3d5s_bloch", "so", "effmass_real", "effmass_bloch"])
+def test_density_accum_wide_amplitude_range(ctx, case):
+    """Electrons per atom (per point for the effective-mass model) from states whose amplitudes
+    span 22 decades, against the oracle's FP64 sum (1e-13 relative): the kernel sums the squares
+    on the FP32 pipe from FP64 amplitudes split into two FP32 parts."""
+    from paper_1003_4570_gb300 import omen
+    if case.startswith("effmass"):
+        bloch = case.endswith("bloch")
+        spec = synth.effmass_spec(9, 7, 5, seed=3, periodic=(2, 2, 0) if bloch else (0, 0, 0),
+                                  kvec=(0.4, -0.2, 0.0) if bloch else None, u_amp=0.0)
+        ham = omen.omen_assemble_effmass(ctx, spec)
+        natoms = ham.nrows
+    else:
+        bloch = case in ("sp3d5s_bloch", "so")
+        lspec = synth.lattice_spec(2, 3, 2, (2, 2, 0) if bloch else (1, 1, 0), seed=5)
+        basis = 5 if case.startswith("sp3s_") else 10
+        p = synth.draw_tb_params(5, basis, 1)
+        lat = omen.omen_build_lattice(ctx, lspec)
+        ham = omen.omen_assemble_H(ctx, lat, p, spin_orbit=(case == "so"),
+                                   k=(0.3, 0.1, 0.0) if bloch else None)
+        natoms = lspec.natoms
+    rng = np.random.default_rng(11)
+    ns = 5
+    mag = 10.0 ** rng.uniform(-20, 2, size=(ns, ham.nrows))
+    assert ham.is_complex == (case in ("sp3d5s_bloch", "so", "effmass_bloch"))
+    psi = mag * rng.choice([-1.0, 1.0], size=mag.shape)
+    if ham.is_complex:
+        psi = psi * np.exp(1j * rng.uniform(0, 2 * np.pi, size=mag.shape))
+    occ = np.array([1.0, 0.5, 0.0, 0.25, 1e-3])
+    n = torch.zeros(natoms, dtype=torch.float64, device="cuda")
+    omen.omen_density_accum(ctx, ham, torch.from_numpy(np.ascontiguousarray(psi)).cuda(), ns, occ, 2.0, n)
+    ref = 2.0 * charge.atom_density(psi.T, occ, natoms)
+    np.testing.assert_allclose(n.cpu().numpy(), ref, rtol=1e-13, atol=0)
+
+
 def test_deposit_gather_density_fermi(ctx):
     from paper_1003_4570_gb300 import omen
     spec = synth.lattice_spec(2, 3, 4, (2, 2, 0), seed=9)
