@@ -714,10 +714,12 @@ def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400, nev=8,
     for i in range(n_train):
         phi = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
         try:
-            rho, info, _ = solve(1000 + i, phi)
+            rho, info, ts = solve(1000 + i, phi)
         except omen.OmenError as e:       # a profile whose loop did not finish is left out
             failed.append({"seed": 1000 + i, "error": str(e)[:120]})
             continue
+        # progress on stderr (stdout carries the one result line)
+        print(json.dumps({"scf_train": i, "iterations": info["iterations"], "seconds": ts}), file=sys.stderr, flush=True)
         omen.omen_mlp_features(ctx, net, grid, rho, X[ok])
         omen.omen_mlp_targets(ctx, net, grid, phi, T[ok])
         ok += 1
@@ -750,6 +752,8 @@ def measure_scf(ctx, omen, nzc=16, n_train=12, n_test=2, train_steps=400, nev=8,
             continue
         zi.append(info0["iterations"]); zt.append(s0)
         li.append(info1["iterations"]); lt.append(s1 + t_inf)
+        print(json.dumps({"scf_test": j, "zero_field": [info0["iterations"], s0], "learned": [info1["iterations"], s1 + t_inf]}),
+              file=sys.stderr, flush=True)
     return {"workload": f"delta-doped Si 1x1x{nzc} cells ({spec.natoms} atoms, {spec.natoms * 10} rows), Gamma, "
                         f"grid {grid.nx}x{grid.ny}x{grid.nz}, {nev} states nearest sigma, Anderson mixing, tol 1e-6 V",
             "zero_field": {"iterations": zi, "seconds": zt, "mean_iterations": float(np.mean(zi))},
