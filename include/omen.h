@@ -514,7 +514,9 @@ omen_status omen_state_weights(omen_ctx* ctx, const omen_ham* ham, const void* p
 
 /* n_atom_dev[i] += weight * sum_n occ_host[n] * sum_o |psi_n(o*natoms + i)|^2 for nstates FP64
  * (double or complex128) vectors psi_dev [nstates][nrows] of ham (paper: charge from the
- * filled states, Section III-A item 2). */
+ * filled states, Section III-A item 2).  The squares are summed in double-float arithmetic
+ * (about 1e-14 relative) on the FP32 pipe: amplitude components below 2^-83 in magnitude
+ * count as zero, components of 2^32 or more overflow, and non-finite ones give NaN. */
 omen_status omen_density_accum(omen_ctx* ctx, const omen_ham* ham, const void* psi_dev, int nstates,
                                const double* occ_host, double weight, double* n_atom_dev);
 

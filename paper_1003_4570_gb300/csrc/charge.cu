@@ -21,7 +21,8 @@
 // significant bits in all).  v^2 2^64 is then hi^2 (the FP32 product plus its exact FMA error)
 // + 2 hi lo + lo^2, the terms added with TwoSum into an FP32 pair (about 1e-14 relative).  The
 // scaling keeps amplitudes in [2^-83, 2^32) clear of FP32 underflow and overflow; smaller ones
-// (contributing below 2^-166) count as zero, and so do occupations below 2^-126.
+// (contributing below 2^-166) count as zero, and so do occupations below 2^-126.  Infinite or
+// NaN amplitudes (and finite ones of 2^96 or more) give NaN.
 template <int kSplitShift>
 __device__ __forceinline__ float2 split_fp64(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -30,6 +31,7 @@ __device__ __forceinline__ float2 split_fp64(double v) {
   // FP32 exponent of hi: e - 1023 + 127 + shift
   const int eh = e - 896 + kSplitShift;
   if (eh <= 0) return make_float2(0.f, 0.f);     // |v| < 2^-158, or zero
+  if (eh >= 255) return make_float2(__int_as_float(0x7fc00000), 0.f);   // beyond FP32, inf or NaN: NaN
   const unsigned sign = hi32 & 0x80000000u;
   const unsigned top23 = ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29);
   const float hi = __uint_as_float(sign | ((unsigned)eh << 23) | top23);
