@@ -957,6 +957,9 @@ def run_gpu(args, rank, world, local_rank):
             result["lanczos_500_iterations_80cubed_si"] = measure_cube_500(ctx, omen)
         result["hx_kbatch"] = measure_hx_kbatch(ctx, omen)
         result["kbatch"] = measure_kbatch(ctx, omen)
+        if args.cells == N_CELLS:
+            # the full batching workload: 8 structures x 128 wave vectors (about two minutes)
+            result["kbatch_full"] = measure_kbatch_full(ctx, omen)
         result["scf_learned_vs_zero"] = measure_scf(ctx, omen)
         result["effective_mass"] = measure_effmass(ctx, omen)
         if args.cells == N_CELLS:
